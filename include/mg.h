@@ -1,0 +1,200 @@
+/*
+ * mg.h - C ABI of the GB300 deflated multigrid solver for the 2D Schwinger-model
+ * Wilson-Dirac operator (Whyte, Wilcox, Morgan, "Deflated GMRES with Multigrid
+ * for Lattice QCD", arXiv:1912.02868).
+ *
+ * The library solves D x = b for many right-hand sides b with one operator D
+ * (Section 2: FGMRES(8) outer solver; three-grid adaptive multigrid V-cycle with
+ * GMRES(2) pre/post smoothing on the fine and intermediate grids; GMRES-DR(m,k)
+ * on the coarsest grid at the first outer iteration and GMRES-Proj(m,k) at every
+ * later one and for every later right-hand side).
+ *
+ * Conventions for every entry point
+ *  - Complex numbers are interleaved (re, im): complex128 = 2 doubles,
+ *    complex64 = 2 floats.
+ *  - Gauge field: complex128[L_t][L_x][2], mu = 0 is the x link, mu = 1 the t link,
+ *    |U| = 1.  The fermion is periodic in x and antiperiodic in t.
+ *  - Fine spinor: complex[L_t][L_x][2] (site = x + L_x t, spin fastest).
+ *  - Coarse vector on a grid of N_t x N_x sites: complex[N_t][N_x][24], dof
+ *    k = 12 c + j (chirality c, near-null vector j).
+ *  - Pointers marked "host or device" may point to pageable host memory, pinned
+ *    host memory or device memory of the current device; the library tells them
+ *    apart with cudaPointerGetAttributes.  Pointers marked "device" must be
+ *    device memory.  The caller keeps ownership of every pointer it passes.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Every call is ordered on that stream and returns after the results it
+ *    reports on the host are complete.
+ *  - Errors come back only as status codes; mg_last_error() returns a message
+ *    for the calling thread's last failure.  No entry point aborts the process.
+ *  - Handles are not thread-safe: one thread at a time per handle.
+ */
+#ifndef MG_H
+#define MG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mg_handle_s* mg_handle;
+
+typedef enum {
+    MG_OK = 0,
+    MG_EINVAL = -1,     /* invalid argument (shape, pointer, parameter) */
+    MG_ENOMEM = -2,     /* device allocation failed */
+    MG_ECUDA = -3,      /* a CUDA runtime call failed */
+    MG_ENOTCONV = -4,   /* a solve reached its iteration limit */
+    MG_EBUDGET = -5,    /* reserved for memory-budget admission */
+    MG_ETIMEOUT = -6    /* reserved for bounded device waits */
+} mg_status;
+
+/* coarsest-grid solver (Section 2) */
+enum { MG_COARSE_DR_PROJ = 0, /* GMRES-DR(m,k) first, then GMRES-Proj(m,k) */
+       MG_COARSE_CGNE = 1     /* CGNE to coarse_tol_rest at every outer iteration */ };
+
+/* arithmetic of the preconditioner; the outer FGMRES is always FP64 */
+enum { MG_FP64 = 0,    /* everything in FP64 */
+       MG_MIXED = 1    /* V-cycle in FP32; deflation space built in FP64 */ };
+
+typedef struct {
+    int levels;            /* grids in the hierarchy: 3 */
+    int block;             /* blocking per direction: 4 (4^2 blocks) */
+    int nvec;              /* near-null vectors per level: 12 */
+    int smooth_steps;      /* GMRES steps of each smoother: 2 */
+    int fgmres_m;          /* outer restart length: 8 */
+    int max_outer;         /* outer iteration limit per right-hand side */
+    int coarse_solver;     /* MG_COARSE_DR_PROJ or MG_COARSE_CGNE */
+    int dr_m, dr_k;        /* GMRES-DR / GMRES-Proj (m, k): 30, 10 */
+    int dr_max_cycles;     /* GMRES-DR cycle limit (100) */
+    int dr_stall_cycles;   /* GMRES-DR ends after this many cycles without progress (2) */
+    int proj_max_cycles;   /* GMRES-Proj cycle limit per solve (1000) */
+    int cgne_max_iters;    /* CGNE iteration limit per solve */
+    int nullvec_max_iters; /* CG iteration limit of each near-null solve */
+    double nullvec_tol;    /* near-null solve tolerance: 1e-4 */
+    double coarse_tol_first; /* GMRES-DR tolerance of the first coarse solve */
+    double coarse_tol_rest;  /* GMRES-Proj / CGNE tolerance: 1e-8 */
+    int precision;         /* MG_FP64 or MG_MIXED */
+    unsigned long long seed; /* start vectors of the near-null solves when none are given */
+} mg_params;
+
+typedef struct {
+    long long mvps[3];       /* operator applications per grid (fine, intermediate, coarse) */
+    double fine_equiv_mvps;  /* Section 3, Eq. 1: fine + (n1/n0) int + (n2/n0) coarse */
+    int outer_iters;         /* FGMRES iterations summed over the right-hand sides */
+    int coarse_solves;       /* coarsest-grid solves */
+    long long coarse_iters;  /* Krylov iterations of all coarsest-grid solves */
+    int dr_solves;           /* coarse solves done by GMRES-DR (builds the deflation space) */
+} mg_solve_stats;
+
+/* Fill *p with the defaults listed beside each field. */
+mg_status mg_default_params(mg_params* p);
+
+/*
+ * Build the three-grid hierarchy of D(m0) on an L_x x L_t lattice (Section 2,
+ * first paragraph): 12 near-null vectors from D D^+ e = -D D^+ x solved by CG to
+ * nullvec_tol with psi = x + e, global orthonormalisation, chiral doubling,
+ * local block x block orthonormalisation into P, D^ = P^+ D P, all repeated on
+ * D^ for the coarsest grid.
+ *   gauge    host or device, complex128[L_t][L_x][2] (copied; not kept)
+ *   L_x, L_t multiples of block^2 (= 16)
+ *   nvec     12 (the only value built); block 4
+ *   p        parameters (NULL = defaults)
+ *   starts0  host or device, complex128[nvec][L_t][L_x][2]: the random x of the
+ *            fine near-null solves; NULL = generated from p->seed
+ *   starts1  host or device, complex128[nvec][L_t/4][L_x/4][24] for the
+ *            intermediate grid; NULL = generated from p->seed
+ *   out      receives the handle; release it with mg_destroy
+ * Errors: MG_EINVAL (shape, parameters, rank-deficient local block),
+ *         MG_ENOMEM, MG_ECUDA.
+ */
+mg_status mg_setup(const void* gauge, int L_x, int L_t, double m0, int nvec, int block,
+                   const mg_params* p, const void* starts0, const void* starts1,
+                   void* stream, mg_handle* out);
+
+/*
+ * Same hierarchy, but from given near-null vectors psi (the result of step 1 of
+ * the set-up) instead of solving for them: used to compare the set-up and the
+ * solve with an independent implementation on identical prolongators.
+ *   nullvecs0 host or device, complex128[nvec][L_t][L_x][2]
+ *   nullvecs1 host or device, complex128[nvec][L_t/4][L_x/4][24]
+ */
+mg_status mg_setup_from_vectors(const void* gauge, int L_x, int L_t, double m0, int nvec, int block,
+                                const mg_params* p, const void* nullvecs0, const void* nullvecs1,
+                                void* stream, mg_handle* out);
+
+/*
+ * Solve D x_i = b_i, i < nrhs, to true relative residual ||b - D x|| / ||b|| <= tol,
+ * recomputed in FP64 (Section 2: FGMRES(8) preconditioned by the V-cycle).
+ *   b        host or device, complex128[nrhs][L_t][L_x][2]
+ *   x        host or device, same shape; output (the initial guess is zero)
+ *   iters    host int[nrhs] or NULL: outer iterations per right-hand side
+ *   relres   host double[nrhs] or NULL: final true relative residuals
+ *   stats    host or NULL: counters summed over this call
+ * The coarse deflation space is built by the first coarse solve of the handle's
+ * first solve and kept for all later outer iterations and right-hand sides.
+ * Returns MG_ENOTCONV when some right-hand side hit max_outer; x then holds the
+ * last iterate and relres its true residual.
+ */
+mg_status mg_solve(mg_handle h, const void* b, void* x, int nrhs, double tol, void* stream,
+                   int* iters, double* relres, mg_solve_stats* stats);
+
+/* Forget the coarse deflation space: the next coarse solve runs GMRES-DR again. */
+mg_status mg_reset_deflation(mg_handle h);
+
+/* Release every device buffer of the handle. NULL is accepted. */
+mg_status mg_destroy(mg_handle h);
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char* mg_last_error(void);
+
+/* ------------------------------------------------------------------------- */
+/* Operator-level entry points (one kernel each), for parity checks and for  */
+/* callers that build their own solvers on the hierarchy.                    */
+/* ------------------------------------------------------------------------- */
+
+/* precision of the operator-level calls: the vectors are complex128 for
+ * MG_F64 and complex64 for MG_F32 */
+enum { MG_F64 = 0, MG_F32 = 1 };
+
+/*
+ * y = D x (dagger = 0) or y = D^+ x = sigma_3 D sigma_3 x (dagger = 1) on one
+ * grid of the hierarchy: level 0 is the Wilson-Dirac operator (Section 2), levels
+ * 1 and 2 the Galerkin stencils D^ = P^+ D P with D^+ = sigma3^ D^ sigma3^.
+ *   x, y  device, complex[n_level] in the precision given (must not alias)
+ */
+mg_status mg_apply(mg_handle h, int level, int dagger, int precision, const void* x, void* y, void* stream);
+
+/* y_c = P^+ y (restriction from `level` to level+1), Section 2. device pointers. */
+mg_status mg_restrict(mg_handle h, int level, int precision, const void* fine, void* coarse, void* stream);
+
+/* y = P y_c (prolongation from level+1 to `level`), Section 2. device pointers. */
+mg_status mg_prolong(mg_handle h, int level, int precision, const void* coarse, void* fine, void* stream);
+
+/*
+ * Copy out the hierarchy (host or device destination, complex128):
+ *   mg_get_stencil: level 1 or 2, complex128[N_t][N_x][5][24][24], directions
+ *     (self, +x, -x, +t, -t), entry [k][l] maps dof l of the neighbour to dof k.
+ *   mg_get_prolongator: level 0 or 1, complex128[B_t][B_x][2][12][16][h],
+ *     h = 1 (level 0) or 12 (level 1); see the layout of P in the set-up.
+ *   mg_get_deflation: W complex128[k+1][n_2] and H complex128[k+1][k]
+ *     (row-major), with D W_k = W H; *k_out = k (0 before the first coarse solve).
+ *     Either pointer may be NULL to query k only.
+ */
+mg_status mg_get_stencil(mg_handle h, int level, void* out);
+mg_status mg_get_prolongator(mg_handle h, int level, void* out);
+mg_status mg_get_deflation(mg_handle h, void* W, void* H, int* k_out);
+
+/* Grid sizes: sites per direction and dofs per site of `level`. */
+mg_status mg_level_shape(mg_handle h, int level, int* n_x, int* n_t, int* dof);
+
+/*
+ * Standalone Wilson-Dirac apply without a hierarchy (Section 2):
+ *   gauge  device, complex128[L_t][L_x][2] (MG_F64) or complex64 (MG_F32)
+ *   x, y   device, complex[L_t][L_x][2]; y = D(m0) x or D^+ x
+ */
+mg_status mg_wilson_apply(const void* gauge, int L_x, int L_t, double m0, int dagger, int precision,
+                          const void* x, void* y, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MG_H */

@@ -168,15 +168,19 @@ def galerkin(A, Q, block=BLOCK):
     lx, lt = x % block, t % block
     cross = {1: lx == block - 1, 2: lx == 0, 3: lt == block - 1, 4: lt == 0}
     for d in range(5):
-        # T[s] = P_s^+ A[s, d] P_nbr(s,d)   -> [Nt, Nx, nc, nc]
+        # left[s] = P_s^+ A[s, d]  (nc x n),  right[s] = P_nbr(s,d)  (n x nc)
         left = np.einsum("tzak,tzab->tzkb", np.conj(Ps), A[:, :, d])
-        T = np.einsum("tzkb,tzbl->tzkl", left, dirac.neighbour(Ps, d, axes=(0, 1)))
+        right = dirac.neighbour(Ps, d, axes=(0, 1))
+        n = right.shape[-2]
+        R = right.reshape(Bt, block, Bx, block, n, nc).transpose(0, 2, 1, 3, 4, 5).reshape(Bt, Bx, -1, nc)
         mask_out = cross[d] if d else np.zeros_like(lx, dtype=bool)
         for dest, m in ((0, ~mask_out), (d, mask_out)):
             if not m.any():
                 continue
-            Tm = T * m[..., None, None]
-            Ac[:, :, dest] += Tm.reshape(Bt, block, Bx, block, nc, nc).sum(axis=(1, 3))
+            # sum over the block's sites s (and the dof index) of P_s^+ A[s, d] P_nbr(s,d)
+            Lm = (left * m[..., None, None]).reshape(Bt, block, Bx, block, nc, n)
+            Lm = Lm.transpose(0, 2, 4, 1, 3, 5).reshape(Bt, Bx, nc, -1)
+            Ac[:, :, dest] += np.matmul(Lm, R)
     return Ac
 
 

@@ -1,0 +1,185 @@
+"""GB300-native deflated multigrid solver for the 2D Schwinger-model Wilson-Dirac
+operator (Whyte, Wilcox, Morgan, arXiv:1912.02868).
+
+The solver is the C ABI of libmg.so (include/mg.h); this package is a thin
+binding with the same names.  Arrays may be torch tensors (CUDA or pinned host)
+or numpy arrays (host); they are passed to the library by pointer.  Complex
+arrays are complex128 (complex64 for the FP32 operator-level calls).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import (MG_COARSE_CGNE, MG_COARSE_DR_PROJ, MG_F32, MG_F64, MG_FP64, MG_MIXED, MG_OK,  # noqa: F401
+                   MG_ENOTCONV, MGError, MGParams, MGSolveStats, load)
+
+__all__ = ["build", "default_params", "mg_setup", "mg_setup_from_vectors", "mg_solve", "mg_destroy",
+           "mg_reset_deflation", "mg_apply", "mg_restrict", "mg_prolong", "mg_get_stencil",
+           "mg_get_prolongator", "mg_get_deflation", "mg_level_shape", "mg_wilson_apply", "Handle"]
+
+
+def build(force: bool = False) -> str:
+    from .build import build as _build
+    return _build(force=force)
+
+
+def _ptr(a):
+    """Data pointer of a torch tensor / numpy array (must be contiguous), or None."""
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    raise TypeError(f"cannot pass {type(a)} as a pointer")
+
+
+def _stream(stream, *arrays):
+    if stream is not None:
+        return stream if isinstance(stream, int) else stream.cuda_stream
+    for a in arrays:
+        if hasattr(a, "is_cuda") and a.is_cuda:
+            import torch
+            return torch.cuda.current_stream(a.device).cuda_stream
+    return None
+
+
+def default_params(**overrides) -> MGParams:
+    p = MGParams()
+    _lib.check(load().mg_default_params(ctypes.byref(p)), "mg_default_params")
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
+class Handle:
+    """Owner of an mg_handle; mg_destroy runs on close() or garbage collection."""
+
+    def __init__(self, ptr: int, Lx: int, Lt: int, params: MGParams):
+        self.ptr = ptr
+        self.Lx, self.Lt = Lx, Lt
+        self.params = params
+
+    def close(self):
+        if self.ptr:
+            load().mg_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def mg_setup(gauge, Lx, Lt, m0, nvec=12, block=4, params=None, starts0=None, starts1=None, stream=None) -> Handle:
+    p = params or default_params()
+    out = ctypes.c_void_p()
+    st = load().mg_setup(_ptr(gauge), Lx, Lt, float(m0), nvec, block, ctypes.byref(p), _ptr(starts0),
+                         _ptr(starts1), _stream(stream, gauge), ctypes.byref(out))
+    _lib.check(st, "mg_setup")
+    return Handle(out.value, Lx, Lt, p)
+
+
+def mg_setup_from_vectors(gauge, Lx, Lt, m0, nullvecs0, nullvecs1, nvec=12, block=4, params=None,
+                          stream=None) -> Handle:
+    p = params or default_params()
+    out = ctypes.c_void_p()
+    st = load().mg_setup_from_vectors(_ptr(gauge), Lx, Lt, float(m0), nvec, block, ctypes.byref(p),
+                                      _ptr(nullvecs0), _ptr(nullvecs1), _stream(stream, gauge), ctypes.byref(out))
+    _lib.check(st, "mg_setup_from_vectors")
+    return Handle(out.value, Lx, Lt, p)
+
+
+def mg_solve(h: Handle, b, x, nrhs, tol, stream=None, allow_notconv=False):
+    """Returns (status, iters[nrhs], relres[nrhs], stats dict)."""
+    iters = (ctypes.c_int * max(nrhs, 1))()
+    relres = (ctypes.c_double * max(nrhs, 1))()
+    stats = MGSolveStats()
+    st = load().mg_solve(h.ptr, _ptr(b), _ptr(x), nrhs, float(tol), _stream(stream, b, x), iters, relres,
+                         ctypes.byref(stats))
+    _lib.check(st, "mg_solve", allow=(MG_OK, MG_ENOTCONV) if allow_notconv else (MG_OK,))
+    sd = {"mvps": list(stats.mvps), "fine_equiv_mvps": stats.fine_equiv_mvps, "outer_iters": stats.outer_iters,
+          "coarse_solves": stats.coarse_solves, "coarse_iters": stats.coarse_iters, "dr_solves": stats.dr_solves}
+    return st, list(iters)[:nrhs], list(relres)[:nrhs], sd
+
+
+def mg_destroy(h: Handle):
+    h.close()
+
+
+def mg_reset_deflation(h: Handle):
+    _lib.check(load().mg_reset_deflation(h.ptr), "mg_reset_deflation")
+
+
+def mg_apply(h: Handle, level, x, y, dagger=False, precision=MG_F64, stream=None):
+    _lib.check(load().mg_apply(h.ptr, level, int(dagger), precision, _ptr(x), _ptr(y), _stream(stream, x)),
+               "mg_apply")
+
+
+def mg_restrict(h: Handle, level, fine, coarse, precision=MG_F64, stream=None):
+    _lib.check(load().mg_restrict(h.ptr, level, precision, _ptr(fine), _ptr(coarse), _stream(stream, fine)),
+               "mg_restrict")
+
+
+def mg_prolong(h: Handle, level, coarse, fine, precision=MG_F64, stream=None):
+    _lib.check(load().mg_prolong(h.ptr, level, precision, _ptr(coarse), _ptr(fine), _stream(stream, coarse)),
+               "mg_prolong")
+
+
+def mg_level_shape(h: Handle, level):
+    nx, nt, dof = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _lib.check(load().mg_level_shape(h.ptr, level, ctypes.byref(nx), ctypes.byref(nt), ctypes.byref(dof)),
+               "mg_level_shape")
+    return nx.value, nt.value, dof.value
+
+
+def mg_get_stencil(h: Handle, level) -> np.ndarray:
+    nx, nt, dof = mg_level_shape(h, level)
+    out = np.empty((nt, nx, 5, dof, dof), dtype=np.complex128)
+    _lib.check(load().mg_get_stencil(h.ptr, level, _ptr(out)), "mg_get_stencil")
+    return out
+
+
+def mg_get_prolongator(h: Handle, level) -> np.ndarray:
+    nxc, ntc, _ = mg_level_shape(h, level + 1)
+    hh = 1 if level == 0 else 12
+    out = np.empty((ntc, nxc, 2, 12, 16, hh), dtype=np.complex128)
+    _lib.check(load().mg_get_prolongator(h.ptr, level, _ptr(out)), "mg_get_prolongator")
+    return out
+
+
+def mg_get_deflation(h: Handle):
+    """(W complex128[k+1][n2], H complex128[k+1][k]) or (None, None) before the first coarse solve."""
+    k = ctypes.c_int()
+    lib = load()
+    _lib.check(lib.mg_get_deflation(h.ptr, None, None, ctypes.byref(k)), "mg_get_deflation")
+    if k.value == 0:
+        return None, None
+    nx, nt, dof = mg_level_shape(h, 2)
+    W = np.empty((k.value + 1, nx * nt * dof), dtype=np.complex128)
+    Hm = np.empty((k.value + 1, k.value), dtype=np.complex128)
+    _lib.check(lib.mg_get_deflation(h.ptr, _ptr(W), _ptr(Hm), ctypes.byref(k)), "mg_get_deflation")
+    return W, Hm
+
+
+def mg_wilson_apply(gauge, Lx, Lt, m0, x, y, dagger=False, precision=MG_F64, stream=None):
+    _lib.check(load().mg_wilson_apply(_ptr(gauge), Lx, Lt, float(m0), int(dagger), precision, _ptr(x), _ptr(y),
+                                      _stream(stream, x)), "mg_wilson_apply")

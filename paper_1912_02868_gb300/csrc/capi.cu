@@ -1,0 +1,527 @@
+// The C ABI declared in include/mg.h: argument checks, buffer management,
+// host/device pointer handling, and error reporting.  No arithmetic of the
+// method is done here; it only calls the kernels and the solver orchestration.
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "handle.cuh"
+
+namespace mg {
+
+static thread_local std::string g_last_error;
+
+void set_error(const char* fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+}
+
+int sm_count() {
+    static int cache[16] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 152;
+    if (dev < 0 || dev >= 16) return 152;
+    if (cache[dev] == 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 152;
+        cache[dev] = v;
+    }
+    return cache[dev];
+}
+
+mg_status halloc(Handle& H, void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        set_error("cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+        (void)cudaGetLastError();
+        return MG_ENOMEM;
+    }
+    H.allocs.push_back(*p);
+    return MG_OK;
+}
+
+template <typename T> mg_status vcycle_entry(Handle& H, const C2<T>* f, C2<T>* x, cudaStream_t s);
+
+namespace {
+
+void free_handle(Handle& H) {
+    for (void* p : H.allocs) cudaFree(p);
+    H.allocs.clear();
+    if (H.pinned) cudaFreeHost(H.pinned);
+    H.pinned = nullptr;
+}
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+mg_status check_params(const mg_params& p) {
+    if (p.levels != 3) return set_error("only 3 grids are built (levels = %d)", p.levels), MG_EINVAL;
+    if (p.block != 4) return set_error("only 4^2 blocking is built (block = %d)", p.block), MG_EINVAL;
+    if (p.nvec != 12) return set_error("only 12 near-null vectors are built (nvec = %d)", p.nvec), MG_EINVAL;
+    if (p.smooth_steps < 1 || p.smooth_steps > 8) return set_error("smooth_steps must be in [1, 8]"), MG_EINVAL;
+    if (p.fgmres_m < 1 || p.fgmres_m > KMAX - 1) return set_error("fgmres_m must be in [1, %d]", KMAX - 1), MG_EINVAL;
+    if (p.dr_m < 2 || p.dr_m > KMAX - 1 || p.dr_m + 1 > RED_MAXD)
+        return set_error("dr_m must be in [2, %d]", KMAX - 1), MG_EINVAL;
+    if (p.dr_k < 1 || p.dr_k >= p.dr_m) return set_error("dr_k must be in [1, dr_m)"), MG_EINVAL;
+    if (p.max_outer < 1 || p.dr_max_cycles < 1 || p.proj_max_cycles < 1 || p.cgne_max_iters < 1 ||
+        p.nullvec_max_iters < 1 || p.dr_stall_cycles < 1)
+        return set_error("iteration limits must be positive"), MG_EINVAL;
+    if (!(p.nullvec_tol > 0.0 && p.nullvec_tol < 1.0) || !(p.coarse_tol_first > 0.0) || !(p.coarse_tol_rest > 0.0))
+        return set_error("tolerances must be in (0, 1)"), MG_EINVAL;
+    if (p.coarse_solver != MG_COARSE_DR_PROJ && p.coarse_solver != MG_COARSE_CGNE)
+        return set_error("unknown coarse_solver %d", p.coarse_solver), MG_EINVAL;
+    if (p.precision != MG_FP64 && p.precision != MG_MIXED)
+        return set_error("unknown precision %d", p.precision), MG_EINVAL;
+    return MG_OK;
+}
+
+template <typename T>
+mg_status alloc_level(Handle& H, Level<T>& L, int steps) {
+    MG_TRY(halloc_t(H, &L.sV, (size_t)(steps + 1) * L.n));
+    MG_TRY(halloc_t(H, &L.x, (size_t)L.n));
+    MG_TRY(halloc_t(H, &L.f, (size_t)L.n));
+    MG_TRY(halloc_t(H, &L.r, (size_t)L.n));
+    MG_TRY(halloc_t(H, &L.ks, 1));
+    return MG_OK;
+}
+
+template <typename T>
+mg_status alloc_coarse(Handle& H, CoarseWS<T>& W, long n, int m, int k) {
+    MG_TRY(halloc_t(H, &W.V, (size_t)(m + 1) * n));
+    MG_TRY(halloc_t(H, &W.V2, (size_t)(m + 1) * n));
+    MG_TRY(halloc_t(H, &W.r, (size_t)n));
+    MG_TRY(halloc_t(H, &W.p, (size_t)n));
+    MG_TRY(halloc_t(H, &W.q, (size_t)n));
+    MG_TRY(halloc_t(H, &W.t, (size_t)n));
+    MG_TRY(halloc_t(H, &W.W, (size_t)(k + 1) * n));
+    MG_TRY(halloc_t(H, &W.ks, 1));
+    return MG_OK;
+}
+
+// Gaussian start vectors (E|z|^2 = 1) from a counter hash of (seed, grid, index)
+void host_gaussian(std::vector<double>& out, size_t ncomplex, unsigned long long seed, int grid) {
+    out.resize(2 * ncomplex);
+    auto mix = [](unsigned long long z) {
+        z += 0x9E3779B97F4A7C15ULL;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+        return z ^ (z >> 31);
+    };
+    const unsigned long long key = mix(seed ^ (0xA5A5ULL + (unsigned long long)grid * 0x1000193ULL));
+    for (size_t i = 0; i < ncomplex; ++i) {
+        const double u1 = ((double)(mix(key ^ mix(2 * i)) >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+        const double u2 = ((double)(mix(key ^ mix(2 * i + 1)) >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+        const double rad = std::sqrt(-std::log(u1));  // |z|^2 ~ Exp(1)
+        out[2 * i] = rad * std::cos(6.283185307179586 * u2);
+        out[2 * i + 1] = rad * std::sin(6.283185307179586 * u2);
+    }
+}
+
+mg_status setup_common(const void* gauge, int Lx, int Lt, double m0, int nvec, int block, const mg_params* pp,
+                       const void* starts0, const void* starts1, const void* nv0, const void* nv1, void* stream,
+                       mg_handle* out) {
+    if (!out) return set_error("out is NULL"), MG_EINVAL;
+    *out = nullptr;
+    if (!gauge) return set_error("gauge is NULL"), MG_EINVAL;
+    mg_params p;
+    mg_default_params(&p);
+    if (pp) p = *pp;
+    if (nvec != p.nvec || block != p.block)
+        return set_error("nvec/block (%d, %d) differ from the parameters (%d, %d)", nvec, block, p.nvec, p.block),
+               MG_EINVAL;
+    MG_TRY(check_params(p));
+    if (Lx < 16 || Lt < 16 || Lx % 16 || Lt % 16)
+        return set_error("lattice %d x %d: both extents must be positive multiples of 16", Lx, Lt), MG_EINVAL;
+    if ((long)Lx * Lt > (1L << 26)) return set_error("lattice too large"), MG_EINVAL;
+    if (!std::isfinite(m0)) return set_error("m0 is not finite"), MG_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    mg_handle_s* hs = new (std::nothrow) mg_handle_s();
+    if (!hs) return set_error("out of host memory"), MG_ENOMEM;
+    Handle& H = hs->h;
+    H.Lx = Lx;
+    H.Lt = Lt;
+    H.m0 = m0;
+    H.p = p;
+    auto fail = [&](mg_status st) {
+        free_handle(H);
+        delete hs;
+        return st;
+    };
+    if (cudaMallocHost(&H.pinned, 1 << 16) != cudaSuccess) {
+        (void)cudaGetLastError();
+        H.pinned = nullptr;
+        set_error("cudaMallocHost failed");
+        return fail(MG_ENOMEM);
+    }
+    // grids
+    const int nx[3] = {Lx, Lx / 4, Lx / 16}, nt[3] = {Lt, Lt / 4, Lt / 16}, dof[3] = {2, 24, 24};
+    for (int l = 0; l < 3; ++l) {
+        H.L64[l].Nx = H.L32[l].Nx = nx[l];
+        H.L64[l].Nt = H.L32[l].Nt = nt[l];
+        H.L64[l].dof = H.L32[l].dof = dof[l];
+        H.L64[l].n = H.L32[l].n = (long)nx[l] * nt[l] * dof[l];
+        H.L64[l].h = H.L32[l].h = dof[l] / 2;
+        H.L64[l].m0 = H.L32[l].m0 = m0;
+    }
+    const long n0 = H.L64[0].n, n2 = H.L64[2].n;
+    mg_status st;
+#define TRYF(e)                     \
+    do {                            \
+        st = (e);                   \
+        if (st != MG_OK) return fail(st); \
+    } while (0)
+    // reductions
+    H.red.max_blocks = 2 * sm_count();
+    TRYF(halloc_t(H, &H.red.partial, (size_t)H.red.max_blocks * RED_MAXD));
+    TRYF(halloc_t(H, &H.red.ticket, 1));
+    TRYF(halloc_t(H, &H.sc, 1));
+    if (cudaMemsetAsync(H.red.ticket, 0, sizeof(unsigned), s) != cudaSuccess ||
+        cudaMemsetAsync(H.sc, 0, sizeof(Scalars), s) != cudaSuccess) {
+        set_error("cudaMemsetAsync failed");
+        return fail(MG_ECUDA);
+    }
+    // hierarchy buffers
+    TRYF(halloc_t(H, &H.U64, (size_t)2 * Lx * Lt));
+    TRYF(halloc_t(H, &H.U32, (size_t)2 * Lx * Lt));
+    for (int l = 1; l < 3; ++l) {
+        TRYF(halloc_t(H, &H.A64[l], (size_t)nx[l] * nt[l] * 5 * 576));
+        TRYF(halloc_t(H, &H.A32[l], (size_t)nx[l] * nt[l] * 5 * 576));
+    }
+    for (int l = 0; l < 2; ++l) {
+        const size_t q = (size_t)nx[l + 1] * nt[l + 1] * 24 * 16 * (dof[l] / 2);
+        TRYF(halloc_t(H, &H.Q64[l], q));
+        TRYF(halloc_t(H, &H.Q32[l], q));
+    }
+    H.L64[0].U = H.U64;
+    H.L32[0].U = H.U32;
+    for (int l = 1; l < 3; ++l) {
+        H.L64[l].A = H.A64[l];
+        H.L32[l].A = H.A32[l];
+    }
+    for (int l = 0; l < 2; ++l) {
+        H.L64[l].Q = H.Q64[l];
+        H.L32[l].Q = H.Q32[l];
+    }
+    for (int l = 0; l < 3; ++l) {
+        TRYF(alloc_level(H, H.L64[l], p.smooth_steps));
+        TRYF(alloc_level(H, H.L32[l], p.smooth_steps));
+    }
+    TRYF(alloc_coarse(H, H.c64, n2, p.dr_m, p.dr_m));
+    TRYF(alloc_coarse(H, H.c32, n2, p.dr_m, p.dr_m));
+    TRYF(halloc_t(H, &H.fV, (size_t)(p.fgmres_m + 1) * n0));
+    TRYF(halloc_t(H, &H.fZ, (size_t)p.fgmres_m * n0));
+    TRYF(halloc_t(H, &H.fx, (size_t)n0));
+    TRYF(halloc_t(H, &H.fr, (size_t)n0));
+    TRYF(halloc_t(H, &H.fb, (size_t)n0));
+    TRYF(halloc_t(H, &H.v32, (size_t)n0));
+    TRYF(halloc_t(H, &H.z32, (size_t)n0));
+    TRYF(halloc_t(H, &H.fks, 1));
+    TRYF(halloc_t(H, &H.cvec, KLD));
+    TRYF(halloc_t(H, &H.dvec, KLD));
+    TRYF(halloc_t(H, &H.uvec, KLD));
+    TRYF(halloc_t(H, &H.dr, 1));
+    TRYF(halloc_t(H, &H.pls, 1));
+    if (cudaMemcpyAsync(H.U64, gauge, sizeof(double2) * 2 * Lx * Lt, cudaMemcpyDefault, s) != cudaSuccess) {
+        set_error("copy of the gauge field failed: %s", cudaGetErrorString(cudaGetLastError()));
+        return fail(MG_ECUDA);
+    }
+    // start vectors of the near-null solves
+    std::vector<double> g0, g1;
+    const long n1 = H.L64[1].n;
+    double2* d_starts[2] = {nullptr, nullptr};
+    if (!nv0 || !nv1) {
+        const void* src[2] = {starts0, starts1};
+        const long nn[2] = {n0, n1};
+        for (int l = 0; l < 2; ++l) {
+            TRYF(halloc_t(H, &d_starts[l], (size_t)p.nvec * nn[l]));
+            if (src[l]) {
+                if (cudaMemcpyAsync(d_starts[l], src[l], sizeof(double2) * p.nvec * nn[l], cudaMemcpyDefault, s) !=
+                    cudaSuccess) {
+                    set_error("copy of start vectors failed");
+                    return fail(MG_ECUDA);
+                }
+            } else {
+                std::vector<double>& g = (l == 0) ? g0 : g1;
+                host_gaussian(g, (size_t)p.nvec * nn[l], p.seed, l);
+                if (cudaMemcpyAsync(d_starts[l], g.data(), sizeof(double) * g.size(), cudaMemcpyHostToDevice, s) !=
+                    cudaSuccess) {
+                    set_error("copy of start vectors failed");
+                    return fail(MG_ECUDA);
+                }
+            }
+        }
+    }
+    const double2* nvd[2] = {nullptr, nullptr};
+    if (nv0 && nv1) {
+        nvd[0] = static_cast<const double2*>(nv0);
+        nvd[1] = static_cast<const double2*>(nv1);
+    }
+    TRYF(build_hierarchy(H, H.U64, d_starts[0], d_starts[1], nvd[0], nvd[1], s));
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+        set_error("set-up failed: %s", cudaGetErrorString(cudaGetLastError()));
+        return fail(MG_ECUDA);
+    }
+#undef TRYF
+    *out = hs;
+    return MG_OK;
+}
+
+}  // namespace
+}  // namespace mg
+
+using namespace mg;
+
+extern "C" {
+
+mg_status mg_default_params(mg_params* p) {
+    if (!p) return set_error("p is NULL"), MG_EINVAL;
+    std::memset(p, 0, sizeof *p);
+    p->levels = 3;
+    p->block = 4;
+    p->nvec = 12;
+    p->smooth_steps = 2;
+    p->fgmres_m = 8;
+    p->max_outer = 500;
+    p->coarse_solver = MG_COARSE_DR_PROJ;
+    p->dr_m = 30;
+    p->dr_k = 10;
+    p->dr_max_cycles = 100;
+    p->dr_stall_cycles = 2;
+    p->proj_max_cycles = 1000;
+    p->cgne_max_iters = 100000;
+    p->nullvec_max_iters = 100000;
+    p->nullvec_tol = 1e-4;
+    p->coarse_tol_first = 1e-14;
+    p->coarse_tol_rest = 1e-8;
+    p->precision = MG_FP64;
+    p->seed = 12345ULL;
+    return MG_OK;
+}
+
+const char* mg_last_error(void) { return g_last_error.c_str(); }
+
+mg_status mg_setup(const void* gauge, int L_x, int L_t, double m0, int nvec, int block, const mg_params* p,
+                   const void* starts0, const void* starts1, void* stream, mg_handle* out) {
+    try {
+        return setup_common(gauge, L_x, L_t, m0, nvec, block, p, starts0, starts1, nullptr, nullptr, stream, out);
+    } catch (const std::bad_alloc&) {
+        set_error("out of host memory");
+        return MG_ENOMEM;
+    }
+}
+
+mg_status mg_setup_from_vectors(const void* gauge, int L_x, int L_t, double m0, int nvec, int block,
+                                const mg_params* p, const void* nullvecs0, const void* nullvecs1, void* stream,
+                                mg_handle* out) {
+    if (!nullvecs0 || !nullvecs1) return set_error("nullvecs0/1 must not be NULL"), MG_EINVAL;
+    try {
+        return setup_common(gauge, L_x, L_t, m0, nvec, block, p, nullptr, nullptr, nullvecs0, nullvecs1, stream,
+                            out);
+    } catch (const std::bad_alloc&) {
+        set_error("out of host memory");
+        return MG_ENOMEM;
+    }
+}
+
+mg_status mg_destroy(mg_handle h) {
+    if (!h) return MG_OK;
+    free_handle(h->h);
+    delete h;
+    return MG_OK;
+}
+
+mg_status mg_reset_deflation(mg_handle h) {
+    if (!h) return set_error("handle is NULL"), MG_EINVAL;
+    h->h.defl_k = 0;
+    return MG_OK;
+}
+
+mg_status mg_solve(mg_handle h, const void* b, void* x, int nrhs, double tol, void* stream, int* iters,
+                   double* relres, mg_solve_stats* stats) {
+    if (!h) return set_error("handle is NULL"), MG_EINVAL;
+    if (!b || !x) return set_error("b or x is NULL"), MG_EINVAL;
+    if (nrhs < 0) return set_error("nrhs < 0"), MG_EINVAL;
+    if (!(tol > 0.0) || !(tol < 1.0)) return set_error("tol must be in (0, 1)"), MG_EINVAL;
+    if (b == x) return set_error("b and x must not alias"), MG_EINVAL;
+    Handle& H = h->h;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    H.st = Stats{};
+    const long n0 = H.L64[0].n;
+    const bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
+    mg_status result = MG_OK;
+    for (int i = 0; i < nrhs; ++i) {
+        const double2* bi = static_cast<const double2*>(b) + (long)i * n0;
+        double2* xi = static_cast<double2*>(x) + (long)i * n0;
+        const double2* bsrc = bi;
+        double2* xdst = xi;
+        if (!bdev) {
+            MG_CUDA_TRY(cudaMemcpyAsync(H.fb, bi, n0 * sizeof(double2), cudaMemcpyHostToDevice, s));
+            bsrc = H.fb;
+        }
+        if (!xdev) xdst = H.fx;
+        int it = 0;
+        double rr = 0.0;
+        bool conv = false;
+        MG_TRY(fgmres_solve(H, bsrc, xdst, tol, s, &it, &rr, &conv));
+        if (!xdev) MG_CUDA_TRY(cudaMemcpyAsync(xi, H.fx, n0 * sizeof(double2), cudaMemcpyDeviceToHost, s));
+        if (iters) iters[i] = it;
+        if (relres) relres[i] = rr;
+        if (!conv) result = MG_ENOTCONV;
+    }
+    MG_CUDA_TRY(cudaStreamSynchronize(s));
+    MG_CUDA_TRY(cudaGetLastError());
+    if (stats) {
+        for (int l = 0; l < 3; ++l) stats->mvps[l] = H.st.mvps[l];
+        const double n1 = (double)H.L64[1].n, n2 = (double)H.L64[2].n, nf = (double)n0;
+        stats->fine_equiv_mvps = H.st.mvps[0] + n1 / nf * H.st.mvps[1] + n2 / nf * H.st.mvps[2];
+        stats->outer_iters = H.st.outer;
+        stats->coarse_solves = H.st.coarse_solves;
+        stats->coarse_iters = H.st.coarse_iters;
+        stats->dr_solves = H.st.dr_solves;
+    }
+    if (result == MG_ENOTCONV) set_error("some right-hand side reached max_outer");
+    return result;
+}
+
+mg_status mg_level_shape(mg_handle h, int level, int* n_x, int* n_t, int* dof) {
+    if (!h || level < 0 || level > 2) return set_error("bad handle or level"), MG_EINVAL;
+    const Level<double>& L = h->h.L64[level];
+    if (n_x) *n_x = L.Nx;
+    if (n_t) *n_t = L.Nt;
+    if (dof) *dof = L.dof;
+    return MG_OK;
+}
+
+mg_status mg_apply(mg_handle h, int level, int dagger, int precision, const void* x, void* y, void* stream) {
+    if (!h || level < 0 || level > 2) return set_error("bad handle or level"), MG_EINVAL;
+    if (!x || !y || x == y) return set_error("x, y must be distinct device pointers"), MG_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (precision == MG_F64)
+        h->h.L64[level].apply(static_cast<double2*>(y), static_cast<const double2*>(x), nullptr, dagger != 0, Gate{}, s);
+    else if (precision == MG_F32)
+        h->h.L32[level].apply(static_cast<float2*>(y), static_cast<const float2*>(x), nullptr, dagger != 0, Gate{}, s);
+    else
+        return set_error("unknown precision"), MG_EINVAL;
+    MG_LAUNCH_CHECK();
+    MG_CUDA_TRY(cudaStreamSynchronize(s));
+    return MG_OK;
+}
+
+mg_status mg_restrict(mg_handle h, int level, int precision, const void* fine, void* coarse, void* stream) {
+    if (!h || level < 0 || level > 1) return set_error("bad handle or level"), MG_EINVAL;
+    if (!fine || !coarse) return set_error("NULL vector"), MG_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Handle& H = h->h;
+    if (precision == MG_F64) {
+        const Level<double>& L = H.L64[level];
+        launch_restrict<double>(static_cast<double2*>(coarse), static_cast<const double2*>(fine), L.Q, L.Nx, L.Nt,
+                                L.h, Gate{}, s);
+    } else if (precision == MG_F32) {
+        const Level<float>& L = H.L32[level];
+        launch_restrict<float>(static_cast<float2*>(coarse), static_cast<const float2*>(fine), L.Q, L.Nx, L.Nt, L.h,
+                               Gate{}, s);
+    } else {
+        return set_error("unknown precision"), MG_EINVAL;
+    }
+    MG_LAUNCH_CHECK();
+    MG_CUDA_TRY(cudaStreamSynchronize(s));
+    return MG_OK;
+}
+
+mg_status mg_prolong(mg_handle h, int level, int precision, const void* coarse, void* fine, void* stream) {
+    if (!h || level < 0 || level > 1) return set_error("bad handle or level"), MG_EINVAL;
+    if (!fine || !coarse) return set_error("NULL vector"), MG_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Handle& H = h->h;
+    if (precision == MG_F64) {
+        const Level<double>& L = H.L64[level];
+        launch_prolong<double>(static_cast<double2*>(fine), static_cast<const double2*>(coarse), L.Q, L.Nx, L.Nt,
+                               L.h, false, Gate{}, s);
+    } else if (precision == MG_F32) {
+        const Level<float>& L = H.L32[level];
+        launch_prolong<float>(static_cast<float2*>(fine), static_cast<const float2*>(coarse), L.Q, L.Nx, L.Nt, L.h,
+                              false, Gate{}, s);
+    } else {
+        return set_error("unknown precision"), MG_EINVAL;
+    }
+    MG_LAUNCH_CHECK();
+    MG_CUDA_TRY(cudaStreamSynchronize(s));
+    return MG_OK;
+}
+
+mg_status mg_get_stencil(mg_handle h, int level, void* out) {
+    if (!h || level < 1 || level > 2 || !out) return set_error("bad handle, level or pointer"), MG_EINVAL;
+    const Handle& H = h->h;
+    const Level<double>& L = H.L64[level];
+    const size_t nblk = (size_t)L.Nx * L.Nt * 5;
+    std::vector<double2> tmp(nblk * 576), tr(nblk * 576);
+    MG_CUDA_TRY(cudaMemcpy(tmp.data(), H.A64[level], tmp.size() * sizeof(double2), cudaMemcpyDeviceToHost));
+    // device blocks are column-major [l][k]; the ABI returns row-major [k][l]
+    for (size_t b = 0; b < nblk; ++b)
+        for (int k = 0; k < 24; ++k)
+            for (int l = 0; l < 24; ++l) tr[b * 576 + k * 24 + l] = tmp[b * 576 + l * 24 + k];
+    MG_CUDA_TRY(cudaMemcpy(out, tr.data(), tr.size() * sizeof(double2), cudaMemcpyDefault));
+    return MG_OK;
+}
+
+mg_status mg_get_prolongator(mg_handle h, int level, void* out) {
+    if (!h || level < 0 || level > 1 || !out) return set_error("bad handle, level or pointer"), MG_EINVAL;
+    const Handle& H = h->h;
+    const size_t q = (size_t)H.L64[level + 1].Nx * H.L64[level + 1].Nt * 24 * 16 * H.L64[level].h;
+    MG_CUDA_TRY(cudaMemcpy(out, H.Q64[level], q * sizeof(double2), cudaMemcpyDefault));
+    return MG_OK;
+}
+
+mg_status mg_get_deflation(mg_handle h, void* W, void* Hm, int* k_out) {
+    if (!h) return set_error("handle is NULL"), MG_EINVAL;
+    const Handle& H = h->h;
+    const int k = H.defl_k;
+    if (k_out) *k_out = k;
+    if (k == 0) return MG_OK;
+    const long n2 = H.L64[2].n;
+    if (W) MG_CUDA_TRY(cudaMemcpy(W, H.c64.W, (size_t)(k + 1) * n2 * sizeof(double2), cudaMemcpyDefault));
+    if (Hm) {
+        std::vector<double2> colmaj((size_t)KLD * KMAX), rowmaj((size_t)(k + 1) * k);
+        MG_CUDA_TRY(cudaMemcpy(colmaj.data(), MG_DEVF(H.pls, double2, H), colmaj.size() * sizeof(double2),
+                               cudaMemcpyDeviceToHost));
+        for (int i = 0; i <= k; ++i)
+            for (int j = 0; j < k; ++j) rowmaj[(size_t)i * k + j] = colmaj[(size_t)i + (size_t)KLD * j];
+        MG_CUDA_TRY(cudaMemcpy(Hm, rowmaj.data(), rowmaj.size() * sizeof(double2), cudaMemcpyDefault));
+    }
+    return MG_OK;
+}
+
+mg_status mg_wilson_apply(const void* gauge, int L_x, int L_t, double m0, int dagger, int precision, const void* x,
+                          void* y, void* stream) {
+    if (!gauge || !x || !y || x == y) return set_error("gauge, x, y must be distinct non-NULL pointers"), MG_EINVAL;
+    if (L_x < 2 || L_t < 2) return set_error("lattice extents must be >= 2"), MG_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (precision == MG_F64)
+        launch_wilson<double>(static_cast<double2*>(y), static_cast<const double2*>(x),
+                              static_cast<const double2*>(gauge), nullptr, m0, L_x, L_t, dagger != 0, Gate{}, s);
+    else if (precision == MG_F32)
+        launch_wilson<float>(static_cast<float2*>(y), static_cast<const float2*>(x), static_cast<const float2*>(gauge),
+                             nullptr, m0, L_x, L_t, dagger != 0, Gate{}, s);
+    else
+        return set_error("unknown precision"), MG_EINVAL;
+    MG_LAUNCH_CHECK();
+    return MG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,127 @@
+// The hierarchy handle: device buffers of all three grids in FP64 and FP32,
+// Krylov workspaces, the coarse deflation space, and host-side counters.
+#pragma once
+#include <vector>
+
+#include "kstate.cuh"
+#include "setup.cuh"
+
+struct mg_handle_s;
+
+namespace mg {
+
+// One grid of the hierarchy in one precision.
+template <typename T>
+struct Level {
+    int Nx = 0, Nt = 0, dof = 0;
+    long n = 0;                   // complex entries of a vector
+    const C2<T>* U = nullptr;     // level 0: gauge field
+    double m0 = 0.0;
+    const C2<T>* A = nullptr;     // levels 1, 2: stencil (column-major blocks)
+    const C2<T>* Q = nullptr;     // prolongator to the next grid (none on the coarsest)
+    int h = 1;                    // dofs per chirality at this grid
+    // workspaces
+    C2<T>* sV = nullptr;          // smoother basis, (smooth_steps + 1) x n
+    C2<T>* x = nullptr;           // cycle output
+    C2<T>* f = nullptr;           // cycle input (levels 1, 2)
+    C2<T>* r = nullptr;           // residual
+    KState* ks = nullptr;         // smoother state
+
+    void apply(C2<T>* y, const C2<T>* xin, const C2<T>* b, bool dagger, Gate g, cudaStream_t s) const {
+        if (U) launch_wilson<T>(y, xin, U, b, m0, Nx, Nt, dagger, g, s);
+        else launch_stencil<T>(y, xin, A, b, Nx, Nt, dof, dagger, g, s);
+    }
+};
+
+// Coarsest-grid Krylov workspace in one precision.
+template <typename T>
+struct CoarseWS {
+    C2<T>* V = nullptr;   // (dr_m + 1) x n2
+    C2<T>* V2 = nullptr;  // restart target, (dr_m + 1) x n2
+    C2<T>* r = nullptr;
+    C2<T>* p = nullptr;   // CG
+    C2<T>* q = nullptr;
+    C2<T>* t = nullptr;
+    C2<T>* W = nullptr;   // deflation space rows (dr_k + 1) x n2
+    KState* ks = nullptr;
+};
+
+struct Scalars {  // device scalars of the host-driven loops
+    double nb2;       // ||b||^2 of the current solve
+    double r2;        // ||r||^2
+    double tmp[8];
+    double rr, pq, rr_new;
+    int cg_active, cg_iters;
+    int err;
+};
+
+struct Stats {
+    long long mvps[3] = {0, 0, 0};
+    int outer = 0;
+    int coarse_solves = 0;
+    long long coarse_iters = 0;
+    int dr_solves = 0;
+};
+
+struct Handle {
+    int Lx = 0, Lt = 0;
+    double m0 = 0.0;
+    mg_params p{};
+    std::vector<void*> allocs;
+    void* pinned = nullptr;       // host staging for status reads
+    RedWS red;
+    Scalars* sc = nullptr;
+    Level<double> L64[3];
+    Level<float> L32[3];
+    // device copies of the set-up in FP64 (owned; the Level views point into them)
+    double2* U64 = nullptr;
+    double2* A64[3] = {nullptr, nullptr, nullptr};
+    double2* Q64[2] = {nullptr, nullptr};
+    float2* U32 = nullptr;
+    float2* A32[3] = {nullptr, nullptr, nullptr};
+    float2* Q32[2] = {nullptr, nullptr};
+    // fine FGMRES (FP64)
+    double2* fV = nullptr;  // (m+1) x n0
+    double2* fZ = nullptr;  // m x n0
+    double2* fx = nullptr;
+    double2* fr = nullptr;
+    double2* fb = nullptr;
+    float2* v32 = nullptr;
+    float2* z32 = nullptr;
+    KState* fks = nullptr;
+    // coarsest grid
+    CoarseWS<double> c64;
+    CoarseWS<float> c32;
+    double2* cvec = nullptr;  // (k+1) Gram coefficients of a projection
+    double2* dvec = nullptr;
+    double2* uvec = nullptr;
+    DRState* dr = nullptr;
+    KState* pls = nullptr;    // factored H_k of the deflation space
+    int defl_k = 0;           // 0: no deflation space yet
+    Stats st;
+
+    template <typename T> Level<T>* levels();
+    template <typename T> CoarseWS<T>& coarse();
+};
+template <> inline Level<double>* Handle::levels<double>() { return L64; }
+template <> inline Level<float>* Handle::levels<float>() { return L32; }
+template <> inline CoarseWS<double>& Handle::coarse<double>() { return c64; }
+template <> inline CoarseWS<float>& Handle::coarse<float>() { return c32; }
+
+// allocation owned by the handle
+mg_status halloc(Handle& H, void** p, size_t bytes);
+template <typename P> mg_status halloc_t(Handle& H, P** p, size_t count) {
+    return halloc(H, reinterpret_cast<void**>(p), count * sizeof(P));
+}
+
+// solve entry points (solver.cu)
+mg_status fgmres_solve(Handle& H, const double2* b, double2* x, double tol, cudaStream_t s, int* iters,
+                       double* relres, bool* converged);
+mg_status build_hierarchy(Handle& H, const double2* gauge_dev, const double2* starts0, const double2* starts1,
+                          const double2* nullvecs0, const double2* nullvecs1, cudaStream_t s);
+
+}  // namespace mg
+
+struct mg_handle_s {
+    mg::Handle h;
+};

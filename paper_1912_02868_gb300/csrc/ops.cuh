@@ -1,0 +1,80 @@
+// Launchers of every kernel of the solve path.  Each kernel file instantiates
+// its templates for T = double and T = float.
+#pragma once
+#include "common.cuh"
+
+namespace mg {
+
+// A kernel with a gate runs only when ptr == nullptr or *ptr == val.  Krylov
+// cycles are enqueued whole; the gates make the steps after convergence no-ops
+// without a host round trip.
+struct Gate {
+    const int* ptr = nullptr;
+    int val = 0;
+};
+__device__ __forceinline__ bool gate_open(const Gate& g) { return g.ptr == nullptr || *g.ptr == g.val; }
+
+// Deterministic reductions: per-block partial sums, the last block to finish
+// adds them in block order.  One workspace per stream.
+constexpr int RED_THREADS = 256;
+constexpr int RED_MAXD = 64;
+struct RedWS {
+    double2* partial = nullptr;  // [max_blocks][RED_MAXD]
+    unsigned* ticket = nullptr;
+    int max_blocks = 0;
+};
+
+// ---------------------------------------------------------------- wilson ----
+// y = D x, D^+ x (dagger), or y = b - D x when b != nullptr.  Section 2.
+template <typename T>
+void launch_wilson(C2<T>* y, const C2<T>* x, const C2<T>* U, const C2<T>* b, double m0, int Lx, int Lt,
+                   bool dagger, Gate g, cudaStream_t s);
+
+// --------------------------------------------------------------- stencil ----
+// y = A x (or sigma3^ A sigma3^ x, or b - A x) for the 5-point block stencil with
+// dof x dof blocks stored column-major: A[s][d][l][k] is entry (k, l).
+template <typename T>
+void launch_stencil(C2<T>* y, const C2<T>* x, const C2<T>* A, const C2<T>* b, int Nx, int Nt, int dof,
+                    bool dagger, Gate g, cudaStream_t s);
+
+// -------------------------------------------------------------- transfer ----
+// Q[B][c][j][l][a]: block B of the finer grid (NxF x NtF sites, 2h dofs per site),
+// chirality c, vector j < 12, site l = lx + 4 lt in the block, dof a < h.
+template <typename T>
+void launch_restrict(C2<T>* coarse, const C2<T>* fine, const C2<T>* Q, int NxF, int NtF, int h, Gate g,
+                     cudaStream_t s);
+template <typename T>
+void launch_prolong(C2<T>* fine, const C2<T>* coarse, const C2<T>* Q, int NxF, int NtF, int h, bool accumulate,
+                    Gate g, cudaStream_t s);
+
+// ------------------------------------------------------------------ blas ----
+// out[i] = sum_e conj(V[i][e]) w[e], i < nd (rows of V have stride ldv)
+template <typename T>
+void launch_gram(double2* out, const C2<T>* V, long ldv, int nd, const C2<T>* w, long n, RedWS ws, Gate g,
+                 cudaStream_t s);
+// w[e] = (zero_first ? 0 : w[e]) + sign * sum_i V[i][e] coef[i], i < count,
+// count = nd_dev ? *nd_dev + nd : nd.  If norm2_out: *norm2_out = ||w||^2 after.
+template <typename T>
+void launch_axpy_multi(C2<T>* w, const C2<T>* V, long ldv, int nd, const int* nd_dev, const double2* coef,
+                       double sign, bool zero_first, long n, double* norm2_out, RedWS ws, Gate g, cudaStream_t s);
+template <typename T>
+void launch_norm2(double* out, const C2<T>* v, long n, RedWS ws, Gate g, cudaStream_t s);
+// y = x * (*factor)
+template <typename T>
+void launch_scale(C2<T>* y, const C2<T>* x, const double* factor, long n, Gate g, cudaStream_t s);
+// y = x (precision change)
+template <typename Ta, typename Tb>
+void launch_convert(C2<Tb>* y, const C2<Ta>* x, long n, Gate g, cudaStream_t s);
+// y = x + a * y  with a = (*num / *den) (CG search direction update), or when
+// den == nullptr, a = *num.
+template <typename T>
+void launch_xpay(C2<T>* y, const C2<T>* x, const double* num, const double* den, long n, Gate g, cudaStream_t s);
+// CG step: e += alpha p, r -= alpha q, alpha = *rr / *pq (real); *rr_new = ||r||^2
+template <typename T>
+void launch_cg_step(C2<T>* e, C2<T>* r, const C2<T>* p, const C2<T>* q, const double* rr, const double* pq,
+                    double* rr_new, long n, RedWS ws, Gate g, cudaStream_t s);
+// *out = Re <x, y>
+template <typename T>
+void launch_redot(double* out, const C2<T>* x, const C2<T>* y, long n, RedWS ws, Gate g, cudaStream_t s);
+
+}  // namespace mg

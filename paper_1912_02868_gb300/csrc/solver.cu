@@ -1,0 +1,489 @@
+// Host orchestration of the solve (Section 2) on one stream:
+//  * Arnoldi steps with CGS2 orthogonalisation, least squares on the device;
+//  * the GMRES(2) smoother, the three-grid V-cycle, the coarsest-grid solvers
+//    (GMRES-DR on the first coarse system, GMRES-Proj afterwards, or CGNE);
+//  * FGMRES(m) outer iterations in FP64 with the true residual recomputed at
+//    every restart;
+//  * the hierarchy set-up (near-null vectors by CG on A A^+, global and local
+//    orthonormalisation, Galerkin operators), built twice for three grids.
+// Every arithmetic step is a kernel; the host only enqueues them and reads a few
+// status words at the end of each Krylov cycle.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <type_traits>
+
+#include "handle.cuh"
+
+namespace mg {
+
+namespace {
+
+struct KHost {
+    int j, j0, step_gate, conv, breakdown, err;
+    double res;
+};
+
+mg_status read_ks(Handle& H, KState* ks, KHost& o, cudaStream_t s) {
+    const size_t off = offsetof(KState, hn2);
+    const size_t len = sizeof(KState) - off;
+    MG_CUDA_TRY(cudaMemcpyAsync(H.pinned, reinterpret_cast<const char*>(ks) + off, len, cudaMemcpyDeviceToHost, s));
+    MG_CUDA_TRY(cudaStreamSynchronize(s));
+    const char* b = static_cast<const char*>(H.pinned) - off;
+    auto geti = [&](size_t o2) {
+        int v;
+        std::memcpy(&v, b + o2, sizeof v);
+        return v;
+    };
+    o.j = geti(offsetof(KState, j));
+    o.j0 = geti(offsetof(KState, j0));
+    o.step_gate = geti(offsetof(KState, step_gate));
+    o.conv = geti(offsetof(KState, conv));
+    o.breakdown = geti(offsetof(KState, breakdown));
+    o.err = geti(offsetof(KState, err));
+    std::memcpy(&o.res, b + offsetof(KState, res), sizeof(double));
+    return MG_OK;
+}
+
+mg_status read_scalars(Handle& H, Scalars& out, cudaStream_t s) {
+    MG_CUDA_TRY(cudaMemcpyAsync(H.pinned, H.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
+    MG_CUDA_TRY(cudaStreamSynchronize(s));
+    std::memcpy(&out, H.pinned, sizeof(Scalars));
+    return MG_OK;
+}
+
+// One Arnoldi step j of a cycle on the rows of V: w = op(input) is written to
+// V[j+1], orthogonalised by CGS2, its column pushed into the least squares,
+// and normalised.  All kernels are gated on the cycle still running.
+template <typename T, typename OpFn>
+void arnoldi_step(Handle& H, OpFn&& op, C2<T>* V, long n, KState* ks, int jh, cudaStream_t s) {
+    const Gate g{MG_DEVF(ks, int, step_gate), jh};
+    C2<T>* w = V + (long)(jh + 1) * n;
+    op(w, g);
+    double2* hA = MG_DEVF(ks, double2, hA);
+    double2* hB = MG_DEVF(ks, double2, hB);
+    launch_gram<T>(hA, V, n, jh + 1, w, n, H.red, g, s);
+    launch_axpy_multi<T>(w, V, n, jh + 1, nullptr, hA, -1.0, false, n, nullptr, H.red, g, s);
+    launch_gram<T>(hB, V, n, jh + 1, w, n, H.red, g, s);
+    launch_axpy_multi<T>(w, V, n, jh + 1, nullptr, hB, -1.0, false, n, MG_DEVF(ks, double, hn2), H.red, g, s);
+    ks_push(ks, jh, s);
+    launch_scale<T>(w, w, MG_DEVF(ks, double, scale), n, Gate{MG_DEVF(ks, int, scale_gate), jh + 1}, s);
+}
+
+// GMRES(steps) from zero on L x = f: x = V d (or x += V d), r_out = V rho.
+template <typename T>
+void smoother(Handle& H, int l, Level<T>& L, const C2<T>* f, C2<T>* x, bool accumulate, C2<T>* r_out,
+              cudaStream_t s) {
+    const long n = L.n;
+    double* t = MG_DEVF(H.sc, double, tmp);
+    KState* ks = L.ks;
+    launch_norm2<T>(t, f, n, H.red, Gate{}, s);
+    ks_start(ks, t, 0.0, t, s);
+    launch_scale<T>(L.sV, f, MG_DEVF(ks, double, scale), n, Gate{MG_DEVF(ks, int, scale_gate), 0}, s);
+    for (int jh = 0; jh < H.p.smooth_steps; ++jh) {
+        const C2<T>* in = L.sV + (long)jh * n;
+        arnoldi_step<T>(H, [&](C2<T>* w, Gate g) { L.apply(w, in, nullptr, false, g, s); }, L.sV, n, ks, jh, s);
+    }
+    ks_finish(ks, s);
+    launch_axpy_multi<T>(x, L.sV, n, 0, MG_DEVF(ks, int, j), MG_DEVF(ks, double2, d), 1.0, !accumulate, n, nullptr,
+                         H.red, Gate{}, s);
+    if (r_out)
+        launch_axpy_multi<T>(r_out, L.sV, n, 1, MG_DEVF(ks, int, j), MG_DEVF(ks, double2, rho), 1.0, true, n,
+                             nullptr, H.red, Gate{}, s);
+    H.st.mvps[l] += H.p.smooth_steps;
+}
+
+// CG on A A^+ y = b from y = 0 (y is zeroed); stops on ||r|| <= tol ||b||.
+template <typename T>
+mg_status cg_normal(Handle& H, int l, Level<T>& L, const C2<T>* b, C2<T>* y, C2<T>* r, C2<T>* p, C2<T>* q,
+                    C2<T>* t, double tol, int maxit, int* iters_out, cudaStream_t s) {
+    const long n = L.n;
+    Scalars* sc = H.sc;
+    double* rr = MG_DEVF(sc, double, rr);
+    double* pq = MG_DEVF(sc, double, pq);
+    double* rr_new = MG_DEVF(sc, double, rr_new);
+    double* nb2 = MG_DEVF(sc, double, nb2);
+    double* r2 = MG_DEVF(sc, double, r2);
+    int* active = MG_DEVF(sc, int, cg_active);
+    int* iters = MG_DEVF(sc, int, cg_iters);
+    MG_CUDA_TRY(cudaMemsetAsync(y, 0, n * sizeof(C2<T>), s));
+    MG_CUDA_TRY(cudaMemcpyAsync(r, b, n * sizeof(C2<T>), cudaMemcpyDeviceToDevice, s));
+    MG_CUDA_TRY(cudaMemcpyAsync(p, b, n * sizeof(C2<T>), cudaMemcpyDeviceToDevice, s));
+    launch_norm2<T>(r2, r, n, H.red, Gate{}, s);
+    cg_init(r2, rr, nb2, tol, active, iters, s);
+    const Gate g{active, 1};
+    int done = 0;
+    Scalars hs{};
+    while (true) {
+        const int batch = 16;
+        for (int it = 0; it < batch; ++it) {
+            L.apply(t, p, nullptr, true, g, s);
+            L.apply(q, t, nullptr, false, g, s);
+            launch_redot<T>(pq, p, q, n, H.red, g, s);
+            launch_cg_step<T>(y, r, p, q, rr, pq, rr_new, n, H.red, g, s);
+            launch_xpay<T>(p, r, rr_new, rr, n, g, s);
+            cg_scalars(rr, rr_new, nb2, tol, active, iters, s);
+        }
+        done += batch;
+        MG_TRY(read_scalars(H, hs, s));
+        if (!hs.cg_active || hs.cg_iters >= maxit) break;
+    }
+    H.st.mvps[l] += 2LL * hs.cg_iters;
+    if (iters_out) *iters_out = hs.cg_iters;
+    (void)done;
+    return MG_OK;
+}
+
+// GMRES-DR(m,k) in FP64 on the coarsest grid from x = 0 (Morgan 2002); keeps the
+// deflation space (V_{k+1}, H_k) of its last cycle in the handle.
+mg_status dr_solve(Handle& H, const double2* f, double2* x, cudaStream_t s) {
+    Level<double>& L = H.L64[2];
+    CoarseWS<double>& W = H.c64;
+    const long n = L.n;
+    const int m = H.p.dr_m, k = H.p.dr_k;
+    double* nb2 = MG_DEVF(H.sc, double, nb2);
+    KState* ks = W.ks;
+    launch_norm2<double>(nb2, f, n, H.red, Gate{}, s);
+    ks_start(ks, nb2, H.p.coarse_tol_first, nb2, s);
+    C2<double>* V = W.V;
+    C2<double>* V2 = W.V2;
+    launch_scale<double>(V, f, MG_DEVF(ks, double, scale), n, Gate{MG_DEVF(ks, int, scale_gate), 0}, s);
+    MG_CUDA_TRY(cudaMemsetAsync(x, 0, n * sizeof(double2), s));
+    int j0 = 0, cycles = 0, stalled = 0;
+    double best = INFINITY;
+    long long iters = 0;
+    while (true) {
+        for (int jh = j0; jh < m; ++jh) {
+            const double2* in = V + (long)jh * n;
+            arnoldi_step<double>(H, [&](double2* w, Gate g) { L.apply(w, in, nullptr, false, g, s); }, V, n, ks, jh,
+                                 s);
+        }
+        ks_finish(ks, s);
+        launch_axpy_multi<double>(x, V, n, 0, MG_DEVF(ks, int, j), MG_DEVF(ks, double2, d), 1.0, false, n, nullptr,
+                                  H.red, Gate{}, s);
+        KHost kh;
+        MG_TRY(read_ks(H, ks, kh, s));
+        if (kh.err) {
+            set_error("GMRES-DR: singular least-squares factor (code %d)", kh.err);
+            return MG_ECUDA;
+        }
+        iters += kh.j - j0;
+        ++cycles;
+        const double res = kh.res;
+        stalled = (res >= best * (1.0 - 1e-3)) ? stalled + 1 : 0;
+        best = std::min(best, res);
+        const bool conv = kh.conv != 0;
+        const bool done = conv || cycles >= H.p.dr_max_cycles || stalled >= H.p.dr_stall_cycles ||
+                          (kh.j < m && !conv);
+        const int jend = kh.j;
+        const int kk = std::min(k, jend - 1);
+        if (kk >= 1) {
+            MG_TRY(dr_restart(ks, H.dr, kk, s));
+            for (int i = 0; i <= kk; ++i)
+                launch_axpy_multi<double>(V2 + (long)i * n, V, n, 1, MG_DEVF(ks, int, j),
+                                          MG_DEVF(H.dr, double2, P) + KLD * i, 1.0, true, n, nullptr, H.red, Gate{},
+                                          s);
+            // reorthogonalise the last basis vector against the first kk
+            double* r2 = MG_DEVF(H.sc, double, r2);
+            double* inv = MG_DEVF(H.sc, double, tmp) + 1;
+            launch_gram<double>(H.cvec, V2, n, kk, V2 + (long)kk * n, n, H.red, Gate{}, s);
+            launch_axpy_multi<double>(V2 + (long)kk * n, V2, n, kk, nullptr, H.cvec, -1.0, false, n, r2, H.red,
+                                      Gate{}, s);
+            scalar_rsqrt(inv, r2, s);
+            launch_scale<double>(V2 + (long)kk * n, V2 + (long)kk * n, inv, n, Gate{}, s);
+        }
+        if (done) {
+            if (kk >= 1) {
+                MG_CUDA_TRY(cudaMemcpyAsync(W.W, V2, (size_t)(kk + 1) * n * sizeof(double2),
+                                            cudaMemcpyDeviceToDevice, s));
+                ks_load_dense(H.pls, MG_DEVF(H.dr, double2, Hk), nullptr, kk, 0.0, s);
+                H.defl_k = kk;
+            } else {
+                // converged in one step: the space is the Arnoldi basis itself
+                MG_CUDA_TRY(cudaMemcpyAsync(W.W, V, (size_t)(jend + 1) * n * sizeof(double2),
+                                            cudaMemcpyDeviceToDevice, s));
+                ks_load_dense(H.pls, MG_DEVF(ks, double2, H), nullptr, jend, 0.0, s);
+                H.defl_k = jend;
+            }
+            H.st.coarse_iters += iters;
+            H.st.mvps[2] += iters;
+            H.st.dr_solves += 1;
+            if (H.defl_k < 1) {
+                set_error("GMRES-DR produced no deflation space");
+                return MG_ECUDA;
+            }
+            return MG_OK;
+        }
+        std::swap(V, V2);
+        ks_load_dense(ks, MG_DEVF(H.dr, double2, Hk), MG_DEVF(H.dr, double2, ck), kk, -1.0, s);
+        j0 = kk;
+    }
+}
+
+// GMRES-Proj(m,k) from x = 0: minimum-residual projection onto the deflation
+// space, then one GMRES(m - k) cycle, repeated (Morgan & Wilcox).
+template <typename T>
+mg_status proj_solve(Handle& H, const C2<T>* f, C2<T>* x, cudaStream_t s) {
+    Level<T>& L = H.levels<T>()[2];
+    CoarseWS<T>& W = H.coarse<T>();
+    const long n = L.n;
+    const int k = H.defl_k;
+    const int ms = std::max(H.p.dr_m - k, 1);
+    double* nb2 = MG_DEVF(H.sc, double, nb2);
+    double* r2 = MG_DEVF(H.sc, double, r2);
+    KState* ks = W.ks;
+    launch_norm2<T>(nb2, f, n, H.red, Gate{}, s);
+    MG_CUDA_TRY(cudaMemsetAsync(x, 0, n * sizeof(C2<T>), s));
+    MG_CUDA_TRY(cudaMemcpyAsync(W.r, f, n * sizeof(C2<T>), cudaMemcpyDeviceToDevice, s));
+    int cycles = 0;
+    long long iters = 0;
+    while (true) {
+        launch_gram<T>(H.cvec, W.W, n, k + 1, W.r, n, H.red, Gate{}, s);
+        proj_solve(H.pls, H.cvec, H.dvec, H.uvec, s);
+        launch_axpy_multi<T>(x, W.W, n, k, nullptr, H.dvec, 1.0, false, n, nullptr, H.red, Gate{}, s);
+        launch_axpy_multi<T>(W.r, W.W, n, k + 1, nullptr, H.uvec, -1.0, false, n, r2, H.red, Gate{}, s);
+        ks_start(ks, r2, H.p.coarse_tol_rest, nb2, s);
+        launch_scale<T>(W.V, W.r, MG_DEVF(ks, double, scale), n, Gate{MG_DEVF(ks, int, scale_gate), 0}, s);
+        for (int jh = 0; jh < ms; ++jh) {
+            const C2<T>* in = W.V + (long)jh * n;
+            arnoldi_step<T>(H, [&](C2<T>* w, Gate g) { L.apply(w, in, nullptr, false, g, s); }, W.V, n, ks, jh, s);
+        }
+        ks_finish(ks, s);
+        launch_axpy_multi<T>(x, W.V, n, 0, MG_DEVF(ks, int, j), MG_DEVF(ks, double2, d), 1.0, false, n, nullptr,
+                             H.red, Gate{}, s);
+        launch_axpy_multi<T>(W.r, W.V, n, 1, MG_DEVF(ks, int, j), MG_DEVF(ks, double2, rho), 1.0, true, n, nullptr,
+                             H.red, Gate{}, s);
+        KHost kh;
+        MG_TRY(read_ks(H, ks, kh, s));
+        iters += kh.j;
+        ++cycles;
+        if (kh.conv || cycles >= H.p.proj_max_cycles) break;
+    }
+    H.st.coarse_iters += iters;
+    H.st.mvps[2] += iters;
+    return MG_OK;
+}
+
+template <typename T>
+mg_status cgne_solve(Handle& H, const C2<T>* f, C2<T>* x, cudaStream_t s) {
+    Level<T>& L = H.levels<T>()[2];
+    CoarseWS<T>& W = H.coarse<T>();
+    int it = 0;
+    MG_TRY(cg_normal<T>(H, 2, L, f, W.V, W.r, W.p, W.q, W.t, H.p.coarse_tol_rest, H.p.cgne_max_iters, &it, s));
+    L.apply(x, W.V, nullptr, true, Gate{}, s);  // x = A^+ y
+    H.st.mvps[2] += 1;
+    H.st.coarse_iters += it;
+    return MG_OK;
+}
+
+template <typename T>
+mg_status coarse_solve(Handle& H, const C2<T>* f, C2<T>* x, cudaStream_t s) {
+    H.st.coarse_solves += 1;
+    if (H.p.coarse_solver == MG_COARSE_CGNE) return cgne_solve<T>(H, f, x, s);
+    if (H.defl_k == 0) {
+        const long n = H.L64[2].n;
+        if constexpr (std::is_same<T, float>::value) {
+            launch_convert<float, double>(H.L64[2].f, f, n, Gate{}, s);
+            MG_TRY(dr_solve(H, H.L64[2].f, H.L64[2].x, s));
+            launch_convert<double, float>(x, H.L64[2].x, n, Gate{}, s);
+        } else {
+            MG_TRY(dr_solve(H, f, x, s));
+        }
+        launch_convert<double, float>(H.c32.W, H.c64.W, (long)(H.defl_k + 1) * n, Gate{}, s);
+        return MG_OK;
+    }
+    return proj_solve<T>(H, f, x, s);
+}
+
+template <typename T>
+mg_status vcycle(Handle& H, int l, const C2<T>* f, C2<T>* x, cudaStream_t s) {
+    Level<T>* Ls = H.levels<T>();
+    Level<T>& L = Ls[l];
+    Level<T>& C = Ls[l + 1];
+    smoother<T>(H, l, L, f, x, false, L.r, s);
+    launch_restrict<T>(C.f, L.r, L.Q, L.Nx, L.Nt, L.h, Gate{}, s);
+    if (l + 1 == 2) MG_TRY(coarse_solve<T>(H, C.f, C.x, s));
+    else MG_TRY(vcycle<T>(H, l + 1, C.f, C.x, s));
+    launch_prolong<T>(x, C.x, L.Q, L.Nx, L.Nt, L.h, true, Gate{}, s);
+    L.apply(L.r, x, f, false, Gate{}, s);  // r = f - A x
+    H.st.mvps[l] += 1;
+    smoother<T>(H, l, L, L.r, x, true, nullptr, s);
+    return MG_OK;
+}
+
+}  // namespace
+
+mg_status fgmres_solve(Handle& H, const double2* b, double2* x, double tol, cudaStream_t s, int* iters,
+                       double* relres, bool* converged) {
+    Level<double>& L0 = H.L64[0];
+    const long n = L0.n;
+    const int m = H.p.fgmres_m;
+    KState* ks = H.fks;
+    double* r2 = MG_DEVF(H.sc, double, r2);
+    double* fnb2 = MG_DEVF(H.sc, double, tmp) + 4;  // ||b||^2 of the outer solve (nb2 is reused inside)
+    launch_norm2<double>(fnb2, b, n, H.red, Gate{}, s);
+    Scalars hs{};
+    MG_TRY(read_scalars(H, hs, s));
+    const double nb = std::sqrt(hs.tmp[4]);
+    MG_CUDA_TRY(cudaMemsetAsync(x, 0, n * sizeof(double2), s));
+    *iters = 0;
+    if (nb == 0.0) {
+        *relres = 0.0;
+        *converged = true;
+        return MG_OK;
+    }
+    MG_CUDA_TRY(cudaMemcpyAsync(H.fr, b, n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+    const bool mixed = H.p.precision == MG_MIXED;
+    int outer = 0;
+    while (true) {
+        launch_norm2<double>(r2, H.fr, n, H.red, Gate{}, s);
+        ks_start(ks, r2, tol, fnb2, s);
+        launch_scale<double>(H.fV, H.fr, MG_DEVF(ks, double, scale), n, Gate{MG_DEVF(ks, int, scale_gate), 0}, s);
+        for (int jh = 0; jh < m && outer < H.p.max_outer; ++jh) {
+            double2* v = H.fV + (long)jh * n;
+            double2* z = H.fZ + (long)jh * n;
+            if (mixed) {
+                launch_convert<double, float>(H.v32, v, n, Gate{}, s);
+                MG_TRY(vcycle<float>(H, 0, H.v32, H.z32, s));
+                launch_convert<float, double>(z, H.z32, n, Gate{}, s);
+            } else {
+                MG_TRY(vcycle<double>(H, 0, v, z, s));
+            }
+            arnoldi_step<double>(H, [&](double2* w, Gate g) { L0.apply(w, z, nullptr, false, g, s); }, H.fV, n, ks,
+                                 jh, s);
+            H.st.mvps[0] += 1;
+            ++outer;
+            KHost kh;
+            MG_TRY(read_ks(H, ks, kh, s));
+            if (kh.step_gate != jh + 1) break;
+        }
+        ks_finish(ks, s);
+        launch_axpy_multi<double>(x, H.fZ, n, 0, MG_DEVF(ks, int, j), MG_DEVF(ks, double2, d), 1.0, false, n,
+                                  nullptr, H.red, Gate{}, s);
+        L0.apply(H.fr, x, b, false, Gate{}, s);  // true residual b - D x (FP64)
+        H.st.mvps[0] += 1;
+        launch_norm2<double>(r2, H.fr, n, H.red, Gate{}, s);
+        MG_TRY(read_scalars(H, hs, s));
+        *relres = std::sqrt(hs.r2) / nb;
+        if (*relres <= tol) {
+            *converged = true;
+            break;
+        }
+        if (outer >= H.p.max_outer) {
+            *converged = false;
+            break;
+        }
+    }
+    *iters = outer;
+    H.st.outer += outer;
+    return MG_OK;
+}
+
+// ---------------------------------------------------------------- set-up ----
+
+namespace {
+
+// modified Gram-Schmidt of the nv rows of V (length n, FP64)
+void global_mgs(Handle& H, double2* V, int nv, long n, cudaStream_t s) {
+    double2* ov = H.cvec;
+    double* r2 = MG_DEVF(H.sc, double, r2);
+    double* inv = MG_DEVF(H.sc, double, tmp) + 2;
+    for (int j = 0; j < nv; ++j) {
+        double2* vj = V + (long)j * n;
+        for (int i = 0; i < j; ++i) {
+            launch_gram<double>(ov, V + (long)i * n, n, 1, vj, n, H.red, Gate{}, s);
+            launch_axpy_multi<double>(vj, V + (long)i * n, n, 1, nullptr, ov, -1.0, false, n, nullptr, H.red, Gate{},
+                                      s);
+        }
+        launch_norm2<double>(r2, vj, n, H.red, Gate{}, s);
+        scalar_rsqrt(inv, r2, s);
+        launch_scale<double>(vj, vj, inv, n, Gate{}, s);
+    }
+}
+
+mg_status nullvectors(Handle& H, int l, double2* NV, int nv, double2* scratch, cudaStream_t s) {
+    Level<double>& L = H.L64[l];
+    const long n = L.n;
+    double2* b = scratch;
+    double2* e = scratch + n;
+    double2* r = scratch + 2 * n;
+    double2* p = scratch + 3 * n;
+    double2* q = scratch + 4 * n;
+    double2* t = scratch + 5 * n;
+    double* m1 = MG_DEVF(H.sc, double, tmp) + 3;
+    double* one = MG_DEVF(H.sc, double, tmp) + 5;
+    scalar_set(m1, -1.0, s);
+    scalar_set(one, 1.0, s);
+    for (int i = 0; i < nv; ++i) {
+        double2* xi = NV + (long)i * n;
+        // b = -A A^+ x
+        L.apply(t, xi, nullptr, true, Gate{}, s);
+        L.apply(b, t, nullptr, false, Gate{}, s);
+        launch_scale<double>(b, b, m1, n, Gate{}, s);
+        int it = 0;
+        MG_TRY(cg_normal<double>(H, l, L, b, e, r, p, q, t, H.p.nullvec_tol, H.p.nullvec_max_iters, &it, s));
+        // psi = x + e
+        launch_xpay<double>(xi, e, one, nullptr, n, Gate{}, s);  // xi = e + 1 * xi
+    }
+    return MG_OK;
+}
+
+}  // namespace
+
+mg_status build_hierarchy(Handle& H, const double2* gauge_dev, const double2* starts0, const double2* starts1,
+                          const double2* nullvecs0, const double2* nullvecs1, cudaStream_t s) {
+    (void)gauge_dev;
+    const int nv = H.p.nvec;
+    Level<double>* L = H.L64;
+    // near-null vectors and prolongator of grid 0 -> 1, Galerkin D^ ; then 1 -> 2
+    double2* NV = nullptr;
+    double2* scratch = nullptr;
+    const long nmax = std::max(L[0].n, L[1].n);
+    MG_TRY(halloc_t(H, &NV, (size_t)nv * nmax));
+    MG_TRY(halloc_t(H, &scratch, (size_t)6 * nmax));
+    int* err = MG_DEVF(H.sc, int, err);
+    for (int l = 0; l < 2; ++l) {
+        const long n = L[l].n;
+        const double2* given = (l == 0) ? nullvecs0 : nullvecs1;
+        const double2* starts = (l == 0) ? starts0 : starts1;
+        if (given) {
+            MG_CUDA_TRY(cudaMemcpyAsync(NV, given, (size_t)nv * n * sizeof(double2), cudaMemcpyDefault, s));
+        } else {
+            MG_CUDA_TRY(cudaMemcpyAsync(NV, starts, (size_t)nv * n * sizeof(double2), cudaMemcpyDefault, s));
+            MG_TRY(nullvectors(H, l, NV, nv, scratch, s));
+        }
+        global_mgs(H, NV, nv, n, s);
+        MG_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
+        launch_local_orth(H.Q64[l], NV, n, L[l].Nx, L[l].Nt, L[l].h, 1e-12, err, s);
+        MG_LAUNCH_CHECK();
+        if (l == 0) launch_galerkin_wilson(H.A64[1], H.U64, H.m0, H.Q64[0], L[0].Nx, L[0].Nt, s);
+        else launch_galerkin_stencil(H.A64[2], H.A64[1], H.Q64[1], L[1].Nx, L[1].Nt, s);
+        MG_LAUNCH_CHECK();
+        Scalars hs{};
+        MG_TRY(read_scalars(H, hs, s));
+        if (hs.err) {
+            set_error("rank-deficient local block in the prolongator of grid %d", l);
+            return MG_EINVAL;
+        }
+    }
+    // FP32 copies of the hierarchy
+    launch_convert<double, float>(H.U32, H.U64, 2L * L[0].Nx * L[0].Nt, Gate{}, s);
+    for (int l = 1; l < 3; ++l)
+        launch_convert<double, float>(H.A32[l], H.A64[l], (long)L[l].Nx * L[l].Nt * 5 * 576, Gate{}, s);
+    for (int l = 0; l < 2; ++l)
+        launch_convert<double, float>(H.Q32[l], H.Q64[l], (long)L[l + 1].Nx * L[l + 1].Nt * 24 * 16 * L[l].h,
+                                      Gate{}, s);
+    MG_LAUNCH_CHECK();
+    MG_CUDA_TRY(cudaStreamSynchronize(s));
+    return MG_OK;
+}
+
+// explicit instantiations used by the C ABI
+template <typename T>
+mg_status vcycle_entry(Handle& H, const C2<T>* f, C2<T>* x, cudaStream_t s) {
+    return vcycle<T>(H, 0, f, x, s);
+}
+template mg_status vcycle_entry<double>(Handle&, const double2*, double2*, cudaStream_t);
+template mg_status vcycle_entry<float>(Handle&, const float2*, float2*, cudaStream_t);
+
+}  // namespace mg
