@@ -194,6 +194,25 @@ mg_status mg_level_shape(mg_handle h, int level, int* n_x, int* n_t, int* dof);
 mg_status mg_wilson_apply(const void* gauge, int L_x, int L_t, double m0, int dagger, int precision,
                           const void* x, void* y, void* stream);
 
+/* ------------------------------------------------------------------------- */
+/* Instrumentation                                                           */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * Time every operator apply on grid `level` of the handle with CUDA events on
+ * the stream the apply runs on (enable = 1), or stop (enable = 0).  Enabling
+ * resets the totals.  mg_timing_read waits for the last recorded event and
+ * returns the summed apply time in milliseconds and the number of applies.
+ * Meant for roofline reports; the events add a few microseconds of host work
+ * per apply.  Not meaningful on the coarsest grid, whose applies may be
+ * skipped on the device after a Krylov cycle has converged.
+ */
+mg_status mg_timing_enable(mg_handle h, int level, int enable);
+mg_status mg_timing_read(mg_handle h, int level, double* total_ms, long long* launches);
+
+/* Number of kernels this library has launched in this process so far. */
+unsigned long long mg_kernel_launches(void);
+
 #ifdef __cplusplus
 }
 #endif

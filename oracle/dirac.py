@@ -116,11 +116,17 @@ def neighbour(v, d, axes=(-3, -2)):
 
 
 def stencil_apply(A, v):
-    """(A v)(s) = sum_d A[s, d] v(nbr(s, d)); v complex[..., N_t, N_x, n]."""
-    out = np.zeros(np.broadcast_shapes(v.shape, A.shape[:2] + (A.shape[-2],)), dtype=np.complex128)
+    """(A v)(s) = sum_d A[s, d] v(nbr(s, d)); v complex[..., N_t, N_x, n].
+
+    Each term is a batch of per-site matrix-vector products (numpy matmul)."""
+    Nt, Nx, _, n, _ = A.shape
+    lead = v.shape[:-3]
+    nb_ = int(np.prod(lead)) if lead else 1
+    out = np.zeros((Nt * Nx, n, nb_), dtype=np.complex128)
     for d in range(5):
-        out = out + np.einsum("tzkl,...tzl->...tzk", A[:, :, d], neighbour(v, d))
-    return out
+        x = neighbour(v, d).reshape(nb_, Nt * Nx, n).transpose(1, 2, 0)  # [site][l][batch]
+        out = out + np.matmul(A[:, :, d].reshape(Nt * Nx, n, n), x)
+    return out.transpose(2, 0, 1).reshape(lead + (Nt, Nx, n))
 
 
 def stencil_dagger_sigma(A, v):

@@ -30,14 +30,21 @@ from . import dirac
 TARGET = 1e-3
 
 
+def _near(A, sigma, k, tol):
+    """k eigenvalues of A nearest sigma: Arnoldi on (A - sigma)^{-1} with a sparse LU."""
+    import scipy.sparse as sp
+    lu = spla.splu((A - sigma * sp.identity(A.shape[0], dtype=A.dtype, format="csc")).tocsc())
+    op = spla.LinearOperator(A.shape, matvec=lu.solve, dtype=np.complex128)
+    mu = spla.eigs(op, k=k, which="LM", return_eigenvectors=False, tol=tol, ncv=max(40, 3 * k))
+    return sigma + 1.0 / mu
+
+
 def leftmost_eigs(U, k=12):
     A = dirac.stencil_sparse(dirac.wilson_stencil(U, 0.0)).tocsc()
-    vals = None
-    for sigma in (0.0, None):
-        if sigma is None:
-            sigma = float(np.min(vals.real)) - 0.02
-        vals = spla.eigs(A, k=k, sigma=sigma, which="LM", return_eigenvectors=False, tol=1e-12)
-    return vals
+    # rough pass around 0, then an accurate pass just left of the smallest real part found
+    vals = _near(A, 0.0, 6, 1e-6)
+    sigma = float(np.min(vals.real)) - 0.005
+    return _near(A, sigma, k, 1e-12)
 
 
 def tune(L, config):

@@ -18,11 +18,12 @@ from ._lib import (MG_COARSE_CGNE, MG_COARSE_DR_PROJ, MG_F32, MG_F64, MG_FP64, M
 
 __all__ = ["build", "default_params", "mg_setup", "mg_setup_from_vectors", "mg_solve", "mg_destroy",
            "mg_reset_deflation", "mg_apply", "mg_restrict", "mg_prolong", "mg_get_stencil",
-           "mg_get_prolongator", "mg_get_deflation", "mg_level_shape", "mg_wilson_apply", "Handle"]
+           "mg_get_prolongator", "mg_get_deflation", "mg_level_shape", "mg_wilson_apply", "mg_timing_enable",
+           "mg_timing_read", "mg_kernel_launches", "Handle"]
 
 
 def build(force: bool = False) -> str:
-    from .build import build as _build
+    from .nvcc_build import build as _build
     return _build(force=force)
 
 
@@ -183,3 +184,18 @@ def mg_get_deflation(h: Handle):
 def mg_wilson_apply(gauge, Lx, Lt, m0, x, y, dagger=False, precision=MG_F64, stream=None):
     _lib.check(load().mg_wilson_apply(_ptr(gauge), Lx, Lt, float(m0), int(dagger), precision, _ptr(x), _ptr(y),
                                       _stream(stream, x)), "mg_wilson_apply")
+
+
+def mg_timing_enable(h: Handle, level, enable=True):
+    _lib.check(load().mg_timing_enable(h.ptr, level, int(enable)), "mg_timing_enable")
+
+
+def mg_timing_read(h: Handle, level):
+    """(total milliseconds, number of applies) of the timed applies on `level`."""
+    ms, n = ctypes.c_double(), ctypes.c_longlong()
+    _lib.check(load().mg_timing_read(h.ptr, level, ctypes.byref(ms), ctypes.byref(n)), "mg_timing_read")
+    return ms.value, n.value
+
+
+def mg_kernel_launches() -> int:
+    return int(load().mg_kernel_launches())

@@ -44,7 +44,8 @@ _lib = None
 # every symbol declared in include/mg.h
 SYMBOLS = ("mg_default_params", "mg_setup", "mg_setup_from_vectors", "mg_solve", "mg_reset_deflation",
            "mg_destroy", "mg_last_error", "mg_apply", "mg_restrict", "mg_prolong", "mg_get_stencil",
-           "mg_get_prolongator", "mg_get_deflation", "mg_level_shape", "mg_wilson_apply")
+           "mg_get_prolongator", "mg_get_deflation", "mg_level_shape", "mg_wilson_apply",
+           "mg_timing_enable", "mg_timing_read", "mg_kernel_launches")
 
 
 def load(path: str | None = None) -> ctypes.CDLL:
@@ -54,7 +55,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         return _lib
     p = path or LIB_PATH
     if not os.path.exists(p):
-        raise ImportError(f"{p} is missing: build it with paper_1912_02868_gb300.build.build()")
+        raise ImportError(f"{p} is missing: build it with paper_1912_02868_gb300.build()")
     lib = ctypes.CDLL(p)
     vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
     sig = {
@@ -73,6 +74,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "mg_get_deflation": (i, [vp, vp, vp, ctypes.POINTER(i)]),
         "mg_level_shape": (i, [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]),
         "mg_wilson_apply": (i, [vp, i, i, d, i, i, vp, vp, vp]),
+        "mg_timing_enable": (i, [vp, i, i]),
+        "mg_timing_read": (i, [vp, i, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong)]),
+        "mg_kernel_launches": (ctypes.c_ulonglong, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

@@ -255,6 +255,7 @@ void launch_gram(double2* out, const C2<T>* V, long ldv, int nd, const C2<T>* w,
                  cudaStream_t s) {
     if (nd <= 0) return;
     k_gram<T><<<red_blocks(n, ws), RED_THREADS, 0, s>>>(out, V, ldv, nd, w, n, ws.partial, ws.ticket, g);
+    count_launch();
 }
 
 template <typename T>
@@ -262,37 +263,44 @@ void launch_axpy_multi(C2<T>* w, const C2<T>* V, long ldv, int nd, const int* nd
                        double sign, bool zero_first, long n, double* norm2_out, RedWS ws, Gate g, cudaStream_t s) {
     k_axpy_multi<T><<<red_blocks(n, ws), RED_THREADS, 0, s>>>(w, V, ldv, nd, nd_dev, coef, sign, zero_first ? 1 : 0,
                                                               n, norm2_out, ws.partial, ws.ticket, g);
+    count_launch();
 }
 
 template <typename T>
 void launch_norm2(double* out, const C2<T>* v, long n, RedWS ws, Gate g, cudaStream_t s) {
     k_norm2<T><<<red_blocks(n, ws), RED_THREADS, 0, s>>>(out, v, n, ws.partial, ws.ticket, g);
+    count_launch();
 }
 
 template <typename T>
 void launch_redot(double* out, const C2<T>* x, const C2<T>* y, long n, RedWS ws, Gate g, cudaStream_t s) {
     k_redot<T><<<red_blocks(n, ws), RED_THREADS, 0, s>>>(out, x, y, n, ws.partial, ws.ticket, g);
+    count_launch();
 }
 
 template <typename T>
 void launch_scale(C2<T>* y, const C2<T>* x, const double* factor, long n, Gate g, cudaStream_t s) {
     k_scale<T><<<ew_blocks(n), 256, 0, s>>>(y, x, factor, n, g);
+    count_launch();
 }
 
 template <typename Ta, typename Tb>
 void launch_convert(C2<Tb>* y, const C2<Ta>* x, long n, Gate g, cudaStream_t s) {
     k_convert<Ta, Tb><<<ew_blocks(n), 256, 0, s>>>(y, x, n, g);
+    count_launch();
 }
 
 template <typename T>
 void launch_xpay(C2<T>* y, const C2<T>* x, const double* num, const double* den, long n, Gate g, cudaStream_t s) {
     k_xpay<T><<<ew_blocks(n), 256, 0, s>>>(y, x, num, den, n, g);
+    count_launch();
 }
 
 template <typename T>
 void launch_cg_step(C2<T>* e, C2<T>* r, const C2<T>* p, const C2<T>* q, const double* rr, const double* pq,
                     double* rr_new, long n, RedWS ws, Gate g, cudaStream_t s) {
     k_cg_step<T><<<red_blocks(n, ws), RED_THREADS, 0, s>>>(e, r, p, q, rr, pq, rr_new, n, ws.partial, ws.ticket, g);
+    count_launch();
 }
 
 #define INST(T)                                                                                                  \

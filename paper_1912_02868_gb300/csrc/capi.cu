@@ -13,6 +13,7 @@
 namespace mg {
 
 static thread_local std::string g_last_error;
+std::atomic<unsigned long long> g_launches{0};
 
 void set_error(const char* fmt, ...) {
     char buf[1024];
@@ -55,6 +56,10 @@ template <typename T> mg_status vcycle_entry(Handle& H, const C2<T>* f, C2<T>* x
 namespace {
 
 void free_handle(Handle& H) {
+    for (auto& t : H.timers) {
+        for (cudaEvent_t e : t.ev) cudaEventDestroy(e);
+        t.ev.clear();
+    }
     for (void* p : H.allocs) cudaFree(p);
     H.allocs.clear();
     if (H.pinned) cudaFreeHost(H.pinned);
@@ -178,6 +183,7 @@ mg_status setup_common(const void* gauge, int Lx, int Lt, double m0, int nvec, i
         H.L64[l].n = H.L32[l].n = (long)nx[l] * nt[l] * dof[l];
         H.L64[l].h = H.L32[l].h = dof[l] / 2;
         H.L64[l].m0 = H.L32[l].m0 = m0;
+        H.L64[l].timer = H.L32[l].timer = &H.timers[l];
     }
     const long n0 = H.L64[0].n, n2 = H.L64[2].n;
     mg_status st;
@@ -237,6 +243,9 @@ mg_status setup_common(const void* gauge, int Lx, int Lt, double m0, int nvec, i
     TRYF(halloc_t(H, &H.uvec, KLD));
     TRYF(halloc_t(H, &H.dr, 1));
     TRYF(halloc_t(H, &H.pls, 1));
+    H.cpart_ctas = sm_count();
+    TRYF(halloc_t(H, &H.cpart, (size_t)2 * H.cpart_ctas * PSTR));
+    TRYF(halloc_t(H, &H.cstats, 1));
     if (cudaMemcpyAsync(H.U64, gauge, sizeof(double2) * 2 * Lx * Lt, cudaMemcpyDefault, s) != cudaSuccess) {
         set_error("copy of the gauge field failed: %s", cudaGetErrorString(cudaGetLastError()));
         return fail(MG_ECUDA);
@@ -364,6 +373,7 @@ mg_status mg_solve(mg_handle h, const void* b, void* x, int nrhs, double tol, vo
     H.st = Stats{};
     const long n0 = H.L64[0].n;
     const bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
+    MG_CUDA_TRY(cudaMemsetAsync(H.cstats, 0, sizeof(CoopStats), s));
     mg_status result = MG_OK;
     for (int i = 0; i < nrhs; ++i) {
         const double2* bi = static_cast<const double2*>(b) + (long)i * n0;
@@ -384,8 +394,13 @@ mg_status mg_solve(mg_handle h, const void* b, void* x, int nrhs, double tol, vo
         if (relres) relres[i] = rr;
         if (!conv) result = MG_ENOTCONV;
     }
+    CoopStats cs{};
+    MG_CUDA_TRY(cudaMemcpyAsync(H.pinned, H.cstats, sizeof(CoopStats), cudaMemcpyDeviceToHost, s));
     MG_CUDA_TRY(cudaStreamSynchronize(s));
     MG_CUDA_TRY(cudaGetLastError());
+    std::memcpy(&cs, H.pinned, sizeof cs);
+    H.st.coarse_iters += cs.iters;
+    H.st.mvps[2] += cs.iters;
     if (stats) {
         for (int l = 0; l < 3; ++l) stats->mvps[l] = H.st.mvps[l];
         const double n1 = (double)H.L64[1].n, n2 = (double)H.L64[2].n, nf = (double)n0;
@@ -506,6 +521,31 @@ mg_status mg_get_deflation(mg_handle h, void* W, void* Hm, int* k_out) {
     }
     return MG_OK;
 }
+
+mg_status mg_timing_enable(mg_handle h, int level, int enable) {
+    if (!h || level < 0 || level > 2) return set_error("bad handle or level"), MG_EINVAL;
+    ApplyTimer& t = h->h.timers[level];
+    t.on = enable != 0;
+    t.used = 0;
+    return MG_OK;
+}
+
+mg_status mg_timing_read(mg_handle h, int level, double* total_ms, long long* launches) {
+    if (!h || level < 0 || level > 2) return set_error("bad handle or level"), MG_EINVAL;
+    ApplyTimer& t = h->h.timers[level];
+    double ms = 0.0;
+    if (t.used >= 2) MG_CUDA_TRY(cudaEventSynchronize(t.ev[t.used - 1]));
+    for (size_t i = 0; i + 1 < t.used; i += 2) {
+        float v = 0.f;
+        MG_CUDA_TRY(cudaEventElapsedTime(&v, t.ev[i], t.ev[i + 1]));
+        ms += v;
+    }
+    if (total_ms) *total_ms = ms;
+    if (launches) *launches = (long long)(t.used / 2);
+    return MG_OK;
+}
+
+unsigned long long mg_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 mg_status mg_wilson_apply(const void* gauge, int L_x, int L_t, double m0, int dagger, int precision, const void* x,
                           void* y, void* stream) {

@@ -1,0 +1,37 @@
+// Cooperative persistent kernel of the coarsest-grid GMRES-Proj solve.
+#pragma once
+#include "kstate.cuh"
+
+namespace mg {
+
+constexpr int MSMAX = 40;  // longest GMRES cycle of a projected solve (m - k)
+constexpr int PSTR = 64;   // stride of one CTA's partial sums
+
+// device-side counters of the projected coarse solves
+struct CoopStats {
+    long long iters, cycles, solves, unconverged;
+};
+
+template <typename T>
+struct CoopArgs {
+    const C2<T>* A;    // coarse stencil, column-major 24x24 blocks
+    int Nx, Nt;        // coarse grid
+    const C2<T>* f;    // right-hand side
+    C2<T>* x;          // solution (output, initial guess zero)
+    C2<T>* r;          // residual workspace
+    C2<T>* V;          // Krylov basis, (ms + 1) rows of n
+    const C2<T>* W;    // deflation space V_{k+1}, (k + 1) rows of n
+    const KState* pls; // H_k and its QR factorisation
+    int k, ms;         // deflation size, GMRES cycle length
+    double tol;        // stop when ||r|| <= tol ||f||
+    int max_cycles;
+    double2* part;     // partial sums: 2 x part_ctas x PSTR
+    int part_ctas;
+    CoopStats* out;
+    int spc;           // sites per CTA (set by the launcher)
+};
+
+template <typename T>
+mg_status launch_coarse_proj(const CoopArgs<T>& a, cudaStream_t s);
+
+}  // namespace mg

@@ -2,6 +2,7 @@
 // interleaved (re, im) pairs, error reporting, launch geometry.
 #pragma once
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstdint>
 #include <cstdio>
 #include <string>
@@ -94,5 +95,9 @@ inline unsigned nblocks(long n, int threads) { return (unsigned)((n + threads - 
 
 // number of SMs of the current device (cached per process for device 0..15)
 int sm_count();
+
+// process-wide count of kernel launches made by this library
+extern std::atomic<unsigned long long> g_launches;
+inline void count_launch(unsigned long long n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 }  // namespace mg

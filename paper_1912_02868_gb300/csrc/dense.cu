@@ -621,24 +621,41 @@ __global__ void __launch_bounds__(DR_THREADS) k_dr_restart(const KState* __restr
 
 void ks_start(KState* ks, const double* nrm2, double tol_rel, const double* nb2, cudaStream_t s) {
     k_ks_start<<<1, 32, 0, s>>>(ks, nrm2, tol_rel, nb2);
+    count_launch();
 }
-void scalar_set(double* out, double v, cudaStream_t s) { k_set<<<1, 32, 0, s>>>(out, v); }
+void scalar_set(double* out, double v, cudaStream_t s) {
+    k_set<<<1, 32, 0, s>>>(out, v);
+    count_launch();
+}
 void cg_init(const double* r2, double* rr, double* nb2, double tol, int* active, int* iters, cudaStream_t s) {
     k_cg_init<<<1, 32, 0, s>>>(r2, rr, nb2, tol, active, iters);
+    count_launch();
 }
 void cg_scalars(double* rr, const double* rr_new, const double* nb2, double tol, int* active, int* iters,
                 cudaStream_t s) {
     k_cg_scalars<<<1, 32, 0, s>>>(rr, rr_new, nb2, tol, active, iters);
+    count_launch();
 }
-void ks_push(KState* ks, int jh, cudaStream_t s) { k_ks_push<<<1, 32, 0, s>>>(ks, jh); }
-void ks_finish(KState* ks, cudaStream_t s) { k_ks_finish<<<1, 32, 0, s>>>(ks); }
+void ks_push(KState* ks, int jh, cudaStream_t s) {
+    k_ks_push<<<1, 32, 0, s>>>(ks, jh);
+    count_launch();
+}
+void ks_finish(KState* ks, cudaStream_t s) {
+    k_ks_finish<<<1, 32, 0, s>>>(ks);
+    count_launch();
+}
 void ks_load_dense(KState* ks, const double2* Hk, const double2* ck, int k, double tol_abs, cudaStream_t s) {
     k_ks_load_dense<<<1, 32, 0, s>>>(ks, Hk, ck, k, tol_abs);
+    count_launch();
 }
 void proj_solve(const KState* pls, const double2* cvec, double2* d, double2* u, cudaStream_t s) {
     k_proj_solve<<<1, 32, 0, s>>>(pls, cvec, d, u);
+    count_launch();
 }
-void scalar_rsqrt(double* out, const double* in, cudaStream_t s) { k_rsqrt<<<1, 32, 0, s>>>(out, in); }
+void scalar_rsqrt(double* out, const double* in, cudaStream_t s) {
+    k_rsqrt<<<1, 32, 0, s>>>(out, in);
+    count_launch();
+}
 
 mg_status dr_restart(const KState* ks, DRState* dr, int k, cudaStream_t s) {
     static int configured = -1;
@@ -650,6 +667,7 @@ mg_status dr_restart(const KState* ks, DRState* dr, int k, cudaStream_t s) {
         configured = dev;
     }
     k_dr_restart<<<1, DR_THREADS, sizeof(DRSmem), s>>>(ks, dr, k);
+    count_launch();
     MG_LAUNCH_CHECK();
     return MG_OK;
 }

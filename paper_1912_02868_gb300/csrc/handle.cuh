@@ -3,12 +3,28 @@
 #pragma once
 #include <vector>
 
+#include "coarse_coop.cuh"
 #include "kstate.cuh"
 #include "setup.cuh"
 
 struct mg_handle_s;
 
 namespace mg {
+
+// CUDA-event timing of every operator apply on one grid (for roofline reports).
+struct ApplyTimer {
+    bool on = false;
+    std::vector<cudaEvent_t> ev;  // start/stop pairs, reused
+    size_t used = 0;
+    cudaEvent_t next() {
+        if (used == ev.size()) {
+            cudaEvent_t e = nullptr;
+            if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+            ev.push_back(e);
+        }
+        return ev[used++];
+    }
+};
 
 // One grid of the hierarchy in one precision.
 template <typename T>
@@ -26,10 +42,18 @@ struct Level {
     C2<T>* f = nullptr;           // cycle input (levels 1, 2)
     C2<T>* r = nullptr;           // residual
     KState* ks = nullptr;         // smoother state
+    ApplyTimer* timer = nullptr;  // shared by both precisions of the grid
 
     void apply(C2<T>* y, const C2<T>* xin, const C2<T>* b, bool dagger, Gate g, cudaStream_t s) const {
+        cudaEvent_t e1 = nullptr;
+        if (timer && timer->on) {
+            cudaEvent_t e0 = timer->next();
+            e1 = timer->next();
+            if (e0) cudaEventRecord(e0, s);
+        }
         if (U) launch_wilson<T>(y, xin, U, b, m0, Nx, Nt, dagger, g, s);
         else launch_stencil<T>(y, xin, A, b, Nx, Nt, dof, dagger, g, s);
+        if (e1) cudaEventRecord(e1, s);
     }
 };
 
@@ -97,8 +121,12 @@ struct Handle {
     double2* uvec = nullptr;
     DRState* dr = nullptr;
     KState* pls = nullptr;    // factored H_k of the deflation space
+    double2* cpart = nullptr; // partial sums of the cooperative coarse solve
+    int cpart_ctas = 0;
+    CoopStats* cstats = nullptr;
     int defl_k = 0;           // 0: no deflation space yet
     Stats st;
+    ApplyTimer timers[3];
 
     template <typename T> Level<T>* levels();
     template <typename T> CoarseWS<T>& coarse();

@@ -167,6 +167,7 @@ void launch_local_orth(double2* Q, const double2* V, long ldv, int NxF, int NtF,
                        cudaStream_t s) {
     const int nc = (NxF / BL) * (NtF / BL);
     k_local_orth<<<2 * nc, LO_THREADS, 0, s>>>(Q, V, ldv, NxF, h, rank_tol, err);
+    count_launch();
 }
 
 void launch_galerkin_wilson(double2* Ac, const double2* U, double m0, const double2* Q, int Lx, int Lt,
@@ -174,12 +175,14 @@ void launch_galerkin_wilson(double2* Ac, const double2* U, double m0, const doub
     const int nc = (Lx / BL) * (Lt / BL);
     FinerWilson f{U, m0 + 2.0, Lx, Lt};
     k_galerkin<FinerWilson><<<nc, 576, 0, s>>>(Ac, f, Q, Lx, Lt, 1);
+    count_launch();
 }
 
 void launch_galerkin_stencil(double2* Ac, const double2* A, const double2* Q, int NxF, int NtF, cudaStream_t s) {
     const int nc = (NxF / BL) * (NtF / BL);
     FinerStencil f{A};
     k_galerkin<FinerStencil><<<nc, 576, 0, s>>>(Ac, f, Q, NxF, NtF, 12);
+    count_launch();
 }
 
 }  // namespace mg

@@ -222,46 +222,32 @@ mg_status dr_solve(Handle& H, const double2* f, double2* x, cudaStream_t s) {
 
 // GMRES-Proj(m,k) from x = 0: minimum-residual projection onto the deflation
 // space, then one GMRES(m - k) cycle, repeated (Morgan & Wilcox).
+// GMRES-Proj(m,k) from x = 0: minimum-residual projection onto the deflation
+// space, then one GMRES(m - k) cycle, repeated (Morgan & Wilcox).  The whole
+// solve is one cooperative kernel (coarse_coop.cu); its iteration counts are
+// accumulated on the device and read once per mg_solve.
 template <typename T>
 mg_status proj_solve(Handle& H, const C2<T>* f, C2<T>* x, cudaStream_t s) {
     Level<T>& L = H.levels<T>()[2];
     CoarseWS<T>& W = H.coarse<T>();
-    const long n = L.n;
-    const int k = H.defl_k;
-    const int ms = std::max(H.p.dr_m - k, 1);
-    double* nb2 = MG_DEVF(H.sc, double, nb2);
-    double* r2 = MG_DEVF(H.sc, double, r2);
-    KState* ks = W.ks;
-    launch_norm2<T>(nb2, f, n, H.red, Gate{}, s);
-    MG_CUDA_TRY(cudaMemsetAsync(x, 0, n * sizeof(C2<T>), s));
-    MG_CUDA_TRY(cudaMemcpyAsync(W.r, f, n * sizeof(C2<T>), cudaMemcpyDeviceToDevice, s));
-    int cycles = 0;
-    long long iters = 0;
-    while (true) {
-        launch_gram<T>(H.cvec, W.W, n, k + 1, W.r, n, H.red, Gate{}, s);
-        proj_solve(H.pls, H.cvec, H.dvec, H.uvec, s);
-        launch_axpy_multi<T>(x, W.W, n, k, nullptr, H.dvec, 1.0, false, n, nullptr, H.red, Gate{}, s);
-        launch_axpy_multi<T>(W.r, W.W, n, k + 1, nullptr, H.uvec, -1.0, false, n, r2, H.red, Gate{}, s);
-        ks_start(ks, r2, H.p.coarse_tol_rest, nb2, s);
-        launch_scale<T>(W.V, W.r, MG_DEVF(ks, double, scale), n, Gate{MG_DEVF(ks, int, scale_gate), 0}, s);
-        for (int jh = 0; jh < ms; ++jh) {
-            const C2<T>* in = W.V + (long)jh * n;
-            arnoldi_step<T>(H, [&](C2<T>* w, Gate g) { L.apply(w, in, nullptr, false, g, s); }, W.V, n, ks, jh, s);
-        }
-        ks_finish(ks, s);
-        launch_axpy_multi<T>(x, W.V, n, 0, MG_DEVF(ks, int, j), MG_DEVF(ks, double2, d), 1.0, false, n, nullptr,
-                             H.red, Gate{}, s);
-        launch_axpy_multi<T>(W.r, W.V, n, 1, MG_DEVF(ks, int, j), MG_DEVF(ks, double2, rho), 1.0, true, n, nullptr,
-                             H.red, Gate{}, s);
-        KHost kh;
-        MG_TRY(read_ks(H, ks, kh, s));
-        iters += kh.j;
-        ++cycles;
-        if (kh.conv || cycles >= H.p.proj_max_cycles) break;
-    }
-    H.st.coarse_iters += iters;
-    H.st.mvps[2] += iters;
-    return MG_OK;
+    CoopArgs<T> a{};
+    a.A = L.A;
+    a.Nx = L.Nx;
+    a.Nt = L.Nt;
+    a.f = f;
+    a.x = x;
+    a.r = W.r;
+    a.V = W.V;
+    a.W = W.W;
+    a.pls = H.pls;
+    a.k = H.defl_k;
+    a.ms = std::max(H.p.dr_m - H.defl_k, 1);
+    a.tol = H.p.coarse_tol_rest;
+    a.max_cycles = H.p.proj_max_cycles;
+    a.part = H.cpart;
+    a.part_ctas = H.cpart_ctas;
+    a.out = H.cstats;
+    return launch_coarse_proj<T>(a, s);
 }
 
 template <typename T>

@@ -60,6 +60,7 @@ void launch_stencil(C2<T>* y, const C2<T>* x, const C2<T>* A, const C2<T>* b, in
     const unsigned grid = (unsigned)((nsite + SPB - 1) / SPB);
     // only dof = 24 is built (12 near-null vectors, chirally doubled)
     k_stencil<T, 24><<<grid, SPB * 24, 0, s>>>(y, x, A, b, Nx, Nt, dagger ? 1 : 0, g);
+    count_launch();
 }
 
 template void launch_stencil<double>(C2<double>*, const C2<double>*, const C2<double>*, const C2<double>*, int, int,

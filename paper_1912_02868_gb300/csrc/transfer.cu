@@ -75,6 +75,7 @@ void launch_restrict(C2<T>* coarse, const C2<T>* fine, const C2<T>* Q, int NxF, 
                      cudaStream_t s) {
     const int nc = (NxF / BL) * (NtF / BL);
     k_restrict<T><<<nc, 256, 0, s>>>(coarse, fine, Q, NxF, h, g);
+    count_launch();
 }
 
 template <typename T>
@@ -82,6 +83,7 @@ void launch_prolong(C2<T>* fine, const C2<T>* coarse, const C2<T>* Q, int NxF, i
                     Gate g, cudaStream_t s) {
     const long nf = (long)NxF * NtF * 2 * h;
     k_prolong<T><<<nblocks(nf, 256), 256, 0, s>>>(fine, coarse, Q, NxF, NtF, h, accumulate ? 1 : 0, g);
+    count_launch();
 }
 
 template void launch_restrict<double>(C2<double>*, const C2<double>*, const C2<double>*, int, int, int, Gate,

@@ -110,6 +110,7 @@ void launch_wilson(C2<T>* y, const C2<T>* x, const C2<T>* U, const C2<T>* b, dou
         if (b) k_wilson<T, false, true><<<grid, 256, 0, s>>>(y, x, U, b, diag, Lx, Lt, g);
         else k_wilson<T, false, false><<<grid, 256, 0, s>>>(y, x, U, b, diag, Lx, Lt, g);
     }
+    count_launch();
 }
 
 template void launch_wilson<double>(C2<double>*, const C2<double>*, const C2<double>*, const C2<double>*, double,
