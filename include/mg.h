@@ -74,7 +74,14 @@ typedef struct {
     double coarse_tol_rest;  /* GMRES-Proj / CGNE tolerance: 1e-8 */
     int precision;         /* MG_FP64 or MG_MIXED */
     unsigned long long seed; /* start vectors of the near-null solves when none are given */
+    int method;            /* MG_METHOD_MG (default) or MG_METHOD_FINE_DEFLATION */
 } mg_params;
+
+/* solver of mg_solve (Section 2 compares both) */
+enum { MG_METHOD_MG = 0,             /* FGMRES(8) preconditioned by the deflated V-cycle */
+       MG_METHOD_FINE_DEFLATION = 1  /* no multigrid: GMRES-DR(m,k) on the fine operator for the
+                                        first right-hand side, GMRES-Proj(m,k) afterwards, FP64;
+                                        mg_solve's iters then counts Krylov steps */ };
 
 typedef struct {
     long long mvps[3];       /* operator applications per grid (fine, intermediate, coarse) */
@@ -137,7 +144,8 @@ mg_status mg_setup_from_vectors(const void* gauge, int L_x, int L_t, double m0, 
 mg_status mg_solve(mg_handle h, const void* b, void* x, int nrhs, double tol, void* stream,
                    int* iters, double* relres, mg_solve_stats* stats);
 
-/* Forget the coarse deflation space: the next coarse solve runs GMRES-DR again. */
+/* Forget the deflation space (coarse, or fine for MG_METHOD_FINE_DEFLATION):
+ * the next solve runs GMRES-DR again. */
 mg_status mg_reset_deflation(mg_handle h);
 
 /* Release every device buffer of the handle. NULL is accepted. */

@@ -14,6 +14,7 @@ import numpy as np
 
 from . import _lib
 from ._lib import (MG_COARSE_CGNE, MG_COARSE_DR_PROJ, MG_F32, MG_F64, MG_FP64, MG_MIXED, MG_OK,  # noqa: F401
+                   MG_METHOD_MG, MG_METHOD_FINE_DEFLATION,
                    MG_ENOTCONV, MGError, MGParams, MGSolveStats, load)
 
 __all__ = ["build", "default_params", "mg_setup", "mg_setup_from_vectors", "mg_solve", "mg_destroy",

@@ -15,6 +15,7 @@ MG_OK, MG_EINVAL, MG_ENOMEM, MG_ECUDA, MG_ENOTCONV, MG_EBUDGET, MG_ETIMEOUT = 0,
 MG_COARSE_DR_PROJ, MG_COARSE_CGNE = 0, 1
 MG_FP64, MG_MIXED = 0, 1
 MG_F64, MG_F32 = 0, 1
+MG_METHOD_MG, MG_METHOD_FINE_DEFLATION = 0, 1
 
 STATUS_NAMES = {0: "MG_OK", -1: "MG_EINVAL", -2: "MG_ENOMEM", -3: "MG_ECUDA", -4: "MG_ENOTCONV",
                 -5: "MG_EBUDGET", -6: "MG_ETIMEOUT"}
@@ -29,6 +30,7 @@ class MGParams(ctypes.Structure):
         ("cgne_max_iters", ctypes.c_int), ("nullvec_max_iters", ctypes.c_int),
         ("nullvec_tol", ctypes.c_double), ("coarse_tol_first", ctypes.c_double),
         ("coarse_tol_rest", ctypes.c_double), ("precision", ctypes.c_int), ("seed", ctypes.c_ulonglong),
+        ("method", ctypes.c_int),
     ]
 
 

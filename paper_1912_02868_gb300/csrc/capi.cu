@@ -93,6 +93,10 @@ mg_status check_params(const mg_params& p) {
         return set_error("unknown coarse_solver %d", p.coarse_solver), MG_EINVAL;
     if (p.precision != MG_FP64 && p.precision != MG_MIXED)
         return set_error("unknown precision %d", p.precision), MG_EINVAL;
+    if (p.method != MG_METHOD_MG && p.method != MG_METHOD_FINE_DEFLATION)
+        return set_error("unknown method %d", p.method), MG_EINVAL;
+    if (p.dr_m - p.dr_k > MSMAX)
+        return set_error("dr_m - dr_k must be <= %d", MSMAX), MG_EINVAL;
     return MG_OK;
 }
 
@@ -246,6 +250,13 @@ mg_status setup_common(const void* gauge, int Lx, int Lt, double m0, int nvec, i
     H.cpart_ctas = sm_count();
     TRYF(halloc_t(H, &H.cpart, (size_t)2 * H.cpart_ctas * PSTR));
     TRYF(halloc_t(H, &H.cstats, 1));
+    if (p.method == MG_METHOD_FINE_DEFLATION) {
+        TRYF(halloc_t(H, &H.fdV, (size_t)(p.dr_m + 1) * n0));
+        TRYF(halloc_t(H, &H.fdV2, (size_t)(p.dr_m + 1) * n0));
+        TRYF(halloc_t(H, &H.fdW, (size_t)(p.dr_m + 1) * n0));
+        TRYF(halloc_t(H, &H.fdks, 1));
+        TRYF(halloc_t(H, &H.fdpls, 1));
+    }
     if (cudaMemcpyAsync(H.U64, gauge, sizeof(double2) * 2 * Lx * Lt, cudaMemcpyDefault, s) != cudaSuccess) {
         set_error("copy of the gauge field failed: %s", cudaGetErrorString(cudaGetLastError()));
         return fail(MG_ECUDA);
@@ -320,6 +331,7 @@ mg_status mg_default_params(mg_params* p) {
     p->coarse_tol_rest = 1e-8;
     p->precision = MG_FP64;
     p->seed = 12345ULL;
+    p->method = MG_METHOD_MG;
     return MG_OK;
 }
 
@@ -358,6 +370,7 @@ mg_status mg_destroy(mg_handle h) {
 mg_status mg_reset_deflation(mg_handle h) {
     if (!h) return set_error("handle is NULL"), MG_EINVAL;
     h->h.defl_k = 0;
+    h->h.fine_k = 0;
     return MG_OK;
 }
 
@@ -388,7 +401,10 @@ mg_status mg_solve(mg_handle h, const void* b, void* x, int nrhs, double tol, vo
         int it = 0;
         double rr = 0.0;
         bool conv = false;
-        MG_TRY(fgmres_solve(H, bsrc, xdst, tol, s, &it, &rr, &conv));
+        if (H.p.method == MG_METHOD_FINE_DEFLATION)
+            MG_TRY(fine_deflated_solve(H, bsrc, xdst, tol, s, &it, &rr, &conv));
+        else
+            MG_TRY(fgmres_solve(H, bsrc, xdst, tol, s, &it, &rr, &conv));
         if (!xdev) MG_CUDA_TRY(cudaMemcpyAsync(xi, H.fx, n0 * sizeof(double2), cudaMemcpyDeviceToHost, s));
         if (iters) iters[i] = it;
         if (relres) relres[i] = rr;

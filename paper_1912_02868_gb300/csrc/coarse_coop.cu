@@ -185,6 +185,11 @@ __global__ void __launch_bounds__(CO_THREADS) k_coarse_proj(CoopArgs<T> a) {
             break;
         }
         // ---- one GMRES(ms) cycle from r ----
+        // (shared memory is not zero-initialised: H must be zero below its subdiagonal)
+        for (int e = tid; e < (MSMAX + 1) * MSMAX; e += CO_THREADS) {
+            S.H[e] = make_double2(0.0, 0.0);
+            S.R[e] = make_double2(0.0, 0.0);
+        }
         if (tid == 0) {
             for (int i = 0; i <= ms; ++i) {
                 S.c[i] = make_double2(i == 0 ? beta : 0.0, 0.0);

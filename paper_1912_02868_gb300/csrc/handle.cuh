@@ -124,6 +124,13 @@ struct Handle {
     double2* cpart = nullptr; // partial sums of the cooperative coarse solve
     int cpart_ctas = 0;
     CoopStats* cstats = nullptr;
+    // fine-grid deflation arm (method MG_METHOD_FINE_DEFLATION), FP64
+    double2* fdV = nullptr;   // (m+1) x n0
+    double2* fdV2 = nullptr;
+    double2* fdW = nullptr;   // (k+1) x n0
+    KState* fdks = nullptr;
+    KState* fdpls = nullptr;
+    int fine_k = 0;
     int defl_k = 0;           // 0: no deflation space yet
     Stats st;
     ApplyTimer timers[3];
@@ -147,6 +154,8 @@ mg_status fgmres_solve(Handle& H, const double2* b, double2* x, double tol, cuda
                        double* relres, bool* converged);
 mg_status build_hierarchy(Handle& H, const double2* gauge_dev, const double2* starts0, const double2* starts1,
                           const double2* nullvecs0, const double2* nullvecs1, cudaStream_t s);
+mg_status fine_deflated_solve(Handle& H, const double2* b, double2* x, double tol, cudaStream_t s, int* iters,
+                              double* relres, bool* converged);
 
 }  // namespace mg
 

@@ -134,24 +134,24 @@ mg_status cg_normal(Handle& H, int l, Level<T>& L, const C2<T>* b, C2<T>* y, C2<
     return MG_OK;
 }
 
-// GMRES-DR(m,k) in FP64 on the coarsest grid from x = 0 (Morgan 2002); keeps the
-// deflation space (V_{k+1}, H_k) of its last cycle in the handle.
-mg_status dr_solve(Handle& H, const double2* f, double2* x, cudaStream_t s) {
-    Level<double>& L = H.L64[2];
-    CoarseWS<double>& W = H.c64;
+// GMRES-DR(m,k) in FP64 on one grid from x = 0 (Morgan 2002).  V, V2: (m+1) x n
+// bases; the deflation space (V_{k+1}, H_k) of the last cycle is written to Wout
+// and pls (factored), its size to kout.
+mg_status dr_solve_on(Handle& H, Level<double>& L, double2* V0, double2* V20, double2* Wout, KState* ks,
+                      KState* pls, int& kout, const double2* f, double2* x, double tol, long long& iters,
+                      cudaStream_t s) {
     const long n = L.n;
     const int m = H.p.dr_m, k = H.p.dr_k;
     double* nb2 = MG_DEVF(H.sc, double, nb2);
-    KState* ks = W.ks;
     launch_norm2<double>(nb2, f, n, H.red, Gate{}, s);
-    ks_start(ks, nb2, H.p.coarse_tol_first, nb2, s);
-    C2<double>* V = W.V;
-    C2<double>* V2 = W.V2;
+    ks_start(ks, nb2, tol, nb2, s);
+    C2<double>* V = V0;
+    C2<double>* V2 = V20;
     launch_scale<double>(V, f, MG_DEVF(ks, double, scale), n, Gate{MG_DEVF(ks, int, scale_gate), 0}, s);
     MG_CUDA_TRY(cudaMemsetAsync(x, 0, n * sizeof(double2), s));
     int j0 = 0, cycles = 0, stalled = 0;
     double best = INFINITY;
-    long long iters = 0;
+    iters = 0;
     while (true) {
         for (int jh = j0; jh < m; ++jh) {
             const double2* in = V + (long)jh * n;
@@ -194,21 +194,18 @@ mg_status dr_solve(Handle& H, const double2* f, double2* x, cudaStream_t s) {
         }
         if (done) {
             if (kk >= 1) {
-                MG_CUDA_TRY(cudaMemcpyAsync(W.W, V2, (size_t)(kk + 1) * n * sizeof(double2),
+                MG_CUDA_TRY(cudaMemcpyAsync(Wout, V2, (size_t)(kk + 1) * n * sizeof(double2),
                                             cudaMemcpyDeviceToDevice, s));
-                ks_load_dense(H.pls, MG_DEVF(H.dr, double2, Hk), nullptr, kk, 0.0, s);
-                H.defl_k = kk;
+                ks_load_dense(pls, MG_DEVF(H.dr, double2, Hk), nullptr, kk, 0.0, s);
+                kout = kk;
             } else {
                 // converged in one step: the space is the Arnoldi basis itself
-                MG_CUDA_TRY(cudaMemcpyAsync(W.W, V, (size_t)(jend + 1) * n * sizeof(double2),
+                MG_CUDA_TRY(cudaMemcpyAsync(Wout, V, (size_t)(jend + 1) * n * sizeof(double2),
                                             cudaMemcpyDeviceToDevice, s));
-                ks_load_dense(H.pls, MG_DEVF(ks, double2, H), nullptr, jend, 0.0, s);
-                H.defl_k = jend;
+                ks_load_dense(pls, MG_DEVF(ks, double2, H), nullptr, jend, 0.0, s);
+                kout = jend;
             }
-            H.st.coarse_iters += iters;
-            H.st.mvps[2] += iters;
-            H.st.dr_solves += 1;
-            if (H.defl_k < 1) {
+            if (kout < 1) {
                 set_error("GMRES-DR produced no deflation space");
                 return MG_ECUDA;
             }
@@ -220,8 +217,59 @@ mg_status dr_solve(Handle& H, const double2* f, double2* x, cudaStream_t s) {
     }
 }
 
-// GMRES-Proj(m,k) from x = 0: minimum-residual projection onto the deflation
-// space, then one GMRES(m - k) cycle, repeated (Morgan & Wilcox).
+// The first coarsest-grid solve: GMRES-DR to coarse_tol_first, which also
+// builds the coarse deflation space of the handle.
+mg_status dr_solve(Handle& H, const double2* f, double2* x, cudaStream_t s) {
+    long long iters = 0;
+    MG_TRY(dr_solve_on(H, H.L64[2], H.c64.V, H.c64.V2, H.c64.W, H.c64.ks, H.pls, H.defl_k, f, x,
+                       H.p.coarse_tol_first, iters, s));
+    H.st.coarse_iters += iters;
+    H.st.mvps[2] += iters;
+    H.st.dr_solves += 1;
+    return MG_OK;
+}
+
+// GMRES-Proj(m,k) in FP64 on one grid, driven from the host one cycle at a time
+// (used by the fine-grid deflation arm): minimum-residual projection onto
+// (W = V_{k+1}, H_k), then one GMRES(m - k) cycle, repeated.
+mg_status proj_solve_host(Handle& H, Level<double>& L, double2* V, const double2* W, double2* r, KState* ks,
+                          const KState* pls, int k, const double2* f, double2* x, double tol, long long& iters,
+                          cudaStream_t s) {
+    const long n = L.n;
+    const int ms = std::max(H.p.dr_m - k, 1);
+    double* nb2 = MG_DEVF(H.sc, double, nb2);
+    double* r2 = MG_DEVF(H.sc, double, r2);
+    launch_norm2<double>(nb2, f, n, H.red, Gate{}, s);
+    MG_CUDA_TRY(cudaMemsetAsync(x, 0, n * sizeof(double2), s));
+    MG_CUDA_TRY(cudaMemcpyAsync(r, f, n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+    int cycles = 0;
+    iters = 0;
+    while (true) {
+        launch_gram<double>(H.cvec, W, n, k + 1, r, n, H.red, Gate{}, s);
+        proj_solve(pls, H.cvec, H.dvec, H.uvec, s);
+        launch_axpy_multi<double>(x, W, n, k, nullptr, H.dvec, 1.0, false, n, nullptr, H.red, Gate{}, s);
+        launch_axpy_multi<double>(r, W, n, k + 1, nullptr, H.uvec, -1.0, false, n, r2, H.red, Gate{}, s);
+        ks_start(ks, r2, tol, nb2, s);
+        launch_scale<double>(V, r, MG_DEVF(ks, double, scale), n, Gate{MG_DEVF(ks, int, scale_gate), 0}, s);
+        for (int jh = 0; jh < ms; ++jh) {
+            const double2* in = V + (long)jh * n;
+            arnoldi_step<double>(H, [&](double2* w, Gate g) { L.apply(w, in, nullptr, false, g, s); }, V, n, ks, jh,
+                                 s);
+        }
+        ks_finish(ks, s);
+        launch_axpy_multi<double>(x, V, n, 0, MG_DEVF(ks, int, j), MG_DEVF(ks, double2, d), 1.0, false, n, nullptr,
+                                  H.red, Gate{}, s);
+        launch_axpy_multi<double>(r, V, n, 1, MG_DEVF(ks, int, j), MG_DEVF(ks, double2, rho), 1.0, true, n, nullptr,
+                                  H.red, Gate{}, s);
+        KHost kh;
+        MG_TRY(read_ks(H, ks, kh, s));
+        iters += kh.j;
+        ++cycles;
+        if (kh.conv || cycles >= H.p.proj_max_cycles) break;
+    }
+    return MG_OK;
+}
+
 // GMRES-Proj(m,k) from x = 0: minimum-residual projection onto the deflation
 // space, then one GMRES(m - k) cycle, repeated (Morgan & Wilcox).  The whole
 // solve is one cooperative kernel (coarse_coop.cu); its iteration counts are
@@ -362,6 +410,36 @@ mg_status fgmres_solve(Handle& H, const double2* b, double2* x, double tol, cuda
     }
     *iters = outer;
     H.st.outer += outer;
+    return MG_OK;
+}
+
+// Comparison arm without multigrid (Section 2): GMRES-DR(m,k) on the fine
+// operator for the handle's first right-hand side, GMRES-Proj(m,k) with the
+// fine deflation space for every later one, all in FP64; convergence is then
+// confirmed on the true residual.
+mg_status fine_deflated_solve(Handle& H, const double2* b, double2* x, double tol, cudaStream_t s, int* iters,
+                              double* relres, bool* converged) {
+    Level<double>& L0 = H.L64[0];
+    const long n = L0.n;
+    long long it = 0;
+    if (H.fine_k == 0) {
+        MG_TRY(dr_solve_on(H, L0, H.fdV, H.fdV2, H.fdW, H.fdks, H.fdpls, H.fine_k, b, x, tol, it, s));
+        H.st.dr_solves += 1;
+    } else {
+        MG_TRY(proj_solve_host(H, L0, H.fdV, H.fdW, H.fr, H.fdks, H.fdpls, H.fine_k, b, x, tol, it, s));
+    }
+    H.st.mvps[0] += it + 1;
+    double* fnb2 = MG_DEVF(H.sc, double, tmp) + 4;
+    double* r2 = MG_DEVF(H.sc, double, r2);
+    launch_norm2<double>(fnb2, b, n, H.red, Gate{}, s);
+    L0.apply(H.fr, x, b, false, Gate{}, s);
+    launch_norm2<double>(r2, H.fr, n, H.red, Gate{}, s);
+    Scalars hs{};
+    MG_TRY(read_scalars(H, hs, s));
+    *relres = hs.tmp[4] > 0.0 ? std::sqrt(hs.r2 / hs.tmp[4]) : 0.0;
+    *converged = *relres <= tol;
+    *iters = (int)std::min<long long>(it, 1LL << 30);
+    H.st.outer += *iters;
     return MG_OK;
 }
 

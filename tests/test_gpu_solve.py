@@ -101,12 +101,21 @@ def test_deflation_space_parity(mgmod, case):
     Wc = W.T
     assert np.abs(Wc.conj().T @ Wc - np.eye(k + 1)).max() < 1e-12
     assert np.linalg.norm(A2 @ Wc[:, :k] - Wc @ Hk) <= 1e-10 * np.linalg.norm(A2, 2)
-    # the same subspace as the oracle's (projectors).  The GMRES-DR solve runs many
-    # restarts before it stalls near 1e-14, and rounding differences between the two
-    # implementations move the not-yet-converged part of the space at the 1e-7 level.
-    Po = Wo.T @ Wo.conj()
-    Pg = Wc @ Wc.conj().T
-    assert np.abs(Po - Pg).max() < 1e-6
+    # Ritz values of the space (unique even when the kept set is not): the k of
+    # smallest modulus, compared as moduli because sigma3^-hermiticity makes the
+    # spectrum closed under conjugation, so |theta| ties come in exact pairs
+    rg = np.sort(np.abs(np.linalg.eigvals(Hk[:k, :k])))
+    ro = np.sort(np.abs(np.linalg.eigvals(osol.deflation.Hk[:k, :k])))
+    assert np.allclose(rg, ro, rtol=1e-6)
+    # the same subspace as the oracle's (projectors) when the kept set is unique
+    # (n_coarse > m: the solve restarts and the space is not an exact eigenspace
+    # split inside a conjugate pair).  The GMRES-DR solve runs many restarts before
+    # it stalls near 1e-14; rounding differences between the two implementations
+    # move the not-yet-converged part of the space at the 1e-7 level.
+    if A2.shape[0] > 30:
+        Po = Wo.T @ Wo.conj()
+        Pg = Wc @ Wc.conj().T
+        assert np.abs(Po - Pg).max() < 1e-6
 
 
 def test_second_rhs_reuses_deflation_and_multi_rhs(mgmod, case):
@@ -165,6 +174,37 @@ def test_cgne_arm(mgmod):
         assert _true_relres(U, m0, host(x), b) <= 1.0001e-8
         xo, info = omg.MGSolver(h, omg.Params(coarse="cgne")).solve(b, 1e-8)
         assert abs(iters[0] - info.iters) <= 1
+    finally:
+        g.close()
+
+
+@pytest.mark.parametrize("L", [16, 32])
+def test_fine_deflation_arm(mgmod, L):
+    """Comparison arm without multigrid: GMRES-DR(30,10) on the fine operator for
+    the first right-hand side, GMRES-Proj(30,10) for the next (Section 2), FP64,
+    against the oracle's gmres_dr / gmres_proj on the same operator."""
+    import torch
+    from oracle import krylov
+    U = synth.gauge_field(L, 0)
+    m0 = synth.m0_for(L, 0)
+    p = mgmod.default_params(method=mgmod.MG_METHOD_FINE_DEFLATION)
+    g = mgmod.mg_setup(dev(U), L, L, m0, params=p)
+    A = lambda v: dirac.wilson(U, v.reshape(L, L, 2), m0).ravel()
+    try:
+        b0, b1 = synth.rhs(L, 0, 0, nrhs=2)
+        x = torch.zeros(b0.shape, dtype=torch.complex128, device="cuda")
+        st, it0, rr0, s0 = mgmod.mg_solve(g, dev(b0), x, 1, 1e-8)
+        xg0 = host(x)
+        xo0, info0, defl = krylov.gmres_dr(A, b0.ravel(), 30, 10, 1e-8)
+        assert s0["dr_solves"] == 1 and rr0[0] <= 1e-8
+        assert _true_relres(U, m0, xg0, b0) <= 1.0001e-8
+        assert abs(it0[0] - info0.iters) <= 2
+        assert rel2(xg0, xo0) <= 1e-6
+        st, it1, rr1, s1 = mgmod.mg_solve(g, dev(b1), x, 1, 1e-8)
+        xo1, info1 = krylov.gmres_proj(A, b1.ravel(), defl, 30, 1e-8)
+        assert s1["dr_solves"] == 0 and rr1[0] <= 1e-8
+        assert _true_relres(U, m0, host(x), b1) <= 1.0001e-8
+        assert abs(it1[0] - info1.iters) <= 2
     finally:
         g.close()
 
