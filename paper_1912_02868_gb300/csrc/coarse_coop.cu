@@ -1,24 +1,33 @@
 // The whole GMRES-Proj(m,k) coarsest-grid solve (Section 2; Morgan & Wilcox)
-// in one cooperative persistent kernel.
+// in one thread-block-cluster kernel.
 //
 // The coarsest grid is small (256 sites x 24 dofs at 256^2) and its solve runs
-// ~10^3 Krylov steps per outer iteration, so a step is bound by latency, not by
-// bytes: one launch per solve, three grid barriers per Arnoldi step, and the
-// small least-squares work done redundantly (and identically) by every CTA.
+// ~10^3 Krylov steps per outer iteration, so a step is bound by latency, not
+// by bytes.  One cluster of up to 16 CTAs runs a whole solve: three hardware
+// cluster barriers per Arnoldi step, reductions through distributed shared
+// memory, and the small least-squares work done redundantly (and identically)
+// by every CTA, so no CTA ever waits for another one's scalar result.  Several
+// solves (one per stream) run side by side on different clusters.
 //
-// Work split: CTA b owns sites [b*spc, (b+1)*spc) and their 24 dofs; every
-// vector operation touches only the CTA's own rows, except the stencil apply,
-// which reads neighbour rows written by other CTAs before the previous barrier.
-// Reductions: each CTA writes one partial per quantity, and after the barrier
-// every CTA sums all partials in CTA order with the same warp tree, so every
-// CTA holds bit-identical scalars and takes identical control decisions.
+// Work split: CTA b of the cluster owns sites [b*spc, (b+1)*spc) and their 24
+// dofs.  Vectors live in global memory (L2-resident); every vector operation
+// touches only the CTA's own rows, except the stencil apply, which stages the
+// five neighbour rows of its sites (written by other CTAs before the previous
+// barrier) in shared memory through L2.
 //
 // Per Arnoldi step j (CGS2, as in the rest of the library):
 //   [sync] w = A v_j; h1 = V^+ w (partials)
 //   [sync] reduce h1; w -= V h1; h2 = V^+ w, n2 = ||w||^2 (partials)
 //   [sync] reduce h2, n2; w -= V h2; ||w||^2 = n2 - |h2|^2 (V orthonormal);
 //          Givens update of the least squares; v_{j+1} = w / h_{j+1,j}
+// Reductions add the CTAs' partials in rank order with one fixed warp tree, so
+// every CTA holds bit-identical scalars and takes identical control decisions.
+//
+// The small least squares runs in the precision of the vectors (FP32 in the
+// mixed-precision V-cycle, FP64 on the plain path).
 #include <cooperative_groups.h>
+
+#include <type_traits>
 
 #include "coarse_coop.cuh"
 
@@ -28,58 +37,75 @@ namespace mg {
 
 namespace {
 
-constexpr int CO_THREADS = 256;
-constexpr int CO_WARPS = CO_THREADS / 32;
 constexpr int NDOF = 24;
+constexpr int MAX_THREADS = 512;
+constexpr int MAX_SPC = 32;  // sites per CTA staged in shared memory
 
-struct CoopSmem {
-    double2 H[(MSMAX + 1) * MSMAX];  // column-major, ld MSMAX + 1
-    double2 R[(MSMAX + 1) * MSMAX];
-    double rc[MSMAX];
-    double2 rs[MSMAX];
-    double2 g[MSMAX + 1], c[MSMAX + 1], d[MSMAX], rho[MSMAX + 1];
-    double2 red[PSTR];               // reduced quantities of the current phase
-    double2 h1[MSMAX + 1];
-    double2 pd[KMAX], pu[KLD];       // projection coefficients
-    double scal[8];
+template <typename R>
+struct Small {  // per-CTA copy of the small least-squares state, precision R
+    using Z = C2<R>;
+    Z H[(MSMAX + 1) * MSMAX];  // column-major, ld MSMAX + 1 (unrotated)
+    Z Rm[(MSMAX + 1) * MSMAX];
+    R rc[MSMAX];
+    Z rs[MSMAX];
+    Z g[MSMAX + 1], c[MSMAX + 1], d[MSMAX], rho[MSMAX + 1];
+    Z pd[KMAX], pu[KLD];       // projection coefficients
+};
+
+template <typename T>
+struct ClusterSmem {
+    using R = T;
+    double2 part[2][PSTR];               // this CTA's partial sums (read by the whole cluster)
+    double2 red[PSTR];                   // reduced values (identical in every CTA)
+    C2<T> h1[MSMAX + 1];
+    C2<T> h2[MSMAX + 1];
+    C2<T> xs[MAX_SPC][5][NDOF];          // staged neighbour rows
+    Small<T> st;
+    T scal[8];
     int ctl[8];
 };
 
-__device__ __forceinline__ double cabsd(double2 a) { return sqrt(a.x * a.x + a.y * a.y); }
-__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+template <typename R>
+__device__ __forceinline__ R cabs_(C2<R> a) { return sqrt(a.x * a.x + a.y * a.y); }
+
+template <typename R>
+__device__ __forceinline__ C2<R> cdiv_(C2<R> a, C2<R> b) {
     if (fabs(b.x) >= fabs(b.y)) {
-        double r = b.y / b.x, den = b.x + b.y * r;
-        return make_double2((a.x + a.y * r) / den, (a.y - a.x * r) / den);
+        R r = b.y / b.x, den = b.x + b.y * r;
+        return mk<R>((a.x + a.y * r) / den, (a.y - a.x * r) / den);
     }
-    double r = b.x / b.y, den = b.x * r + b.y;
-    return make_double2((a.x * r + a.y) / den, (a.y * r - a.x) / den);
+    R r = b.x / b.y, den = b.x * r + b.y;
+    return mk<R>((a.x * r + a.y) / den, (a.y * r - a.x) / den);
 }
-__device__ __forceinline__ void givens(double2 a, double2 b, double& c, double2& s, double2& r) {
-    const double ab = cabsd(b);
-    if (ab == 0.0) { c = 1.0; s = make_double2(0.0, 0.0); r = a; return; }
-    const double aa = cabsd(a);
-    if (aa == 0.0) { c = 0.0; s = make_double2(b.x / ab, -b.y / ab); r = make_double2(ab, 0.0); return; }
-    const double rh = hypot(aa, ab);
+
+// Complex Givens rotation G = [[c, s], [-conj(s), c]] with G [a; b] = [r; 0].
+template <typename R>
+__device__ __forceinline__ void givens_(C2<R> a, C2<R> b, R& c, C2<R>& s, C2<R>& r) {
+    const R ab = cabs_<R>(b);
+    if (ab == R(0)) { c = R(1); s = mk<R>(0, 0); r = a; return; }
+    const R aa = cabs_<R>(a);
+    if (aa == R(0)) { c = R(0); s = mk<R>(b.x / ab, -b.y / ab); r = mk<R>(ab, 0); return; }
+    const R rh = hypot(aa, ab);
     c = aa / rh;
-    const double2 ph = make_double2(a.x / aa, a.y / aa);
-    s = cscale(cmul(ph, conj_(b)), 1.0 / rh);
+    const C2<R> ph = mk<R>(a.x / aa, a.y / aa);
+    s = cscale(cmul(ph, conj_(b)), R(1) / rh);
     r = cscale(ph, rh);
 }
-__device__ __forceinline__ void rot_apply(double c, double2 s, double2& up, double2& uq) {
-    const double2 p = up, q = uq;
+template <typename R>
+__device__ __forceinline__ void rot_(R c, C2<R> s, C2<R>& up, C2<R>& uq) {
+    const C2<R> p = up, q = uq;
     up = cadd(cscale(p, c), cmul(s, q));
     uq = csub(cscale(q, c), cmul(conj_(s), p));
 }
 
 // Partials of nd inner products conj(X[i]) . y over the CTA's rows (warp per
-// product, lanes over rows), plus optionally ||y||^2 in slot nd.  Written to
-// part[blockIdx.x * PSTR + i].
+// product, lanes over rows), plus optionally ||y||^2 in slot nd.
 template <typename T>
 __device__ void partial_gram(const C2<T>* X, long ldx, int nd, const C2<T>* y, long r0, int nrows, bool norm,
                              double2* part) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int ntot = nd + (norm ? 1 : 0);
-    for (int i = warp; i < ntot; i += CO_WARPS) {
+    for (int i = warp; i < ntot; i += nw) {
         C2<T> acc = mk<T>(0, 0);
         if (i < nd) {
             const C2<T>* xi = X + (long)i * ldx + r0;
@@ -90,24 +116,23 @@ __device__ void partial_gram(const C2<T>* X, long ldx, int nd, const C2<T>* y, l
                 acc.x += v.x * v.x + v.y * v.y;
             }
         }
-        double2 a = to_d2(acc);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            a.x += __shfl_xor_sync(0xffffffffu, a.x, o);
-            a.y += __shfl_xor_sync(0xffffffffu, a.y, o);
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
         }
-        if (lane == 0) part[(size_t)blockIdx.x * PSTR + i] = a;
+        if (lane == 0) part[i] = to_d2(acc);
     }
 }
 
-// Sum the partials of all CTAs in CTA order (every CTA computes the same
-// result): red[i] = sum_b part[b * PSTR + i], i < n.
-__device__ void reduce_partials(const double2* part, int n, double2* red) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int G = gridDim.x;
-    for (int i = warp; i < n; i += CO_WARPS) {
+// Sum the partials of all CTAs of the cluster in rank order (every CTA gets the
+// same result): red[i] = sum_r part_r[i], i < n.
+__device__ void reduce_partials(cg::cluster_group& cluster, double2* part, int n, double2* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int nr = (int)cluster.num_blocks();
+    for (int i = warp; i < n; i += nw) {
         double2 a = make_double2(0.0, 0.0);
-        for (int b = lane; b < G; b += 32) a = cadd(a, __ldcg(part + (size_t)b * PSTR + i));
+        if (lane < nr) a = *cluster.map_shared_rank(part + i, lane);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             a.x += __shfl_xor_sync(0xffffffffu, a.x, o);
@@ -119,66 +144,70 @@ __device__ void reduce_partials(const double2* part, int n, double2* red) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(CO_THREADS) k_coarse_proj(CoopArgs<T> a) {
-    cg::grid_group grid = cg::this_grid();
+__global__ void k_coarse_proj(CoopArgs<T> a) {
+    using Z = C2<T>;
+    cg::cluster_group cluster = cg::this_cluster();
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    CoopSmem& S = *reinterpret_cast<CoopSmem*>(smem_raw);
-    const int tid = threadIdx.x;
+    ClusterSmem<T>& S = *reinterpret_cast<ClusterSmem<T>*>(smem_raw);
+    Small<T>& st = S.st;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int rank = (int)cluster.block_rank();
     const long nsite = (long)a.Nx * a.Nt;
     const long n = nsite * NDOF;
-    const long s0 = (long)blockIdx.x * a.spc;
+    const long s0 = (long)rank * a.spc;
     const long s1 = min(nsite, s0 + a.spc);
+    const int my_sites = (int)max(0L, s1 - s0);
     const long r0 = s0 * NDOF;
-    const int nrows = (int)max(0L, (s1 - s0) * NDOF);
+    const int nrows = my_sites * NDOF;
     const int k = a.k, ms = a.ms;
-    double2* partA = a.part;
-    double2* partB = a.part + (size_t)gridDim.x * PSTR;
+    const int LD = MSMAX + 1;
 
     // x = 0, r = f, ||f||^2
-    for (int e = tid; e < nrows; e += CO_THREADS) {
+    for (int e = tid; e < nrows; e += nt) {
         a.x[r0 + e] = mk<T>(0, 0);
         a.r[r0 + e] = a.f[r0 + e];
     }
     __syncthreads();
-    partial_gram<T>(a.r, 0, 0, a.r, r0, nrows, true, partA);
-    grid.sync();
-    reduce_partials(partA, 1, S.red);
+    partial_gram<T>(a.r, 0, 0, a.r, r0, nrows, true, S.part[0]);
+    cluster.sync();
+    reduce_partials(cluster, S.part[0], 1, S.red);
     const double nb = sqrt(fmax(S.red[0].x, 0.0));
     const double tol_abs = a.tol * nb;
     int iters = 0, cycles = 0, conv = 0;
     while (true) {
         // ---- projection onto the deflation space: d = argmin ||W^+ r - H_k d|| ----
-        partial_gram<T>(a.W, n, k + 1, a.r, r0, nrows, false, partB);
-        grid.sync();
-        reduce_partials(partB, k + 1, S.red);
+        partial_gram<T>(a.W, n, k + 1, a.r, r0, nrows, false, S.part[1]);
+        cluster.sync();
+        reduce_partials(cluster, S.part[1], k + 1, S.red);
         if (tid == 0) {
             const KState* P = a.pls;
-            double2 g[KLD];
-            for (int i = 0; i <= k; ++i) g[i] = S.red[i];
-            for (int t = 0; t < P->nrot; ++t) rot_apply(P->rc[t], P->rs[t], g[P->ra[t]], g[P->rb[t]]);
+            Z g[KLD];
+            for (int i = 0; i <= k; ++i) g[i] = from_d2<T>(S.red[i]);
+            for (int t = 0; t < P->nrot; ++t)
+                rot_<T>((T)P->rc[t], from_d2<T>(P->rs[t]), g[P->ra[t]], g[P->rb[t]]);
             for (int i = k - 1; i >= 0; --i) {
-                double2 acc = g[i];
-                for (int l = i + 1; l < k; ++l) acc = csub(acc, cmul(P->R[i + KLD * l], S.pd[l]));
-                S.pd[i] = cdiv(acc, P->R[i + KLD * i]);
+                Z acc = g[i];
+                for (int l = i + 1; l < k; ++l) acc = csub(acc, cmul(from_d2<T>(P->R[i + KLD * l]), st.pd[l]));
+                st.pd[i] = cdiv_<T>(acc, from_d2<T>(P->R[i + KLD * i]));
             }
             for (int i = 0; i <= k; ++i) {
-                double2 acc = make_double2(0.0, 0.0);
-                for (int l = 0; l < k; ++l) acc = cfma(P->H[i + KLD * l], S.pd[l], acc);
-                S.pu[i] = acc;
+                Z acc = mk<T>(0, 0);
+                for (int l = 0; l < k; ++l) acc = cfma(from_d2<T>(P->H[i + KLD * l]), st.pd[l], acc);
+                st.pu[i] = acc;
             }
         }
         __syncthreads();
-        for (int e = tid; e < nrows; e += CO_THREADS) {
-            C2<T> xv = a.x[r0 + e], rv = a.r[r0 + e];
-            for (int i = 0; i < k; ++i) xv = cfma(a.W[(long)i * n + r0 + e], from_d2<T>(S.pd[i]), xv);
-            for (int i = 0; i <= k; ++i) rv = csub(rv, cmul(a.W[(long)i * n + r0 + e], from_d2<T>(S.pu[i])));
+        for (int e = tid; e < nrows; e += nt) {
+            Z xv = a.x[r0 + e], rv = a.r[r0 + e];
+            for (int i = 0; i < k; ++i) xv = cfma(a.W[(long)i * n + r0 + e], st.pd[i], xv);
+            for (int i = 0; i <= k; ++i) rv = csub(rv, cmul(a.W[(long)i * n + r0 + e], st.pu[i]));
             a.x[r0 + e] = xv;
             a.r[r0 + e] = rv;
         }
         __syncthreads();
-        partial_gram<T>(a.r, 0, 0, a.r, r0, nrows, true, partA);
-        grid.sync();
-        reduce_partials(partA, 1, S.red);
+        partial_gram<T>(a.r, 0, 0, a.r, r0, nrows, true, S.part[0]);
+        cluster.sync();
+        reduce_partials(cluster, S.part[0], 1, S.red);
         const double beta = sqrt(fmax(S.red[0].x, 0.0));
         if (beta <= tol_abs || beta == 0.0) {
             conv = 1;
@@ -186,94 +215,105 @@ __global__ void __launch_bounds__(CO_THREADS) k_coarse_proj(CoopArgs<T> a) {
         }
         // ---- one GMRES(ms) cycle from r ----
         // (shared memory is not zero-initialised: H must be zero below its subdiagonal)
-        for (int e = tid; e < (MSMAX + 1) * MSMAX; e += CO_THREADS) {
-            S.H[e] = make_double2(0.0, 0.0);
-            S.R[e] = make_double2(0.0, 0.0);
+        for (int e = tid; e < LD * MSMAX; e += nt) {
+            st.H[e] = mk<T>(0, 0);
+            st.Rm[e] = mk<T>(0, 0);
         }
         if (tid == 0) {
             for (int i = 0; i <= ms; ++i) {
-                S.c[i] = make_double2(i == 0 ? beta : 0.0, 0.0);
-                S.g[i] = S.c[i];
+                st.c[i] = mk<T>(i == 0 ? (T)beta : T(0), 0);
+                st.g[i] = st.c[i];
             }
-            S.scal[0] = 1.0 / beta;
+            S.scal[0] = (T)(1.0 / beta);
         }
         __syncthreads();
         {
-            const T sc = (T)S.scal[0];
-            for (int e = tid; e < nrows; e += CO_THREADS) a.V[r0 + e] = cscale(a.r[r0 + e], sc);
+            const T sc = S.scal[0];
+            for (int e = tid; e < nrows; e += nt) a.V[r0 + e] = cscale(a.r[r0 + e], sc);
         }
         int j = 0, stop = 0;
         for (; j < ms && !stop; ++j) {
-            grid.sync();  // v_j complete everywhere
-            C2<T>* vj = a.V + (long)j * n;
-            C2<T>* w = a.V + (long)(j + 1) * n;
-            // w = A v_j on the CTA's rows (column-major 24x24 blocks)
-            for (int e = tid; e < nrows; e += CO_THREADS) {
-                const long s = s0 + e / NDOF;
-                const int kk = e % NDOF;
-                const int xx = (int)(s % a.Nx), tt = (int)(s / a.Nx);
-                const long nb5[5] = {s, (xx + 1 == a.Nx) ? s - xx : s + 1, (xx == 0) ? s + a.Nx - 1 : s - 1,
-                                     (tt + 1 == a.Nt) ? (long)xx : s + a.Nx,
-                                     (tt == 0) ? s + (long)a.Nx * (a.Nt - 1) : s - a.Nx};
-                const C2<T>* Ab = a.A + s * (5L * NDOF * NDOF) + kk;
-                C2<T> acc = mk<T>(0, 0);
-#pragma unroll
-                for (int d = 0; d < 5; ++d) {
-                    // neighbour rows were written by other CTAs: read through L2 (L1 is not coherent)
-                    const C2<T>* xv = vj + nb5[d] * NDOF;
-#pragma unroll 8
-                    for (int l = 0; l < NDOF; ++l) acc = cfma(Ab[(d * NDOF + l) * NDOF], __ldcg(xv + l), acc);
+            cluster.sync();  // v_j complete in every CTA
+            const Z* vj = a.V + (long)j * n;
+            Z* w = a.V + (long)(j + 1) * n;
+            // w = A v_j on the CTA's rows (column-major 24x24 blocks), MAX_SPC sites at a
+            // time: stage the five neighbour rows of each site (other CTAs' rows: through L2)
+            for (int c0 = 0; c0 < my_sites; c0 += MAX_SPC) {
+                const int cs = min(MAX_SPC, my_sites - c0);
+                for (int e = tid; e < cs * 5 * NDOF; e += nt) {
+                    const int ls = e / (5 * NDOF), rem = e - ls * 5 * NDOF, d = rem / NDOF, l = rem - d * NDOF;
+                    const long s = s0 + c0 + ls;
+                    const int xx = (int)(s % a.Nx), tt = (int)(s / a.Nx);
+                    long nbs = s;
+                    if (d == 1) nbs = (xx + 1 == a.Nx) ? s - xx : s + 1;
+                    if (d == 2) nbs = (xx == 0) ? s + a.Nx - 1 : s - 1;
+                    if (d == 3) nbs = (tt + 1 == a.Nt) ? (long)xx : s + a.Nx;
+                    if (d == 4) nbs = (tt == 0) ? s + (long)a.Nx * (a.Nt - 1) : s - a.Nx;
+                    S.xs[ls][d][l] = __ldcg(vj + nbs * NDOF + l);
                 }
-                w[r0 + e] = acc;
+                __syncthreads();
+                for (int e = tid; e < cs * NDOF; e += nt) {
+                    const int ls = e / NDOF, kk = e - ls * NDOF;
+                    const Z* Ab = a.A + (s0 + c0 + ls) * (5L * NDOF * NDOF) + kk;
+                    Z acc = mk<T>(0, 0);
+#pragma unroll
+                    for (int d = 0; d < 5; ++d) {
+#pragma unroll
+                        for (int l = 0; l < NDOF; ++l)
+                            acc = cfma(__ldg(Ab + (d * NDOF + l) * NDOF), S.xs[ls][d][l], acc);
+                    }
+                    w[r0 + (long)c0 * NDOF + e] = acc;
+                }
+                __syncthreads();
             }
+            partial_gram<T>(a.V, n, j + 1, w, r0, nrows, false, S.part[1]);
+            cluster.sync();
+            reduce_partials(cluster, S.part[1], j + 1, S.red);
+            for (int i = tid; i <= j; i += nt) S.h1[i] = from_d2<T>(S.red[i]);
             __syncthreads();
-            partial_gram<T>(a.V, n, j + 1, w, r0, nrows, false, partB);
-            grid.sync();
-            reduce_partials(partB, j + 1, S.red);
-            for (int i = tid; i <= j; i += CO_THREADS) S.h1[i] = S.red[i];
-            __syncthreads();
-            for (int e = tid; e < nrows; e += CO_THREADS) {
-                C2<T> wv = w[r0 + e];
-                for (int i = 0; i <= j; ++i) wv = csub(wv, cmul(a.V[(long)i * n + r0 + e], from_d2<T>(S.h1[i])));
+            for (int e = tid; e < nrows; e += nt) {
+                Z wv = w[r0 + e];
+                for (int i = 0; i <= j; ++i) wv = csub(wv, cmul(a.V[(long)i * n + r0 + e], S.h1[i]));
                 w[r0 + e] = wv;
             }
             __syncthreads();
-            partial_gram<T>(a.V, n, j + 1, w, r0, nrows, true, partA);
-            grid.sync();
-            reduce_partials(partA, j + 2, S.red);
+            partial_gram<T>(a.V, n, j + 1, w, r0, nrows, true, S.part[0]);
+            cluster.sync();
+            reduce_partials(cluster, S.part[0], j + 2, S.red);
+            for (int i = tid; i <= j; i += nt) S.h2[i] = from_d2<T>(S.red[i]);
             if (tid == 0) {
-                double h2n = 0.0;
+                T h2n = 0;
                 for (int i = 0; i <= j; ++i) {
-                    const double2 hh = cadd(S.h1[i], S.red[i]);
-                    S.H[i + (MSMAX + 1) * j] = hh;
-                    S.R[i + (MSMAX + 1) * j] = hh;
-                    h2n += cabs2(S.red[i]);
+                    const Z h2 = from_d2<T>(S.red[i]);
+                    const Z hh = cadd(S.h1[i], h2);
+                    st.H[i + LD * j] = hh;
+                    st.Rm[i + LD * j] = hh;
+                    h2n += h2.x * h2.x + h2.y * h2.y;
                 }
-                const double hn = sqrt(fmax(S.red[j + 1].x - h2n, 0.0));
-                S.H[(j + 1) + (MSMAX + 1) * j] = make_double2(hn, 0.0);
-                S.R[(j + 1) + (MSMAX + 1) * j] = make_double2(hn, 0.0);
-                double2* Rc = S.R + (MSMAX + 1) * j;
-                for (int t = 0; t < j; ++t) rot_apply(S.rc[t], S.rs[t], Rc[t], Rc[t + 1]);
-                double cc;
-                double2 ss, rr;
-                givens(Rc[j], Rc[j + 1], cc, ss, rr);
+                const T hn = sqrt(fmax((T)S.red[j + 1].x - h2n, T(0)));
+                st.H[(j + 1) + LD * j] = mk<T>(hn, 0);
+                st.Rm[(j + 1) + LD * j] = mk<T>(hn, 0);
+                Z* Rc = st.Rm + LD * j;
+                for (int t = 0; t < j; ++t) rot_<T>(st.rc[t], st.rs[t], Rc[t], Rc[t + 1]);
+                T cc;
+                Z ss, rr;
+                givens_<T>(Rc[j], Rc[j + 1], cc, ss, rr);
                 Rc[j] = rr;
-                Rc[j + 1] = make_double2(0.0, 0.0);
-                S.rc[j] = cc;
-                S.rs[j] = ss;
-                rot_apply(cc, ss, S.g[j], S.g[j + 1]);
-                const double res = cabsd(S.g[j + 1]);
+                Rc[j + 1] = mk<T>(0, 0);
+                st.rc[j] = cc;
+                st.rs[j] = ss;
+                rot_<T>(cc, ss, st.g[j], st.g[j + 1]);
+                const double res = (double)cabs_<T>(st.g[j + 1]);
                 S.ctl[0] = (res <= tol_abs) ? 1 : 0;
-                S.ctl[1] = (hn == 0.0) ? 1 : 0;
-                S.scal[1] = hn > 0.0 ? 1.0 / hn : 0.0;
+                S.ctl[1] = (hn == T(0)) ? 1 : 0;
+                S.scal[1] = hn > T(0) ? T(1) / hn : T(0);
             }
             __syncthreads();
             {
-                const T sc = (T)S.scal[1];
-                for (int e = tid; e < nrows; e += CO_THREADS) {
-                    C2<T> wv = w[r0 + e];
-                    for (int i = 0; i <= j; ++i)
-                        wv = csub(wv, cmul(a.V[(long)i * n + r0 + e], from_d2<T>(S.red[i])));
+                const T sc = S.scal[1];
+                for (int e = tid; e < nrows; e += nt) {
+                    Z wv = w[r0 + e];
+                    for (int i = 0; i <= j; ++i) wv = csub(wv, cmul(a.V[(long)i * n + r0 + e], S.h2[i]));
                     w[r0 + e] = cscale(wv, sc);
                 }
             }
@@ -286,23 +326,23 @@ __global__ void __launch_bounds__(CO_THREADS) k_coarse_proj(CoopArgs<T> a) {
         const int jj = j;
         if (tid == 0) {
             for (int i = jj - 1; i >= 0; --i) {
-                double2 acc = S.g[i];
-                for (int l = i + 1; l < jj; ++l) acc = csub(acc, cmul(S.R[i + (MSMAX + 1) * l], S.d[l]));
-                const double2 piv = S.R[i + (MSMAX + 1) * i];
-                S.d[i] = (piv.x == 0.0 && piv.y == 0.0) ? make_double2(0.0, 0.0) : cdiv(acc, piv);
+                Z acc = st.g[i];
+                for (int l = i + 1; l < jj; ++l) acc = csub(acc, cmul(st.Rm[i + LD * l], st.d[l]));
+                const Z piv = st.Rm[i + LD * i];
+                st.d[i] = (piv.x == T(0) && piv.y == T(0)) ? mk<T>(0, 0) : cdiv_<T>(acc, piv);
             }
             for (int i = 0; i <= jj; ++i) {
-                double2 acc = S.c[i];
-                for (int l = 0; l < jj; ++l) acc = csub(acc, cmul(S.H[i + (MSMAX + 1) * l], S.d[l]));
-                S.rho[i] = acc;
+                Z acc = st.c[i];
+                for (int l = 0; l < jj; ++l) acc = csub(acc, cmul(st.H[i + LD * l], st.d[l]));
+                st.rho[i] = acc;
             }
         }
         __syncthreads();
-        for (int e = tid; e < nrows; e += CO_THREADS) {
-            C2<T> xv = a.x[r0 + e];
-            C2<T> rv = mk<T>(0, 0);
-            for (int i = 0; i < jj; ++i) xv = cfma(a.V[(long)i * n + r0 + e], from_d2<T>(S.d[i]), xv);
-            for (int i = 0; i <= jj; ++i) rv = cfma(a.V[(long)i * n + r0 + e], from_d2<T>(S.rho[i]), rv);
+        for (int e = tid; e < nrows; e += nt) {
+            Z xv = a.x[r0 + e];
+            Z rv = mk<T>(0, 0);
+            for (int i = 0; i < jj; ++i) xv = cfma(a.V[(long)i * n + r0 + e], st.d[i], xv);
+            for (int i = 0; i <= jj; ++i) rv = cfma(a.V[(long)i * n + r0 + e], st.rho[i], rv);
             a.x[r0 + e] = xv;
             a.r[r0 + e] = rv;
         }
@@ -310,44 +350,63 @@ __global__ void __launch_bounds__(CO_THREADS) k_coarse_proj(CoopArgs<T> a) {
         __syncthreads();
         if (conv || cycles >= a.max_cycles) break;
     }
-    if (blockIdx.x == 0 && tid == 0) {
+    if (rank == 0 && tid == 0) {
         a.out->iters += iters;
         a.out->cycles += cycles;
         a.out->solves += 1;
         a.out->unconverged += conv ? 0 : 1;
     }
+    cluster.sync();  // no CTA leaves while others may still read its shared memory
 }
 
-template <typename T>
 struct Geometry {
-    int grid = 0, spc = 0;
+    int cluster = 1, spc = 1, threads = 32;
 };
 
 template <typename T>
-mg_status geometry(long nsite, Geometry<T>& g) {
-    static int max_active[16] = {0};
+mg_status geometry(long nsite, Geometry& g) {
+    static bool configured[2][16] = {};
     int dev = 0;
     MG_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 16) dev = 0;
-    if (max_active[dev] == 0) {
+    const int pi = std::is_same<T, float>::value ? 0 : 1;
+    if (!configured[pi][dev]) {
         MG_CUDA_TRY(cudaFuncSetAttribute(k_coarse_proj<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sizeof(CoopSmem)));
-        int per_sm = 0;
-        MG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coarse_proj<T>, CO_THREADS,
-                                                                  sizeof(CoopSmem)));
-        max_active[dev] = per_sm * sm_count();
-        if (max_active[dev] < 1) {
-            set_error("the coarse solve kernel cannot be resident");
-            return MG_ECUDA;
-        }
+                                         (int)sizeof(ClusterSmem<T>)));
+        MG_CUDA_TRY(cudaFuncSetAttribute(k_coarse_proj<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        configured[pi][dev] = true;
     }
-    // about 8 sites (192 rows) per CTA, at most one CTA per SM
-    long G = (nsite + 7) / 8;
-    G = std::min<long>(G, std::min<long>(sm_count(), max_active[dev]));
-    G = std::max<long>(G, 1);
-    g.spc = (int)((nsite + G - 1) / G);
-    g.grid = (int)((nsite + g.spc - 1) / g.spc);
-    return MG_OK;
+    // the largest cluster (<= 16 CTAs) that can be resident
+    for (int cl = 16; cl >= 1; cl >>= 1) {
+        const long spc = (nsite + cl - 1) / cl;
+        const int ctas = (int)((nsite + spc - 1) / spc);
+        const int rows = (int)spc * NDOF;
+        int threads = ((rows + 31) / 32) * 32;
+        threads = std::min(std::max(threads, 64), MAX_THREADS);
+        cudaLaunchConfig_t cfg{};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = ctas;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(ctas);
+        cfg.blockDim = dim3(threads);
+        cfg.dynamicSmemBytes = sizeof(ClusterSmem<T>);
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, k_coarse_proj<T>, &cfg) != cudaSuccess) {
+            (void)cudaGetLastError();
+            continue;
+        }
+        if (nclusters < 1) continue;
+        g.cluster = ctas;
+        g.spc = (int)spc;
+        g.threads = threads;
+        return MG_OK;
+    }
+    set_error("coarse solve: no resident cluster shape for %ld coarse sites", nsite);
+    return MG_EINVAL;
 }
 
 }  // namespace
@@ -359,16 +418,22 @@ mg_status launch_coarse_proj(const CoopArgs<T>& args_in, cudaStream_t s) {
         set_error("coarse solve: unsupported (m - k, k) = (%d, %d)", a.ms, a.k);
         return MG_EINVAL;
     }
-    Geometry<T> g;
+    Geometry g;
     MG_TRY(geometry<T>((long)a.Nx * a.Nt, g));
-    if (g.grid > a.part_ctas) {
-        set_error("coarse solve: %d CTAs exceed the partial-sum buffer (%d)", g.grid, a.part_ctas);
-        return MG_EINVAL;
-    }
     a.spc = g.spc;
-    void* params[] = {&a};
-    MG_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_coarse_proj<T>, dim3(g.grid), dim3(CO_THREADS), params,
-                                            sizeof(CoopSmem), s));
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = g.cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(g.cluster);
+    cfg.blockDim = dim3(g.threads);
+    cfg.dynamicSmemBytes = sizeof(ClusterSmem<T>);
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    MG_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_coarse_proj<T>, a));
     count_launch();
     return MG_OK;
 }
