@@ -106,16 +106,26 @@ __device__ void partial_gram(const C2<T>* X, long ldx, int nd, const C2<T>* y, l
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int ntot = nd + (norm ? 1 : 0);
     for (int i = warp; i < ntot; i += nw) {
-        C2<T> acc = mk<T>(0, 0);
-        if (i < nd) {
-            const C2<T>* xi = X + (long)i * ldx + r0;
-            for (int e = lane; e < nrows; e += 32) acc = cfmac(xi[e], y[r0 + e], acc);
-        } else {
-            for (int e = lane; e < nrows; e += 32) {
-                const C2<T> v = y[r0 + e];
-                acc.x += v.x * v.x + v.y * v.y;
+        // four independent accumulators keep four loads per lane in flight
+        C2<T> acc4[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc4[u] = mk<T>(0, 0);
+        const C2<T>* xi = (i < nd) ? X + (long)i * ldx + r0 : y + r0;
+        const C2<T>* yy = y + r0;
+        int e = lane;
+        for (; e + 96 < nrows; e += 128) {
+            C2<T> xv[4], yv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                xv[u] = xi[e + 32 * u];
+                yv[u] = yy[e + 32 * u];
             }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc4[u] = cfmac(xv[u], yv[u], acc4[u]);
         }
+        for (; e < nrows; e += 32) acc4[0] = cfmac(xi[e], yy[e], acc4[0]);
+        C2<T> acc = cadd(cadd(acc4[0], acc4[1]), cadd(acc4[2], acc4[3]));
+        if (i >= nd) acc.y = 0;  // ||y||^2 = conj(y) . y is real
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
@@ -123,6 +133,25 @@ __device__ void partial_gram(const C2<T>* X, long ldx, int nd, const C2<T>* y, l
         }
         if (lane == 0) part[i] = to_d2(acc);
     }
+}
+
+// acc +/- sum_{i < cnt} X[i][row] coef[i], loading eight rows of X at a time
+template <typename T, bool SUB>
+__device__ __forceinline__ C2<T> accum_rows(C2<T> acc, const C2<T>* X, long ldx, long row, const C2<T>* coef,
+                                            int cnt) {
+    int i = 0;
+    for (; i + 8 <= cnt; i += 8) {
+        C2<T> v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = X[(long)(i + u) * ldx + row];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc = SUB ? csub(acc, cmul(v[u], coef[i + u])) : cfma(v[u], coef[i + u], acc);
+    }
+    for (; i < cnt; ++i) {
+        const C2<T> v = X[(long)i * ldx + row];
+        acc = SUB ? csub(acc, cmul(v, coef[i])) : cfma(v, coef[i], acc);
+    }
+    return acc;
 }
 
 // Sum the partials of all CTAs of the cluster in rank order (every CTA gets the
@@ -199,8 +228,8 @@ __global__ void k_coarse_proj(CoopArgs<T> a) {
         __syncthreads();
         for (int e = tid; e < nrows; e += nt) {
             Z xv = a.x[r0 + e], rv = a.r[r0 + e];
-            for (int i = 0; i < k; ++i) xv = cfma(a.W[(long)i * n + r0 + e], st.pd[i], xv);
-            for (int i = 0; i <= k; ++i) rv = csub(rv, cmul(a.W[(long)i * n + r0 + e], st.pu[i]));
+            xv = accum_rows<T, false>(xv, a.W, n, r0 + e, st.pd, k);
+            rv = accum_rows<T, true>(rv, a.W, n, r0 + e, st.pu, k + 1);
             a.x[r0 + e] = xv;
             a.r[r0 + e] = rv;
         }
@@ -273,7 +302,7 @@ __global__ void k_coarse_proj(CoopArgs<T> a) {
             __syncthreads();
             for (int e = tid; e < nrows; e += nt) {
                 Z wv = w[r0 + e];
-                for (int i = 0; i <= j; ++i) wv = csub(wv, cmul(a.V[(long)i * n + r0 + e], S.h1[i]));
+                wv = accum_rows<T, true>(wv, a.V, n, r0 + e, S.h1, j + 1);
                 w[r0 + e] = wv;
             }
             __syncthreads();
@@ -313,7 +342,7 @@ __global__ void k_coarse_proj(CoopArgs<T> a) {
                 const T sc = S.scal[1];
                 for (int e = tid; e < nrows; e += nt) {
                     Z wv = w[r0 + e];
-                    for (int i = 0; i <= j; ++i) wv = csub(wv, cmul(a.V[(long)i * n + r0 + e], S.h2[i]));
+                    wv = accum_rows<T, true>(wv, a.V, n, r0 + e, S.h2, j + 1);
                     w[r0 + e] = cscale(wv, sc);
                 }
             }
@@ -341,8 +370,8 @@ __global__ void k_coarse_proj(CoopArgs<T> a) {
         for (int e = tid; e < nrows; e += nt) {
             Z xv = a.x[r0 + e];
             Z rv = mk<T>(0, 0);
-            for (int i = 0; i < jj; ++i) xv = cfma(a.V[(long)i * n + r0 + e], st.d[i], xv);
-            for (int i = 0; i <= jj; ++i) rv = cfma(a.V[(long)i * n + r0 + e], st.rho[i], rv);
+            xv = accum_rows<T, false>(xv, a.V, n, r0 + e, st.d, jj);
+            rv = accum_rows<T, false>(rv, a.V, n, r0 + e, st.rho, jj + 1);
             a.x[r0 + e] = xv;
             a.r[r0 + e] = rv;
         }
