@@ -10,10 +10,12 @@
 // solves (one per stream) run side by side on different clusters.
 //
 // Work split: CTA b of the cluster owns sites [b*spc, (b+1)*spc) and their 24
-// dofs.  Vectors live in global memory (L2-resident); every vector operation
-// touches only the CTA's own rows, except the stencil apply, which stages the
-// five neighbour rows of its sites (written by other CTAs before the previous
-// barrier) in shared memory through L2.
+// dofs.  When it fits, the CTA keeps its rows of the Krylov basis and of the
+// deflation space in shared memory, so the Gram and update passes never leave
+// the SM; the basis is also written to global memory (L2-resident), from where
+// the stencil apply stages the five neighbour rows of each own site (rows of
+// other CTAs, written before the previous barrier).  Neighbour indices are
+// tabulated once per launch.
 //
 // Per Arnoldi step j (CGS2, as in the rest of the library):
 //   [sync] w = A v_j; h1 = V^+ w (partials)
@@ -39,7 +41,9 @@ namespace {
 
 constexpr int NDOF = 24;
 constexpr int MAX_THREADS = 512;
-constexpr int MAX_SPC = 32;  // sites per CTA staged in shared memory
+constexpr int MAX_SPC = 32;       // sites per apply chunk (staged neighbour rows)
+constexpr int MAX_NB_SITES = 256; // sites per CTA in the neighbour table
+constexpr size_t SMEM_LIMIT = 227 * 1024;
 
 template <typename R>
 struct Small {  // per-CTA copy of the small least-squares state, precision R
@@ -54,16 +58,23 @@ struct Small {  // per-CTA copy of the small least-squares state, precision R
 
 template <typename T>
 struct ClusterSmem {
-    using R = T;
     double2 part[2][PSTR];               // this CTA's partial sums (read by the whole cluster)
     double2 red[PSTR];                   // reduced values (identical in every CTA)
     C2<T> h1[MSMAX + 1];
     C2<T> h2[MSMAX + 1];
     C2<T> xs[MAX_SPC][5][NDOF];          // staged neighbour rows
+    int nbt[MAX_NB_SITES][5];            // neighbour site of each own site and direction
     Small<T> st;
     T scal[8];
     int ctl[8];
 };
+
+// dynamic shared memory: ClusterSmem, then (optionally) the basis slice
+// Vs[(ms + 1)][rows] and the deflation slice Ws[(k + 1)][rows]
+template <typename T>
+__host__ __device__ inline size_t slice_bytes(int ms, int k, int rows) {
+    return (size_t)(ms + 1 + k + 1) * rows * sizeof(C2<T>);
+}
 
 template <typename R>
 __device__ __forceinline__ R cabs_(C2<R> a) { return sqrt(a.x * a.x + a.y * a.y); }
@@ -98,11 +109,11 @@ __device__ __forceinline__ void rot_(R c, C2<R> s, C2<R>& up, C2<R>& uq) {
     uq = csub(cscale(q, c), cmul(conj_(s), p));
 }
 
-// Partials of nd inner products conj(X[i]) . y over the CTA's rows (warp per
-// product, lanes over rows), plus optionally ||y||^2 in slot nd.
+// Partials of nd inner products conj(X[i]) . y over the CTA's rows (X, y point
+// at the own rows; warp per product, lanes over rows), plus optionally ||y||^2
+// in slot nd.
 template <typename T>
-__device__ void partial_gram(const C2<T>* X, long ldx, int nd, const C2<T>* y, long r0, int nrows, bool norm,
-                             double2* part) {
+__device__ void partial_gram(const C2<T>* X, long ldx, int nd, const C2<T>* y, int nrows, bool norm, double2* part) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int ntot = nd + (norm ? 1 : 0);
     for (int i = warp; i < ntot; i += nw) {
@@ -110,20 +121,19 @@ __device__ void partial_gram(const C2<T>* X, long ldx, int nd, const C2<T>* y, l
         C2<T> acc4[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) acc4[u] = mk<T>(0, 0);
-        const C2<T>* xi = (i < nd) ? X + (long)i * ldx + r0 : y + r0;
-        const C2<T>* yy = y + r0;
+        const C2<T>* xi = (i < nd) ? X + (long)i * ldx : y;
         int e = lane;
         for (; e + 96 < nrows; e += 128) {
             C2<T> xv[4], yv[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 xv[u] = xi[e + 32 * u];
-                yv[u] = yy[e + 32 * u];
+                yv[u] = y[e + 32 * u];
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) acc4[u] = cfmac(xv[u], yv[u], acc4[u]);
         }
-        for (; e < nrows; e += 32) acc4[0] = cfmac(xi[e], yy[e], acc4[0]);
+        for (; e < nrows; e += 32) acc4[0] = cfmac(xi[e], y[e], acc4[0]);
         C2<T> acc = cadd(cadd(acc4[0], acc4[1]), cadd(acc4[2], acc4[3]));
         if (i >= nd) acc.y = 0;  // ||y||^2 = conj(y) . y is real
 #pragma unroll
@@ -135,20 +145,20 @@ __device__ void partial_gram(const C2<T>* X, long ldx, int nd, const C2<T>* y, l
     }
 }
 
-// acc +/- sum_{i < cnt} X[i][row] coef[i], loading eight rows of X at a time
+// acc +/- sum_{i < cnt} X[i][e] coef[i], loading eight rows of X at a time
 template <typename T, bool SUB>
-__device__ __forceinline__ C2<T> accum_rows(C2<T> acc, const C2<T>* X, long ldx, long row, const C2<T>* coef,
+__device__ __forceinline__ C2<T> accum_rows(C2<T> acc, const C2<T>* X, long ldx, int e, const C2<T>* coef,
                                             int cnt) {
     int i = 0;
     for (; i + 8 <= cnt; i += 8) {
         C2<T> v[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = X[(long)(i + u) * ldx + row];
+        for (int u = 0; u < 8; ++u) v[u] = X[(long)(i + u) * ldx + e];
 #pragma unroll
         for (int u = 0; u < 8; ++u) acc = SUB ? csub(acc, cmul(v[u], coef[i + u])) : cfma(v[u], coef[i + u], acc);
     }
     for (; i < cnt; ++i) {
-        const C2<T> v = X[(long)i * ldx + row];
+        const C2<T> v = X[(long)i * ldx + e];
         acc = SUB ? csub(acc, cmul(v, coef[i])) : cfma(v, coef[i], acc);
     }
     return acc;
@@ -172,6 +182,15 @@ __device__ void reduce_partials(cg::cluster_group& cluster, double2* part, int n
     __syncthreads();
 }
 
+__device__ __forceinline__ long nbr_site(long s, int d, int Nx, int Nt) {
+    const int xx = (int)(s % Nx), tt = (int)(s / Nx);
+    if (d == 1) return (xx + 1 == Nx) ? s - xx : s + 1;
+    if (d == 2) return (xx == 0) ? s + Nx - 1 : s - 1;
+    if (d == 3) return (tt + 1 == Nt) ? (long)xx : s + Nx;
+    if (d == 4) return (tt == 0) ? s + (long)Nx * (Nt - 1) : s - Nx;
+    return s;
+}
+
 template <typename T>
 __global__ void k_coarse_proj(CoopArgs<T> a) {
     using Z = C2<T>;
@@ -190,14 +209,40 @@ __global__ void k_coarse_proj(CoopArgs<T> a) {
     const int nrows = my_sites * NDOF;
     const int k = a.k, ms = a.ms;
     const int LD = MSMAX + 1;
+    const bool table = my_sites <= MAX_NB_SITES;
 
+    // own rows of the basis and of the deflation space: shared memory when it fits
+    Z* Vl;
+    const Z* Wl;
+    long ldv, ldw;
+    if (a.vs) {
+        const int rows_cap = a.spc * NDOF;
+        Z* Vs = reinterpret_cast<Z*>(smem_raw + sizeof(ClusterSmem<T>));
+        Z* Ws = Vs + (long)(ms + 1) * rows_cap;
+        for (int e = tid; e < (k + 1) * nrows; e += nt) {
+            const int i = e / nrows, rr = e - i * nrows;
+            Ws[(long)i * rows_cap + rr] = a.W[(long)i * n + r0 + rr];
+        }
+        Vl = Vs;
+        Wl = Ws;
+        ldv = ldw = rows_cap;
+    } else {
+        Vl = a.V + r0;
+        Wl = a.W + r0;
+        ldv = ldw = n;
+    }
+    if (table)
+        for (int e = tid; e < my_sites * 5; e += nt) S.nbt[e / 5][e % 5] = (int)nbr_site(s0 + e / 5, e % 5, a.Nx, a.Nt);
+
+    Z* xl = a.x + r0;
+    Z* rl = a.r + r0;
     // x = 0, r = f, ||f||^2
     for (int e = tid; e < nrows; e += nt) {
-        a.x[r0 + e] = mk<T>(0, 0);
-        a.r[r0 + e] = a.f[r0 + e];
+        xl[e] = mk<T>(0, 0);
+        rl[e] = a.f[r0 + e];
     }
     __syncthreads();
-    partial_gram<T>(a.r, 0, 0, a.r, r0, nrows, true, S.part[0]);
+    partial_gram<T>(rl, 0, 0, rl, nrows, true, S.part[0]);
     cluster.sync();
     reduce_partials(cluster, S.part[0], 1, S.red);
     const double nb = sqrt(fmax(S.red[0].x, 0.0));
@@ -205,7 +250,7 @@ __global__ void k_coarse_proj(CoopArgs<T> a) {
     int iters = 0, cycles = 0, conv = 0;
     while (true) {
         // ---- projection onto the deflation space: d = argmin ||W^+ r - H_k d|| ----
-        partial_gram<T>(a.W, n, k + 1, a.r, r0, nrows, false, S.part[1]);
+        partial_gram<T>(Wl, ldw, k + 1, rl, nrows, false, S.part[1]);
         cluster.sync();
         reduce_partials(cluster, S.part[1], k + 1, S.red);
         if (tid == 0) {
@@ -227,14 +272,11 @@ __global__ void k_coarse_proj(CoopArgs<T> a) {
         }
         __syncthreads();
         for (int e = tid; e < nrows; e += nt) {
-            Z xv = a.x[r0 + e], rv = a.r[r0 + e];
-            xv = accum_rows<T, false>(xv, a.W, n, r0 + e, st.pd, k);
-            rv = accum_rows<T, true>(rv, a.W, n, r0 + e, st.pu, k + 1);
-            a.x[r0 + e] = xv;
-            a.r[r0 + e] = rv;
+            xl[e] = accum_rows<T, false>(xl[e], Wl, ldw, e, st.pd, k);
+            rl[e] = accum_rows<T, true>(rl[e], Wl, ldw, e, st.pu, k + 1);
         }
         __syncthreads();
-        partial_gram<T>(a.r, 0, 0, a.r, r0, nrows, true, S.part[0]);
+        partial_gram<T>(rl, 0, 0, rl, nrows, true, S.part[0]);
         cluster.sync();
         reduce_partials(cluster, S.part[0], 1, S.red);
         const double beta = sqrt(fmax(S.red[0].x, 0.0));
@@ -258,26 +300,24 @@ __global__ void k_coarse_proj(CoopArgs<T> a) {
         __syncthreads();
         {
             const T sc = S.scal[0];
-            for (int e = tid; e < nrows; e += nt) a.V[r0 + e] = cscale(a.r[r0 + e], sc);
+            for (int e = tid; e < nrows; e += nt) {
+                const Z v = cscale(rl[e], sc);
+                Vl[e] = v;
+                if (a.vs) a.V[r0 + e] = v;
+            }
         }
         int j = 0, stop = 0;
         for (; j < ms && !stop; ++j) {
             cluster.sync();  // v_j complete in every CTA
             const Z* vj = a.V + (long)j * n;
-            Z* w = a.V + (long)(j + 1) * n;
+            Z* wl = Vl + (long)(j + 1) * ldv;
             // w = A v_j on the CTA's rows (column-major 24x24 blocks), MAX_SPC sites at a
             // time: stage the five neighbour rows of each site (other CTAs' rows: through L2)
             for (int c0 = 0; c0 < my_sites; c0 += MAX_SPC) {
                 const int cs = min(MAX_SPC, my_sites - c0);
                 for (int e = tid; e < cs * 5 * NDOF; e += nt) {
                     const int ls = e / (5 * NDOF), rem = e - ls * 5 * NDOF, d = rem / NDOF, l = rem - d * NDOF;
-                    const long s = s0 + c0 + ls;
-                    const int xx = (int)(s % a.Nx), tt = (int)(s / a.Nx);
-                    long nbs = s;
-                    if (d == 1) nbs = (xx + 1 == a.Nx) ? s - xx : s + 1;
-                    if (d == 2) nbs = (xx == 0) ? s + a.Nx - 1 : s - 1;
-                    if (d == 3) nbs = (tt + 1 == a.Nt) ? (long)xx : s + a.Nx;
-                    if (d == 4) nbs = (tt == 0) ? s + (long)a.Nx * (a.Nt - 1) : s - a.Nx;
+                    const long nbs = table ? (long)S.nbt[c0 + ls][d] : nbr_site(s0 + c0 + ls, d, a.Nx, a.Nt);
                     S.xs[ls][d][l] = __ldcg(vj + nbs * NDOF + l);
                 }
                 __syncthreads();
@@ -291,22 +331,18 @@ __global__ void k_coarse_proj(CoopArgs<T> a) {
                         for (int l = 0; l < NDOF; ++l)
                             acc = cfma(__ldg(Ab + (d * NDOF + l) * NDOF), S.xs[ls][d][l], acc);
                     }
-                    w[r0 + (long)c0 * NDOF + e] = acc;
+                    wl[(long)c0 * NDOF + e] = acc;
                 }
                 __syncthreads();
             }
-            partial_gram<T>(a.V, n, j + 1, w, r0, nrows, false, S.part[1]);
+            partial_gram<T>(Vl, ldv, j + 1, wl, nrows, false, S.part[1]);
             cluster.sync();
             reduce_partials(cluster, S.part[1], j + 1, S.red);
             for (int i = tid; i <= j; i += nt) S.h1[i] = from_d2<T>(S.red[i]);
             __syncthreads();
-            for (int e = tid; e < nrows; e += nt) {
-                Z wv = w[r0 + e];
-                wv = accum_rows<T, true>(wv, a.V, n, r0 + e, S.h1, j + 1);
-                w[r0 + e] = wv;
-            }
+            for (int e = tid; e < nrows; e += nt) wl[e] = accum_rows<T, true>(wl[e], Vl, ldv, e, S.h1, j + 1);
             __syncthreads();
-            partial_gram<T>(a.V, n, j + 1, w, r0, nrows, true, S.part[0]);
+            partial_gram<T>(Vl, ldv, j + 1, wl, nrows, true, S.part[0]);
             cluster.sync();
             reduce_partials(cluster, S.part[0], j + 2, S.red);
             for (int i = tid; i <= j; i += nt) S.h2[i] = from_d2<T>(S.red[i]);
@@ -340,10 +376,11 @@ __global__ void k_coarse_proj(CoopArgs<T> a) {
             __syncthreads();
             {
                 const T sc = S.scal[1];
+                Z* wg = a.V + (long)(j + 1) * n + r0;
                 for (int e = tid; e < nrows; e += nt) {
-                    Z wv = w[r0 + e];
-                    wv = accum_rows<T, true>(wv, a.V, n, r0 + e, S.h2, j + 1);
-                    w[r0 + e] = cscale(wv, sc);
+                    const Z v = cscale(accum_rows<T, true>(wl[e], Vl, ldv, e, S.h2, j + 1), sc);
+                    wl[e] = v;
+                    if (a.vs) wg[e] = v;
                 }
             }
             ++iters;
@@ -368,12 +405,8 @@ __global__ void k_coarse_proj(CoopArgs<T> a) {
         }
         __syncthreads();
         for (int e = tid; e < nrows; e += nt) {
-            Z xv = a.x[r0 + e];
-            Z rv = mk<T>(0, 0);
-            xv = accum_rows<T, false>(xv, a.V, n, r0 + e, st.d, jj);
-            rv = accum_rows<T, false>(rv, a.V, n, r0 + e, st.rho, jj + 1);
-            a.x[r0 + e] = xv;
-            a.r[r0 + e] = rv;
+            xl[e] = accum_rows<T, false>(xl[e], Vl, ldv, e, st.d, jj);
+            rl[e] = accum_rows<T, false>(mk<T>(0, 0), Vl, ldv, e, st.rho, jj + 1);
         }
         ++cycles;
         __syncthreads();
@@ -389,11 +422,12 @@ __global__ void k_coarse_proj(CoopArgs<T> a) {
 }
 
 struct Geometry {
-    int cluster = 1, spc = 1, threads = 32;
+    int cluster = 1, spc = 1, threads = 32, vs = 0;
+    size_t smem = 0;
 };
 
 template <typename T>
-mg_status geometry(long nsite, Geometry& g) {
+mg_status geometry(long nsite, int ms, int k, Geometry& g) {
     static bool configured[2][16] = {};
     int dev = 0;
     MG_CUDA_TRY(cudaGetDevice(&dev));
@@ -401,38 +435,45 @@ mg_status geometry(long nsite, Geometry& g) {
     const int pi = std::is_same<T, float>::value ? 0 : 1;
     if (!configured[pi][dev]) {
         MG_CUDA_TRY(cudaFuncSetAttribute(k_coarse_proj<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sizeof(ClusterSmem<T>)));
+                                         (int)SMEM_LIMIT));
         MG_CUDA_TRY(cudaFuncSetAttribute(k_coarse_proj<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
         configured[pi][dev] = true;
     }
-    // the largest cluster (<= 16 CTAs) that can be resident
+    // the largest cluster (<= 16 CTAs) that can be resident; the basis slice in
+    // shared memory when it fits
     for (int cl = 16; cl >= 1; cl >>= 1) {
         const long spc = (nsite + cl - 1) / cl;
         const int ctas = (int)((nsite + spc - 1) / spc);
         const int rows = (int)spc * NDOF;
         int threads = ((rows + 31) / 32) * 32;
         threads = std::min(std::max(threads, 64), MAX_THREADS);
-        cudaLaunchConfig_t cfg{};
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = ctas;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.gridDim = dim3(ctas);
-        cfg.blockDim = dim3(threads);
-        cfg.dynamicSmemBytes = sizeof(ClusterSmem<T>);
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        int nclusters = 0;
-        if (cudaOccupancyMaxActiveClusters(&nclusters, k_coarse_proj<T>, &cfg) != cudaSuccess) {
-            (void)cudaGetLastError();
-            continue;
+        for (int vs = 1; vs >= 0; --vs) {
+            const size_t smem = sizeof(ClusterSmem<T>) + (vs ? slice_bytes<T>(ms, k, rows) : 0);
+            if (smem > SMEM_LIMIT) continue;
+            cudaLaunchConfig_t cfg{};
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = ctas;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.gridDim = dim3(ctas);
+            cfg.blockDim = dim3(threads);
+            cfg.dynamicSmemBytes = smem;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            int nclusters = 0;
+            if (cudaOccupancyMaxActiveClusters(&nclusters, k_coarse_proj<T>, &cfg) != cudaSuccess) {
+                (void)cudaGetLastError();
+                continue;
+            }
+            if (nclusters < 1) continue;
+            g.cluster = ctas;
+            g.spc = (int)spc;
+            g.threads = threads;
+            g.vs = vs;
+            g.smem = smem;
+            return MG_OK;
         }
-        if (nclusters < 1) continue;
-        g.cluster = ctas;
-        g.spc = (int)spc;
-        g.threads = threads;
-        return MG_OK;
     }
     set_error("coarse solve: no resident cluster shape for %ld coarse sites", nsite);
     return MG_EINVAL;
@@ -448,8 +489,9 @@ mg_status launch_coarse_proj(const CoopArgs<T>& args_in, cudaStream_t s) {
         return MG_EINVAL;
     }
     Geometry g;
-    MG_TRY(geometry<T>((long)a.Nx * a.Nt, g));
+    MG_TRY(geometry<T>((long)a.Nx * a.Nt, a.ms, a.k, g));
     a.spc = g.spc;
+    a.vs = g.vs;
     cudaLaunchConfig_t cfg{};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -458,7 +500,7 @@ mg_status launch_coarse_proj(const CoopArgs<T>& args_in, cudaStream_t s) {
     attr[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3(g.cluster);
     cfg.blockDim = dim3(g.threads);
-    cfg.dynamicSmemBytes = sizeof(ClusterSmem<T>);
+    cfg.dynamicSmemBytes = g.smem;
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 1;

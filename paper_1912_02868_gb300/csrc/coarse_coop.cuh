@@ -29,6 +29,7 @@ struct CoopArgs {
     int part_ctas;
     CoopStats* out;
     int spc;           // sites per CTA (set by the launcher)
+    int vs;            // 1: own basis rows kept in shared memory (set by the launcher)
 };
 
 template <typename T>
