@@ -75,6 +75,10 @@ typedef struct {
     int precision;         /* MG_FP64 or MG_MIXED */
     unsigned long long seed; /* start vectors of the near-null solves when none are given */
     int method;            /* MG_METHOD_MG (default) or MG_METHOD_FINE_DEFLATION */
+    int parallel;          /* right-hand sides of one mg_solve solved concurrently (1):
+                              with > 1, the first right-hand side of a handle builds the
+                              deflation space alone, then up to `parallel` solve contexts
+                              (shared hierarchy, own workspaces and streams) share the rest */
 } mg_params;
 
 /* solver of mg_solve (Section 2 compares both) */
@@ -201,6 +205,60 @@ mg_status mg_level_shape(mg_handle h, int level, int* n_x, int* n_t, int* dof);
  */
 mg_status mg_wilson_apply(const void* gauge, int L_x, int L_t, double m0, int dagger, int precision,
                           const void* x, void* y, void* stream);
+
+/* ------------------------------------------------------------------------- */
+/* Serving: continuous batching of solve requests over many operators        */
+/* (the serving pattern layered on the method; the paper has no serving).    */
+/* ------------------------------------------------------------------------- */
+
+typedef struct mg_server_s* mg_server;
+
+typedef struct {
+    unsigned long long key;   /* caller's name of the operator (gauge field, m0, lattice) */
+    const void* gauge;        /* host or device, complex128[L_t][L_x][2]; read only when
+                                 `key` is not resident; valid until the request completes */
+    int L_x, L_t;
+    double m0;
+    const void* starts0;      /* optional near-null start vectors as in mg_setup (NULL: seed) */
+    const void* starts1;
+    const void* b;            /* host or device, complex128[nrhs][L_t][L_x][2] */
+    void* x;                  /* host or device, same shape; output */
+    int nrhs;                 /* >= 1 */
+    double tol;               /* true relative residual per right-hand side */
+} mg_request;
+
+typedef struct {
+    int resident_keys;              /* operators whose hierarchy is in HBM */
+    unsigned long long device_bytes;/* device bytes held by resident hierarchies and contexts */
+    long long evictions;            /* hierarchies dropped to admit others */
+    long long cold_starts;          /* hierarchies built */
+    long long completed;            /* requests finished */
+    long long queued_items;         /* right-hand sides waiting for a worker */
+} mg_server_info;
+
+/*
+ * Create a server with `workers` host threads on the current device.  Every
+ * right-hand side of every request is one work item; items run in arrival order
+ * on solve contexts (own workspaces and CUDA stream) of their key's hierarchy,
+ * so requests of different keys and lattice sizes overlap on the GPU and new
+ * requests join as soon as a worker is free.  A key's hierarchy is built on its
+ * first request (mg_setup with `p`), and its coarse deflation space by one solve
+ * of a fixed seeded right-hand side, so results do not depend on which requests
+ * came first.  Hierarchies stay resident (LRU) while the estimated device bytes
+ * stay within hbm_budget_bytes (0 = unlimited); a new key waits until an idle
+ * hierarchy can be evicted.
+ */
+mg_status mg_server_create(const mg_params* p, unsigned long long hbm_budget_bytes, int workers,
+                           mg_server* out);
+/* Queue a request; *ticket identifies it for mg_server_wait. */
+mg_status mg_server_submit(mg_server s, const mg_request* r, unsigned long long* ticket);
+/* Block until the request is done.  iters/relres: host [nrhs] or NULL;
+ * latency_s: host or NULL, seconds from submission to completion. */
+mg_status mg_server_wait(mg_server s, unsigned long long ticket, int* iters, double* relres,
+                         double* latency_s);
+mg_status mg_server_stats(mg_server s, mg_server_info* out);
+/* Stop the workers (queued items are dropped) and free every hierarchy. */
+mg_status mg_server_destroy(mg_server s);
 
 /* ------------------------------------------------------------------------- */
 /* Instrumentation                                                           */

@@ -81,8 +81,10 @@ def main(argv):
             table["entries"][f"{int(L)}:{c}"] = e
             print(f"L={L} c={c} m0={e['m0']:.12f} lam=({e['lambda_min_re']:.6f},{e['lambda_min_im']:.2e}) "
                   f"min|lam|={e['min_abs_eig']:.3e} ({time.time() - t0:.1f}s)", flush=True)
-            with open(path, "w") as f:
+            tmp = path + f".{os.getpid()}.tmp"
+            with open(tmp, "w") as f:
                 json.dump(table, f, indent=1, sort_keys=True)
+            os.replace(tmp, path)  # readers never see a half-written table
 
 
 if __name__ == "__main__":

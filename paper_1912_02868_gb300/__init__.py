@@ -200,3 +200,56 @@ def mg_timing_read(h: Handle, level):
 
 def mg_kernel_launches() -> int:
     return int(load().mg_kernel_launches())
+
+
+class Server:
+    """Continuous-batching solve server (mg_server_*): requests over many operators
+    (keys) share the GPU; hierarchies are cached under an HBM byte budget."""
+
+    def __init__(self, params=None, hbm_budget_bytes=0, workers=8):
+        self.params = params or default_params()
+        out = ctypes.c_void_p()
+        _lib.check(load().mg_server_create(ctypes.byref(self.params), int(hbm_budget_bytes), int(workers),
+                                           ctypes.byref(out)), "mg_server_create")
+        self.ptr = out.value
+        self._keep = {}
+
+    def submit(self, key, gauge, Lx, Lt, m0, b, x, nrhs, tol, starts0=None, starts1=None) -> int:
+        r = _lib.MGRequest(key=int(key), gauge=_ptr(gauge), L_x=Lx, L_t=Lt, m0=float(m0), starts0=_ptr(starts0),
+                           starts1=_ptr(starts1), b=_ptr(b), x=_ptr(x), nrhs=int(nrhs), tol=float(tol))
+        t = ctypes.c_ulonglong()
+        _lib.check(load().mg_server_submit(self.ptr, ctypes.byref(r), ctypes.byref(t)), "mg_server_submit")
+        self._keep[t.value] = (gauge, b, x, starts0, starts1)  # the arrays must outlive the request
+        return t.value
+
+    def wait(self, ticket, nrhs, allow_notconv=False):
+        """(status, iters[nrhs], relres[nrhs], latency seconds)"""
+        it = (ctypes.c_int * nrhs)()
+        rr = (ctypes.c_double * nrhs)()
+        lat = ctypes.c_double()
+        st = load().mg_server_wait(self.ptr, int(ticket), it, rr, ctypes.byref(lat))
+        self._keep.pop(ticket, None)
+        _lib.check(st, "mg_server_wait", allow=(MG_OK, MG_ENOTCONV) if allow_notconv else (MG_OK,))
+        return st, list(it), list(rr), lat.value
+
+    def stats(self) -> dict:
+        info = _lib.MGServerInfo()
+        _lib.check(load().mg_server_stats(self.ptr, ctypes.byref(info)), "mg_server_stats")
+        return {f: getattr(info, f) for f, _ in info._fields_}
+
+    def close(self):
+        if self.ptr:
+            load().mg_server_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -30,7 +30,7 @@ class MGParams(ctypes.Structure):
         ("cgne_max_iters", ctypes.c_int), ("nullvec_max_iters", ctypes.c_int),
         ("nullvec_tol", ctypes.c_double), ("coarse_tol_first", ctypes.c_double),
         ("coarse_tol_rest", ctypes.c_double), ("precision", ctypes.c_int), ("seed", ctypes.c_ulonglong),
-        ("method", ctypes.c_int),
+        ("method", ctypes.c_int), ("parallel", ctypes.c_int),
     ]
 
 
@@ -41,13 +41,29 @@ class MGSolveStats(ctypes.Structure):
     ]
 
 
+class MGRequest(ctypes.Structure):
+    _fields_ = [
+        ("key", ctypes.c_ulonglong), ("gauge", ctypes.c_void_p), ("L_x", ctypes.c_int), ("L_t", ctypes.c_int),
+        ("m0", ctypes.c_double), ("starts0", ctypes.c_void_p), ("starts1", ctypes.c_void_p),
+        ("b", ctypes.c_void_p), ("x", ctypes.c_void_p), ("nrhs", ctypes.c_int), ("tol", ctypes.c_double),
+    ]
+
+
+class MGServerInfo(ctypes.Structure):
+    _fields_ = [
+        ("resident_keys", ctypes.c_int), ("device_bytes", ctypes.c_ulonglong), ("evictions", ctypes.c_longlong),
+        ("cold_starts", ctypes.c_longlong), ("completed", ctypes.c_longlong), ("queued_items", ctypes.c_longlong),
+    ]
+
+
 _lib = None
 
 # every symbol declared in include/mg.h
 SYMBOLS = ("mg_default_params", "mg_setup", "mg_setup_from_vectors", "mg_solve", "mg_reset_deflation",
            "mg_destroy", "mg_last_error", "mg_apply", "mg_restrict", "mg_prolong", "mg_get_stencil",
            "mg_get_prolongator", "mg_get_deflation", "mg_level_shape", "mg_wilson_apply",
-           "mg_timing_enable", "mg_timing_read", "mg_kernel_launches")
+           "mg_timing_enable", "mg_timing_read", "mg_kernel_launches", "mg_server_create", "mg_server_submit",
+           "mg_server_wait", "mg_server_stats", "mg_server_destroy")
 
 
 def load(path: str | None = None) -> ctypes.CDLL:
@@ -79,6 +95,11 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "mg_timing_enable": (i, [vp, i, i]),
         "mg_timing_read": (i, [vp, i, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong)]),
         "mg_kernel_launches": (ctypes.c_ulonglong, []),
+        "mg_server_create": (i, [ctypes.POINTER(MGParams), ctypes.c_ulonglong, i, ctypes.POINTER(vp)]),
+        "mg_server_submit": (i, [vp, ctypes.POINTER(MGRequest), ctypes.POINTER(ctypes.c_ulonglong)]),
+        "mg_server_wait": (i, [vp, ctypes.c_ulonglong, ctypes.POINTER(i), ctypes.POINTER(d), ctypes.POINTER(d)]),
+        "mg_server_stats": (i, [vp, ctypes.POINTER(MGServerInfo)]),
+        "mg_server_destroy": (i, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

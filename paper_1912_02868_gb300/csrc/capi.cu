@@ -6,7 +6,9 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
+#include <algorithm>
 
 #include "handle.cuh"
 
@@ -48,6 +50,7 @@ mg_status halloc(Handle& H, void** p, size_t bytes) {
         return MG_ENOMEM;
     }
     H.allocs.push_back(*p);
+    H.bytes += bytes;
     return MG_OK;
 }
 
@@ -56,6 +59,13 @@ template <typename T> mg_status vcycle_entry(Handle& H, const C2<T>* f, C2<T>* x
 namespace {
 
 void free_handle(Handle& H) {
+    for (mg_handle_s* c : H.contexts) {
+        free_handle(c->h);
+        delete c;
+    }
+    H.contexts.clear();
+    if (H.own_stream) cudaStreamDestroy(H.own_stream);
+    H.own_stream = nullptr;
     for (auto& t : H.timers) {
         for (cudaEvent_t e : t.ev) cudaEventDestroy(e);
         t.ev.clear();
@@ -111,15 +121,168 @@ mg_status alloc_level(Handle& H, Level<T>& L, int steps) {
 }
 
 template <typename T>
-mg_status alloc_coarse(Handle& H, CoarseWS<T>& W, long n, int m, int k) {
+mg_status alloc_coarse(Handle& H, CoarseWS<T>& W, long n, int m, int k, bool own_defl) {
     MG_TRY(halloc_t(H, &W.V, (size_t)(m + 1) * n));
     MG_TRY(halloc_t(H, &W.V2, (size_t)(m + 1) * n));
     MG_TRY(halloc_t(H, &W.r, (size_t)n));
     MG_TRY(halloc_t(H, &W.p, (size_t)n));
     MG_TRY(halloc_t(H, &W.q, (size_t)n));
     MG_TRY(halloc_t(H, &W.t, (size_t)n));
-    MG_TRY(halloc_t(H, &W.W, (size_t)(k + 1) * n));
+    if (own_defl) MG_TRY(halloc_t(H, &W.W, (size_t)(k + 1) * n));
     MG_TRY(halloc_t(H, &W.ks, 1));
+    return MG_OK;
+}
+
+// Every buffer a solve writes.  The owner of a hierarchy also holds the
+// deflation spaces; a context made by make_context shares them.
+mg_status alloc_workspaces(Handle& H, cudaStream_t s, bool owner) {
+    const mg_params& p = H.p;
+    const long n0 = H.L64[0].n, n2 = H.L64[2].n;
+    H.red.max_blocks = 2 * sm_count();
+    MG_TRY(halloc_t(H, &H.red.partial, (size_t)H.red.max_blocks * RED_MAXD));
+    MG_TRY(halloc_t(H, &H.red.ticket, 1));
+    MG_TRY(halloc_t(H, &H.sc, 1));
+    MG_CUDA_TRY(cudaMemsetAsync(H.red.ticket, 0, sizeof(unsigned), s));
+    MG_CUDA_TRY(cudaMemsetAsync(H.sc, 0, sizeof(Scalars), s));
+    for (int l = 0; l < 3; ++l) {
+        MG_TRY(alloc_level(H, H.L64[l], p.smooth_steps));
+        MG_TRY(alloc_level(H, H.L32[l], p.smooth_steps));
+    }
+    MG_TRY(alloc_coarse(H, H.c64, n2, p.dr_m, p.dr_m, owner));
+    MG_TRY(alloc_coarse(H, H.c32, n2, p.dr_m, p.dr_m, owner));
+    MG_TRY(halloc_t(H, &H.fV, (size_t)(p.fgmres_m + 1) * n0));
+    MG_TRY(halloc_t(H, &H.fZ, (size_t)p.fgmres_m * n0));
+    MG_TRY(halloc_t(H, &H.fx, (size_t)n0));
+    MG_TRY(halloc_t(H, &H.fr, (size_t)n0));
+    MG_TRY(halloc_t(H, &H.fb, (size_t)n0));
+    MG_TRY(halloc_t(H, &H.v32, (size_t)n0));
+    MG_TRY(halloc_t(H, &H.z32, (size_t)n0));
+    MG_TRY(halloc_t(H, &H.fks, 1));
+    MG_TRY(halloc_t(H, &H.cvec, KLD));
+    MG_TRY(halloc_t(H, &H.dvec, KLD));
+    MG_TRY(halloc_t(H, &H.uvec, KLD));
+    MG_TRY(halloc_t(H, &H.dr, 1));
+    if (owner) MG_TRY(halloc_t(H, &H.pls, 1));
+    H.cpart_ctas = sm_count();
+    MG_TRY(halloc_t(H, &H.cpart, (size_t)2 * H.cpart_ctas * PSTR));
+    MG_TRY(halloc_t(H, &H.cstats, 1));
+    if (p.method == MG_METHOD_FINE_DEFLATION) {
+        MG_TRY(halloc_t(H, &H.fdV, (size_t)(p.dr_m + 1) * n0));
+        MG_TRY(halloc_t(H, &H.fdV2, (size_t)(p.dr_m + 1) * n0));
+        MG_TRY(halloc_t(H, &H.fdks, 1));
+        if (owner) {
+            MG_TRY(halloc_t(H, &H.fdW, (size_t)(p.dr_m + 1) * n0));
+            MG_TRY(halloc_t(H, &H.fdpls, 1));
+        }
+    }
+    return MG_OK;
+}
+
+// Solve right-hand sides i = i0, i0 + step, ... < i1 on handle (or context) H and
+// stream s; counters accumulate in H.st.  Returns MG_ENOTCONV when one of them
+// reached the iteration limit.
+mg_status solve_rhs(Handle& H, const double2* B, double2* X, bool bdev, bool xdev, int i0, int i1, int step,
+                    double tol, cudaStream_t s, int* iters, double* relres) {
+    const long n0 = H.L64[0].n;
+    if (H.is_context) {
+        const bool needs = H.p.method == MG_METHOD_FINE_DEFLATION || H.p.coarse_solver == MG_COARSE_DR_PROJ;
+        const int k = H.p.method == MG_METHOD_FINE_DEFLATION ? H.fine_k : H.defl_k;
+        if (needs && k == 0) return set_error("a solve context cannot build the deflation space"), MG_EINVAL;
+    }
+    MG_CUDA_TRY(cudaMemsetAsync(H.cstats, 0, sizeof(CoopStats), s));
+    mg_status result = MG_OK;
+    for (int i = i0; i < i1; i += step) {
+        const double2* bi = B + (long)i * n0;
+        double2* xi = X + (long)i * n0;
+        const double2* bsrc = bi;
+        double2* xdst = xi;
+        if (!bdev) {
+            MG_CUDA_TRY(cudaMemcpyAsync(H.fb, bi, n0 * sizeof(double2), cudaMemcpyHostToDevice, s));
+            bsrc = H.fb;
+        }
+        if (!xdev) xdst = H.fx;
+        int it = 0;
+        double rr = 0.0;
+        bool conv = false;
+        if (H.p.method == MG_METHOD_FINE_DEFLATION)
+            MG_TRY(fine_deflated_solve(H, bsrc, xdst, tol, s, &it, &rr, &conv));
+        else
+            MG_TRY(fgmres_solve(H, bsrc, xdst, tol, s, &it, &rr, &conv));
+        if (!xdev) MG_CUDA_TRY(cudaMemcpyAsync(xi, H.fx, n0 * sizeof(double2), cudaMemcpyDeviceToHost, s));
+        if (iters) iters[i] = it;
+        if (relres) relres[i] = rr;
+        if (!conv) result = MG_ENOTCONV;
+    }
+    CoopStats cs{};
+    MG_CUDA_TRY(cudaMemcpyAsync(H.pinned, H.cstats, sizeof(CoopStats), cudaMemcpyDeviceToHost, s));
+    MG_CUDA_TRY(cudaStreamSynchronize(s));
+    std::memcpy(&cs, H.pinned, sizeof cs);
+    H.st.coarse_iters += cs.iters;
+    H.st.mvps[2] += cs.iters;
+    return result;
+}
+
+// A solve context of hierarchy P: the same (read-only) hierarchy and deflation
+// spaces, its own workspaces and stream, so that right-hand sides can be solved
+// concurrently.  Requires the deflation space of P to exist.
+mg_status make_context(Handle& P, mg_handle_s** out) {
+    *out = nullptr;
+    mg_handle_s* cs = new (std::nothrow) mg_handle_s();
+    if (!cs) return set_error("out of host memory"), MG_ENOMEM;
+    Handle& C = cs->h;
+    C.Lx = P.Lx;
+    C.Lt = P.Lt;
+    C.m0 = P.m0;
+    C.p = P.p;
+    C.is_context = true;
+    for (int l = 0; l < 3; ++l) {
+        C.L64[l] = P.L64[l];
+        C.L32[l] = P.L32[l];
+        C.L64[l].timer = C.L32[l].timer = &C.timers[l];
+    }
+    C.U64 = P.U64;
+    C.U32 = P.U32;
+    for (int l = 0; l < 3; ++l) {
+        C.A64[l] = P.A64[l];
+        C.A32[l] = P.A32[l];
+    }
+    for (int l = 0; l < 2; ++l) {
+        C.Q64[l] = P.Q64[l];
+        C.Q32[l] = P.Q32[l];
+    }
+    C.c64.W = P.c64.W;
+    C.c32.W = P.c32.W;
+    C.pls = P.pls;
+    C.defl_k = P.defl_k;
+    C.fdW = P.fdW;
+    C.fdpls = P.fdpls;
+    C.fine_k = P.fine_k;
+    auto fail = [&](mg_status st) {
+        for (void* q : C.allocs) cudaFree(q);
+        if (C.pinned) cudaFreeHost(C.pinned);
+        if (C.own_stream) cudaStreamDestroy(C.own_stream);
+        delete cs;
+        return st;
+    };
+    if (cudaMallocHost(&C.pinned, 1 << 16) != cudaSuccess) {
+        (void)cudaGetLastError();
+        C.pinned = nullptr;
+        set_error("cudaMallocHost failed");
+        return fail(MG_ENOMEM);
+    }
+    if (cudaStreamCreateWithFlags(&C.own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        (void)cudaGetLastError();
+        C.own_stream = nullptr;
+        set_error("cudaStreamCreate failed");
+        return fail(MG_ECUDA);
+    }
+    mg_status st = alloc_workspaces(C, C.own_stream, false);
+    if (st != MG_OK) return fail(st);
+    if (cudaStreamSynchronize(C.own_stream) != cudaSuccess) {
+        set_error("context set-up failed");
+        return fail(MG_ECUDA);
+    }
+    *out = cs;
     return MG_OK;
 }
 
@@ -189,23 +352,13 @@ mg_status setup_common(const void* gauge, int Lx, int Lt, double m0, int nvec, i
         H.L64[l].m0 = H.L32[l].m0 = m0;
         H.L64[l].timer = H.L32[l].timer = &H.timers[l];
     }
-    const long n0 = H.L64[0].n, n2 = H.L64[2].n;
+    const long n0 = H.L64[0].n;
     mg_status st;
 #define TRYF(e)                     \
     do {                            \
         st = (e);                   \
         if (st != MG_OK) return fail(st); \
     } while (0)
-    // reductions
-    H.red.max_blocks = 2 * sm_count();
-    TRYF(halloc_t(H, &H.red.partial, (size_t)H.red.max_blocks * RED_MAXD));
-    TRYF(halloc_t(H, &H.red.ticket, 1));
-    TRYF(halloc_t(H, &H.sc, 1));
-    if (cudaMemsetAsync(H.red.ticket, 0, sizeof(unsigned), s) != cudaSuccess ||
-        cudaMemsetAsync(H.sc, 0, sizeof(Scalars), s) != cudaSuccess) {
-        set_error("cudaMemsetAsync failed");
-        return fail(MG_ECUDA);
-    }
     // hierarchy buffers
     TRYF(halloc_t(H, &H.U64, (size_t)2 * Lx * Lt));
     TRYF(halloc_t(H, &H.U32, (size_t)2 * Lx * Lt));
@@ -228,35 +381,7 @@ mg_status setup_common(const void* gauge, int Lx, int Lt, double m0, int nvec, i
         H.L64[l].Q = H.Q64[l];
         H.L32[l].Q = H.Q32[l];
     }
-    for (int l = 0; l < 3; ++l) {
-        TRYF(alloc_level(H, H.L64[l], p.smooth_steps));
-        TRYF(alloc_level(H, H.L32[l], p.smooth_steps));
-    }
-    TRYF(alloc_coarse(H, H.c64, n2, p.dr_m, p.dr_m));
-    TRYF(alloc_coarse(H, H.c32, n2, p.dr_m, p.dr_m));
-    TRYF(halloc_t(H, &H.fV, (size_t)(p.fgmres_m + 1) * n0));
-    TRYF(halloc_t(H, &H.fZ, (size_t)p.fgmres_m * n0));
-    TRYF(halloc_t(H, &H.fx, (size_t)n0));
-    TRYF(halloc_t(H, &H.fr, (size_t)n0));
-    TRYF(halloc_t(H, &H.fb, (size_t)n0));
-    TRYF(halloc_t(H, &H.v32, (size_t)n0));
-    TRYF(halloc_t(H, &H.z32, (size_t)n0));
-    TRYF(halloc_t(H, &H.fks, 1));
-    TRYF(halloc_t(H, &H.cvec, KLD));
-    TRYF(halloc_t(H, &H.dvec, KLD));
-    TRYF(halloc_t(H, &H.uvec, KLD));
-    TRYF(halloc_t(H, &H.dr, 1));
-    TRYF(halloc_t(H, &H.pls, 1));
-    H.cpart_ctas = sm_count();
-    TRYF(halloc_t(H, &H.cpart, (size_t)2 * H.cpart_ctas * PSTR));
-    TRYF(halloc_t(H, &H.cstats, 1));
-    if (p.method == MG_METHOD_FINE_DEFLATION) {
-        TRYF(halloc_t(H, &H.fdV, (size_t)(p.dr_m + 1) * n0));
-        TRYF(halloc_t(H, &H.fdV2, (size_t)(p.dr_m + 1) * n0));
-        TRYF(halloc_t(H, &H.fdW, (size_t)(p.dr_m + 1) * n0));
-        TRYF(halloc_t(H, &H.fdks, 1));
-        TRYF(halloc_t(H, &H.fdpls, 1));
-    }
+    TRYF(alloc_workspaces(H, s, true));
     if (cudaMemcpyAsync(H.U64, gauge, sizeof(double2) * 2 * Lx * Lt, cudaMemcpyDefault, s) != cudaSuccess) {
         set_error("copy of the gauge field failed: %s", cudaGetErrorString(cudaGetLastError()));
         return fail(MG_ECUDA);
@@ -303,6 +428,14 @@ mg_status setup_common(const void* gauge, int Lx, int Lt, double m0, int nvec, i
 }
 
 }  // namespace
+
+mg_status make_solve_context(mg_handle_s* owner, mg_handle_s** out) {
+    if (!owner || owner->h.is_context) return set_error("a solve context needs a hierarchy owner"), MG_EINVAL;
+    return make_context(owner->h, out);
+}
+size_t handle_device_bytes(const mg_handle_s* h) { return h ? h->h.bytes : 0; }
+cudaStream_t handle_stream(const mg_handle_s* h) { return h ? h->h.own_stream : nullptr; }
+
 }  // namespace mg
 
 using namespace mg;
@@ -332,6 +465,7 @@ mg_status mg_default_params(mg_params* p) {
     p->precision = MG_FP64;
     p->seed = 12345ULL;
     p->method = MG_METHOD_MG;
+    p->parallel = 1;
     return MG_OK;
 }
 
@@ -386,37 +520,84 @@ mg_status mg_solve(mg_handle h, const void* b, void* x, int nrhs, double tol, vo
     H.st = Stats{};
     const long n0 = H.L64[0].n;
     const bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
-    MG_CUDA_TRY(cudaMemsetAsync(H.cstats, 0, sizeof(CoopStats), s));
-    mg_status result = MG_OK;
-    for (int i = 0; i < nrhs; ++i) {
-        const double2* bi = static_cast<const double2*>(b) + (long)i * n0;
-        double2* xi = static_cast<double2*>(x) + (long)i * n0;
-        const double2* bsrc = bi;
-        double2* xdst = xi;
-        if (!bdev) {
-            MG_CUDA_TRY(cudaMemcpyAsync(H.fb, bi, n0 * sizeof(double2), cudaMemcpyHostToDevice, s));
-            bsrc = H.fb;
+    const double2* B = static_cast<const double2*>(b);
+    double2* X = static_cast<double2*>(x);
+    const bool have_defl = (H.p.method == MG_METHOD_FINE_DEFLATION) ? H.fine_k > 0 : H.defl_k > 0;
+    const bool needs_defl = H.p.method == MG_METHOD_FINE_DEFLATION || H.p.coarse_solver == MG_COARSE_DR_PROJ;
+    int par = std::min(nrhs, std::max(H.p.parallel, 1));
+    bool notconv = false;
+    auto seq = [&](int i0, int i1) -> mg_status {
+        const mg_status r = solve_rhs(H, B, X, bdev, xdev, i0, i1, 1, tol, s, iters, relres);
+        if (r == MG_ENOTCONV) notconv = true;
+        return r == MG_ENOTCONV ? MG_OK : r;
+    };
+    if (par <= 1) {
+        MG_TRY(seq(0, nrhs));
+    } else {
+        // the first right-hand side builds the deflation space alone; the rest are
+        // spread over `par` concurrent contexts (this handle + par - 1 contexts)
+        int first = 0;
+        if (needs_defl && !have_defl) {
+            MG_TRY(seq(0, 1));
+            first = 1;
+            par = std::min(par, nrhs - 1);
         }
-        if (!xdev) xdst = H.fx;
-        int it = 0;
-        double rr = 0.0;
-        bool conv = false;
-        if (H.p.method == MG_METHOD_FINE_DEFLATION)
-            MG_TRY(fine_deflated_solve(H, bsrc, xdst, tol, s, &it, &rr, &conv));
-        else
-            MG_TRY(fgmres_solve(H, bsrc, xdst, tol, s, &it, &rr, &conv));
-        if (!xdev) MG_CUDA_TRY(cudaMemcpyAsync(xi, H.fx, n0 * sizeof(double2), cudaMemcpyDeviceToHost, s));
-        if (iters) iters[i] = it;
-        if (relres) relres[i] = rr;
-        if (!conv) result = MG_ENOTCONV;
+        if (first < nrhs) {
+            while ((int)H.contexts.size() < par - 1) {
+                mg_handle_s* c = nullptr;
+                MG_TRY(make_context(H, &c));
+                H.contexts.push_back(c);
+            }
+            for (mg_handle_s* c : H.contexts) {  // a context created before a deflation reset
+                c->h.defl_k = H.defl_k;
+                c->h.fine_k = H.fine_k;
+            }
+            // inputs written on the caller's stream must be visible to the context streams
+            cudaEvent_t ev;
+            MG_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+            MG_CUDA_TRY(cudaEventRecord(ev, s));
+            for (int w = 0; w < par - 1; ++w) MG_CUDA_TRY(cudaStreamWaitEvent(H.contexts[w]->h.own_stream, ev, 0));
+            std::vector<mg_status> st_w(par, MG_OK);
+            std::vector<std::string> err_w(par);
+            std::vector<std::thread> th;
+            int dev = 0;
+            MG_CUDA_TRY(cudaGetDevice(&dev));
+            for (int w = 1; w < par; ++w) {
+                th.emplace_back([&, w]() {
+                    cudaSetDevice(dev);
+                    Handle& C = H.contexts[w - 1]->h;
+                    C.st = Stats{};
+                    st_w[w] = solve_rhs(C, B, X, bdev, xdev, first + w, nrhs, par, tol, C.own_stream, iters, relres);
+                    if (st_w[w] != MG_OK && st_w[w] != MG_ENOTCONV) err_w[w] = mg_last_error();
+                });
+            }
+            const Stats keep = H.st;  // the first right-hand side, if it ran alone
+            H.st = Stats{};
+            st_w[0] = solve_rhs(H, B, X, bdev, xdev, first, nrhs, par, tol, s, iters, relres);
+            for (auto& t : th) t.join();
+            cudaEventDestroy(ev);
+            Stats sum = keep;
+            for (int w = 0; w < par; ++w) {
+                const Stats& sw = (w == 0) ? H.st : H.contexts[w - 1]->h.st;
+                for (int l = 0; l < 3; ++l) sum.mvps[l] += sw.mvps[l];
+                sum.outer += sw.outer;
+                sum.coarse_solves += sw.coarse_solves;
+                sum.coarse_iters += sw.coarse_iters;
+                sum.dr_solves += sw.dr_solves;
+            }
+            H.st = sum;
+            for (int w = 0; w < par; ++w) {
+                if (st_w[w] != MG_OK && st_w[w] != MG_ENOTCONV) {
+                    if (!err_w[w].empty()) set_error("%s", err_w[w].c_str());
+                    return st_w[w];
+                }
+            }
+            for (int w = 0; w < par; ++w)
+                if (st_w[w] == MG_ENOTCONV) notconv = true;
+        }
     }
-    CoopStats cs{};
-    MG_CUDA_TRY(cudaMemcpyAsync(H.pinned, H.cstats, sizeof(CoopStats), cudaMemcpyDeviceToHost, s));
-    MG_CUDA_TRY(cudaStreamSynchronize(s));
     MG_CUDA_TRY(cudaGetLastError());
-    std::memcpy(&cs, H.pinned, sizeof cs);
-    H.st.coarse_iters += cs.iters;
-    H.st.mvps[2] += cs.iters;
+    const mg_status result = notconv ? MG_ENOTCONV : MG_OK;
     if (stats) {
         for (int l = 0; l < 3; ++l) stats->mvps[l] = H.st.mvps[l];
         const double n1 = (double)H.L64[1].n, n2 = (double)H.L64[2].n, nf = (double)n0;

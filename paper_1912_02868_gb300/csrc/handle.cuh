@@ -134,6 +134,11 @@ struct Handle {
     int defl_k = 0;           // 0: no deflation space yet
     Stats st;
     ApplyTimer timers[3];
+    // concurrent solve contexts sharing this hierarchy (mg_solve with nrhs > 1)
+    bool is_context = false;             // a context: shares hierarchy and deflation, owns workspaces
+    cudaStream_t own_stream = nullptr;   // a context's stream
+    std::vector<mg_handle_s*> contexts;
+    size_t bytes = 0;                    // device bytes this handle allocated
 
     template <typename T> Level<T>* levels();
     template <typename T> CoarseWS<T>& coarse();
@@ -156,6 +161,12 @@ mg_status build_hierarchy(Handle& H, const double2* gauge_dev, const double2* st
                           const double2* nullvecs0, const double2* nullvecs1, cudaStream_t s);
 mg_status fine_deflated_solve(Handle& H, const double2* b, double2* x, double tol, cudaStream_t s, int* iters,
                               double* relres, bool* converged);
+// A solve context of `owner` (capi.cu): same hierarchy and deflation space,
+// own workspaces and stream; usable with mg_solve and released with mg_destroy
+// (before its owner).  The owner's deflation space must exist.
+mg_status make_solve_context(mg_handle_s* owner, mg_handle_s** out);
+size_t handle_device_bytes(const mg_handle_s* h);
+cudaStream_t handle_stream(const mg_handle_s* h);
 
 }  // namespace mg
 
