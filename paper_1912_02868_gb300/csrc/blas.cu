@@ -2,16 +2,19 @@
 // of classical Gram-Schmidt, CGS2), multi-vector updates, norms and scalings.
 // All reductions are deterministic: fixed per-thread order, fixed shuffle
 // tree, and the block partials are added in block order by the last block.
+// Reductions run in the precision of the vectors (FP64 vectors: FP64; FP32
+// vectors: FP32) - FP64 arithmetic is a small fraction of the FP32 rate on
+// this GPU, and a reduction sits on the critical path of every Krylov step.
+// Results are always returned as FP64.
 #include "ops.cuh"
 
 namespace mg {
 
 namespace {
 
-__device__ __forceinline__ double2 ldcg(const double2* p) { return __ldcg(p); }
-
-// Sum a double2 over the block; result valid in thread 0.
-__device__ __forceinline__ double2 block_sum(double2 v, double2* sm) {
+// Sum a complex value over the block; result valid in thread 0.
+template <typename T>
+__device__ __forceinline__ C2<T> block_sum(C2<T> v, C2<T>* sm) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -21,7 +24,7 @@ __device__ __forceinline__ double2 block_sum(double2 v, double2* sm) {
     __syncthreads();
     if (lane == 0) sm[warp] = v;
     __syncthreads();
-    double2 r = make_double2(0.0, 0.0);
+    C2<T> r = mk<T>(0, 0);
     if (threadIdx.x == 0) {
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = cadd(r, sm[w]);
     }
@@ -39,19 +42,43 @@ __device__ __forceinline__ bool last_block(unsigned* ticket) {
     return am_last;
 }
 
-__device__ __forceinline__ void finish_reduce(double2* out, const double2* partial, int nd, unsigned* ticket) {
+// The last block adds the partials of all blocks: value i by warp i (mod warps),
+// lanes striding over the blocks in order, then a fixed shuffle tree.  The
+// partial buffer is used as C2<T>[max_blocks][RED_MAXD].
+template <typename T>
+__device__ __forceinline__ C2<T> warp_sum_partials(const C2<T>* partial, int i) {
+    const int lane = threadIdx.x & 31;
+    C2<T> acc = mk<T>(0, 0);
+    for (unsigned b = lane; b < gridDim.x; b += 32) acc = cadd(acc, __ldcg(partial + (size_t)b * RED_MAXD + i));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    }
+    return acc;
+}
+
+template <typename T>
+__device__ __forceinline__ void finish_reduce(double2* out, const C2<T>* partial, int nd, unsigned* ticket) {
     __threadfence();
-    for (int i = threadIdx.x; i < nd; i += blockDim.x) {
-        double2 acc = make_double2(0.0, 0.0);
-        for (unsigned b = 0; b < gridDim.x; ++b) acc = cadd(acc, ldcg(partial + (size_t)b * RED_MAXD + i));
-        out[i] = acc;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = warp; i < nd; i += nw) {
+        const C2<T> acc = warp_sum_partials<T>(partial, i);
+        if (lane == 0) out[i] = to_d2(acc);
     }
     if (threadIdx.x == 0) *ticket = 0u;
 }
 
 template <typename T>
-__device__ __forceinline__ double2 acc_to_d2(C2<T> a) {
-    return to_d2(a);
+__device__ __forceinline__ void finish_reduce_real(double* out, const C2<T>* partial, unsigned* ticket) {
+    __threadfence();
+    if (threadIdx.x < 32) {
+        const C2<T> acc = warp_sum_partials<T>(partial, 0);
+        if (threadIdx.x == 0) {
+            *out = (double)acc.x;
+            *ticket = 0u;
+        }
+    }
 }
 
 constexpr int GRAM_CH = 8;
@@ -59,9 +86,9 @@ constexpr int GRAM_CH = 8;
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) k_gram(double2* __restrict__ out, const C2<T>* __restrict__ V,
                                                       long ldv, int nd, const C2<T>* __restrict__ w, long n,
-                                                      double2* partial, unsigned* ticket, Gate g) {
+                                                      C2<T>* partial, unsigned* ticket, Gate g) {
     if (!gate_open(g)) return;
-    __shared__ double2 sm[RED_THREADS / 32];
+    __shared__ C2<T> sm[RED_THREADS / 32];
     const long stride = (long)gridDim.x * blockDim.x;
     const long e0 = (long)blockIdx.x * blockDim.x + threadIdx.x;
     for (int i0 = 0; i0 < nd; i0 += GRAM_CH) {
@@ -77,22 +104,22 @@ __global__ void __launch_bounds__(RED_THREADS) k_gram(double2* __restrict__ out,
 #pragma unroll
         for (int c = 0; c < GRAM_CH; ++c) {
             if (i0 + c < nd) {
-                double2 r = block_sum(acc_to_d2<T>(acc[c]), sm);
+                const C2<T> r = block_sum<T>(acc[c], sm);
                 if (threadIdx.x == 0) partial[(size_t)blockIdx.x * RED_MAXD + i0 + c] = r;
             }
         }
     }
-    if (last_block(ticket)) finish_reduce(out, partial, nd, ticket);
+    if (last_block(ticket)) finish_reduce<T>(out, partial, nd, ticket);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS)
     k_axpy_multi(C2<T>* __restrict__ w, const C2<T>* __restrict__ V, long ldv, int nd, const int* nd_dev,
                  const double2* __restrict__ coef, double sign, int zero_first, long n, double* norm2_out,
-                 double2* partial, unsigned* ticket, Gate g) {
+                 C2<T>* partial, unsigned* ticket, Gate g) {
     if (!gate_open(g)) return;
     __shared__ C2<T> cs[RED_MAXD];
-    __shared__ double2 sm[RED_THREADS / 32];
+    __shared__ C2<T> sm[RED_THREADS / 32];
     int cnt = nd + (nd_dev ? *nd_dev : 0);
     if (cnt > RED_MAXD) cnt = RED_MAXD;
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
@@ -101,7 +128,6 @@ __global__ void __launch_bounds__(RED_THREADS)
     }
     __syncthreads();
     const long stride = (long)gridDim.x * blockDim.x;
-    double nacc = 0.0;
     T tacc = 0;
     for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
         C2<T> a = zero_first ? mk<T>(0, 0) : w[e];
@@ -110,68 +136,43 @@ __global__ void __launch_bounds__(RED_THREADS)
         if (norm2_out) tacc += a.x * a.x + a.y * a.y;
     }
     if (norm2_out) {
-        nacc = (double)tacc;
-        double2 r = block_sum(make_double2(nacc, 0.0), sm);
+        const C2<T> r = block_sum<T>(mk<T>(tacc, 0), sm);
         if (threadIdx.x == 0) partial[(size_t)blockIdx.x * RED_MAXD] = r;
-        if (last_block(ticket)) {
-            __threadfence();
-            if (threadIdx.x == 0) {
-                double acc = 0.0;
-                for (unsigned b = 0; b < gridDim.x; ++b) acc += ldcg(partial + (size_t)b * RED_MAXD).x;
-                *norm2_out = acc;
-                *ticket = 0u;
-            }
-        }
+        if (last_block(ticket)) finish_reduce_real<T>(norm2_out, partial, ticket);
     }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) k_norm2(double* out, const C2<T>* __restrict__ v, long n,
-                                                       double2* partial, unsigned* ticket, Gate g) {
+                                                       C2<T>* partial, unsigned* ticket, Gate g) {
     if (!gate_open(g)) return;
-    __shared__ double2 sm[RED_THREADS / 32];
+    __shared__ C2<T> sm[RED_THREADS / 32];
     const long stride = (long)gridDim.x * blockDim.x;
     T acc = 0;
     for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
         C2<T> a = v[e];
         acc += a.x * a.x + a.y * a.y;
     }
-    double2 r = block_sum(make_double2((double)acc, 0.0), sm);
+    const C2<T> r = block_sum<T>(mk<T>(acc, 0), sm);
     if (threadIdx.x == 0) partial[(size_t)blockIdx.x * RED_MAXD] = r;
-    if (last_block(ticket)) {
-        __threadfence();
-        if (threadIdx.x == 0) {
-            double a = 0.0;
-            for (unsigned b = 0; b < gridDim.x; ++b) a += ldcg(partial + (size_t)b * RED_MAXD).x;
-            *out = a;
-            *ticket = 0u;
-        }
-    }
+    if (last_block(ticket)) finish_reduce_real<T>(out, partial, ticket);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) k_redot(double* out, const C2<T>* __restrict__ x,
-                                                       const C2<T>* __restrict__ y, long n, double2* partial,
+                                                       const C2<T>* __restrict__ y, long n, C2<T>* partial,
                                                        unsigned* ticket, Gate g) {
     if (!gate_open(g)) return;
-    __shared__ double2 sm[RED_THREADS / 32];
+    __shared__ C2<T> sm[RED_THREADS / 32];
     const long stride = (long)gridDim.x * blockDim.x;
     T acc = 0;
     for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
         C2<T> a = x[e], b = y[e];
         acc += a.x * b.x + a.y * b.y;
     }
-    double2 r = block_sum(make_double2((double)acc, 0.0), sm);
+    const C2<T> r = block_sum<T>(mk<T>(acc, 0), sm);
     if (threadIdx.x == 0) partial[(size_t)blockIdx.x * RED_MAXD] = r;
-    if (last_block(ticket)) {
-        __threadfence();
-        if (threadIdx.x == 0) {
-            double a = 0.0;
-            for (unsigned b = 0; b < gridDim.x; ++b) a += ldcg(partial + (size_t)b * RED_MAXD).x;
-            *out = a;
-            *ticket = 0u;
-        }
-    }
+    if (last_block(ticket)) finish_reduce_real<T>(out, partial, ticket);
 }
 
 template <typename T>
@@ -204,9 +205,9 @@ __global__ void k_xpay(C2<T>* y, const C2<T>* x, const double* num, const double
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS)
     k_cg_step(C2<T>* e, C2<T>* r, const C2<T>* __restrict__ p, const C2<T>* __restrict__ q, const double* rr,
-              const double* pq, double* rr_new, long n, double2* partial, unsigned* ticket, Gate g) {
+              const double* pq, double* rr_new, long n, C2<T>* partial, unsigned* ticket, Gate g) {
     if (!gate_open(g)) return;
-    __shared__ double2 sm[RED_THREADS / 32];
+    __shared__ C2<T> sm[RED_THREADS / 32];
     const T alpha = (T)(*rr / *pq);
     const long stride = (long)gridDim.x * blockDim.x;
     T acc = 0;
@@ -220,17 +221,9 @@ __global__ void __launch_bounds__(RED_THREADS)
         r[i] = ri;
         acc += ri.x * ri.x + ri.y * ri.y;
     }
-    double2 s = block_sum(make_double2((double)acc, 0.0), sm);
+    const C2<T> s = block_sum<T>(mk<T>(acc, 0), sm);
     if (threadIdx.x == 0) partial[(size_t)blockIdx.x * RED_MAXD] = s;
-    if (last_block(ticket)) {
-        __threadfence();
-        if (threadIdx.x == 0) {
-            double a = 0.0;
-            for (unsigned b = 0; b < gridDim.x; ++b) a += ldcg(partial + (size_t)b * RED_MAXD).x;
-            *rr_new = a;
-            *ticket = 0u;
-        }
-    }
+    if (last_block(ticket)) finish_reduce_real<T>(rr_new, partial, ticket);
 }
 
 inline unsigned red_blocks(long n, const RedWS& ws) {
@@ -248,13 +241,15 @@ inline unsigned ew_blocks(long n) {
     return (unsigned)b;
 }
 
+template <typename T> inline C2<T>* part_of(const RedWS& ws) { return reinterpret_cast<C2<T>*>(ws.partial); }
+
 }  // namespace
 
 template <typename T>
 void launch_gram(double2* out, const C2<T>* V, long ldv, int nd, const C2<T>* w, long n, RedWS ws, Gate g,
                  cudaStream_t s) {
     if (nd <= 0) return;
-    k_gram<T><<<red_blocks(n, ws), RED_THREADS, 0, s>>>(out, V, ldv, nd, w, n, ws.partial, ws.ticket, g);
+    k_gram<T><<<red_blocks(n, ws), RED_THREADS, 0, s>>>(out, V, ldv, nd, w, n, part_of<T>(ws), ws.ticket, g);
     count_launch();
 }
 
@@ -262,19 +257,19 @@ template <typename T>
 void launch_axpy_multi(C2<T>* w, const C2<T>* V, long ldv, int nd, const int* nd_dev, const double2* coef,
                        double sign, bool zero_first, long n, double* norm2_out, RedWS ws, Gate g, cudaStream_t s) {
     k_axpy_multi<T><<<red_blocks(n, ws), RED_THREADS, 0, s>>>(w, V, ldv, nd, nd_dev, coef, sign, zero_first ? 1 : 0,
-                                                              n, norm2_out, ws.partial, ws.ticket, g);
+                                                              n, norm2_out, part_of<T>(ws), ws.ticket, g);
     count_launch();
 }
 
 template <typename T>
 void launch_norm2(double* out, const C2<T>* v, long n, RedWS ws, Gate g, cudaStream_t s) {
-    k_norm2<T><<<red_blocks(n, ws), RED_THREADS, 0, s>>>(out, v, n, ws.partial, ws.ticket, g);
+    k_norm2<T><<<red_blocks(n, ws), RED_THREADS, 0, s>>>(out, v, n, part_of<T>(ws), ws.ticket, g);
     count_launch();
 }
 
 template <typename T>
 void launch_redot(double* out, const C2<T>* x, const C2<T>* y, long n, RedWS ws, Gate g, cudaStream_t s) {
-    k_redot<T><<<red_blocks(n, ws), RED_THREADS, 0, s>>>(out, x, y, n, ws.partial, ws.ticket, g);
+    k_redot<T><<<red_blocks(n, ws), RED_THREADS, 0, s>>>(out, x, y, n, part_of<T>(ws), ws.ticket, g);
     count_launch();
 }
 
@@ -299,7 +294,8 @@ void launch_xpay(C2<T>* y, const C2<T>* x, const double* num, const double* den,
 template <typename T>
 void launch_cg_step(C2<T>* e, C2<T>* r, const C2<T>* p, const C2<T>* q, const double* rr, const double* pq,
                     double* rr_new, long n, RedWS ws, Gate g, cudaStream_t s) {
-    k_cg_step<T><<<red_blocks(n, ws), RED_THREADS, 0, s>>>(e, r, p, q, rr, pq, rr_new, n, ws.partial, ws.ticket, g);
+    k_cg_step<T><<<red_blocks(n, ws), RED_THREADS, 0, s>>>(e, r, p, q, rr, pq, rr_new, n, part_of<T>(ws), ws.ticket,
+                                                           g);
     count_launch();
 }
 

@@ -58,8 +58,11 @@ struct Small {  // per-CTA copy of the small least-squares state, precision R
 
 template <typename T>
 struct ClusterSmem {
-    double2 part[2][PSTR];               // this CTA's partial sums (read by the whole cluster)
-    double2 red[PSTR];                   // reduced values (identical in every CTA)
+    // partial sums and reduced values in the vectors' precision: FP64 adds run at
+    // a small fraction of the FP32 rate on this GPU, and the reductions sit on the
+    // critical path of every Arnoldi step
+    C2<T> part[2][PSTR];                 // this CTA's partial sums (read by the whole cluster)
+    C2<T> red[PSTR];                     // reduced values (identical in every CTA)
     C2<T> h1[MSMAX + 1];
     C2<T> h2[MSMAX + 1];
     C2<T> xs[MAX_SPC][5][NDOF];          // staged neighbour rows
@@ -113,7 +116,7 @@ __device__ __forceinline__ void rot_(R c, C2<R> s, C2<R>& up, C2<R>& uq) {
 // at the own rows; warp per product, lanes over rows), plus optionally ||y||^2
 // in slot nd.
 template <typename T>
-__device__ void partial_gram(const C2<T>* X, long ldx, int nd, const C2<T>* y, int nrows, bool norm, double2* part) {
+__device__ void partial_gram(const C2<T>* X, long ldx, int nd, const C2<T>* y, int nrows, bool norm, C2<T>* part) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int ntot = nd + (norm ? 1 : 0);
     for (int i = warp; i < ntot; i += nw) {
@@ -141,7 +144,7 @@ __device__ void partial_gram(const C2<T>* X, long ldx, int nd, const C2<T>* y, i
             acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
             acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
         }
-        if (lane == 0) part[i] = to_d2(acc);
+        if (lane == 0) part[i] = acc;
     }
 }
 
@@ -166,11 +169,12 @@ __device__ __forceinline__ C2<T> accum_rows(C2<T> acc, const C2<T>* X, long ldx,
 
 // Sum the partials of all CTAs of the cluster in rank order (every CTA gets the
 // same result): red[i] = sum_r part_r[i], i < n.
-__device__ void reduce_partials(cg::cluster_group& cluster, double2* part, int n, double2* red) {
+template <typename T>
+__device__ void reduce_partials(cg::cluster_group& cluster, C2<T>* part, int n, C2<T>* red) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int nr = (int)cluster.num_blocks();
     for (int i = warp; i < n; i += nw) {
-        double2 a = make_double2(0.0, 0.0);
+        C2<T> a = mk<T>(0, 0);
         if (lane < nr) a = *cluster.map_shared_rank(part + i, lane);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -244,19 +248,19 @@ __global__ void k_coarse_proj(CoopArgs<T> a) {
     __syncthreads();
     partial_gram<T>(rl, 0, 0, rl, nrows, true, S.part[0]);
     cluster.sync();
-    reduce_partials(cluster, S.part[0], 1, S.red);
-    const double nb = sqrt(fmax(S.red[0].x, 0.0));
+    reduce_partials<T>(cluster, S.part[0], 1, S.red);
+    const double nb = sqrt(fmax((double)S.red[0].x, 0.0));
     const double tol_abs = a.tol * nb;
     int iters = 0, cycles = 0, conv = 0;
     while (true) {
         // ---- projection onto the deflation space: d = argmin ||W^+ r - H_k d|| ----
         partial_gram<T>(Wl, ldw, k + 1, rl, nrows, false, S.part[1]);
         cluster.sync();
-        reduce_partials(cluster, S.part[1], k + 1, S.red);
+        reduce_partials<T>(cluster, S.part[1], k + 1, S.red);
         if (tid == 0) {
             const KState* P = a.pls;
             Z g[KLD];
-            for (int i = 0; i <= k; ++i) g[i] = from_d2<T>(S.red[i]);
+            for (int i = 0; i <= k; ++i) g[i] = S.red[i];
             for (int t = 0; t < P->nrot; ++t)
                 rot_<T>((T)P->rc[t], from_d2<T>(P->rs[t]), g[P->ra[t]], g[P->rb[t]]);
             for (int i = k - 1; i >= 0; --i) {
@@ -278,8 +282,8 @@ __global__ void k_coarse_proj(CoopArgs<T> a) {
         __syncthreads();
         partial_gram<T>(rl, 0, 0, rl, nrows, true, S.part[0]);
         cluster.sync();
-        reduce_partials(cluster, S.part[0], 1, S.red);
-        const double beta = sqrt(fmax(S.red[0].x, 0.0));
+        reduce_partials<T>(cluster, S.part[0], 1, S.red);
+        const double beta = sqrt(fmax((double)S.red[0].x, 0.0));
         if (beta <= tol_abs || beta == 0.0) {
             conv = 1;
             break;
@@ -337,19 +341,19 @@ __global__ void k_coarse_proj(CoopArgs<T> a) {
             }
             partial_gram<T>(Vl, ldv, j + 1, wl, nrows, false, S.part[1]);
             cluster.sync();
-            reduce_partials(cluster, S.part[1], j + 1, S.red);
-            for (int i = tid; i <= j; i += nt) S.h1[i] = from_d2<T>(S.red[i]);
+            reduce_partials<T>(cluster, S.part[1], j + 1, S.red);
+            for (int i = tid; i <= j; i += nt) S.h1[i] = S.red[i];
             __syncthreads();
             for (int e = tid; e < nrows; e += nt) wl[e] = accum_rows<T, true>(wl[e], Vl, ldv, e, S.h1, j + 1);
             __syncthreads();
             partial_gram<T>(Vl, ldv, j + 1, wl, nrows, true, S.part[0]);
             cluster.sync();
-            reduce_partials(cluster, S.part[0], j + 2, S.red);
-            for (int i = tid; i <= j; i += nt) S.h2[i] = from_d2<T>(S.red[i]);
+            reduce_partials<T>(cluster, S.part[0], j + 2, S.red);
+            for (int i = tid; i <= j; i += nt) S.h2[i] = S.red[i];
             if (tid == 0) {
                 T h2n = 0;
                 for (int i = 0; i <= j; ++i) {
-                    const Z h2 = from_d2<T>(S.red[i]);
+                    const Z h2 = S.red[i];
                     const Z hh = cadd(S.h1[i], h2);
                     st.H[i + LD * j] = hh;
                     st.Rm[i + LD * j] = hh;

@@ -54,11 +54,13 @@ def test_parallel_multi_rhs_equals_sequential(mgmod, prec):
         for i in range(7):
             assert rrp[i] <= 1e-8
             assert _true_relres(U, m0, Xh[i], B[i]) <= 1.0001e-8
-        # a second call reuses the contexts (host buffers this time)
+        # a second call reuses the contexts (host buffers this time); right-hand side
+        # 0 now runs GMRES-Proj instead of building the space, the others repeat exactly
         Xh2 = np.zeros_like(B)
         _, it2, rr2, st2 = mgmod.mg_solve(gp, B, Xh2, 7, 1e-8)
         assert st2["dr_solves"] == 0
-        assert np.array_equal(Xh2, Xh)
+        assert np.array_equal(Xh2[1:], Xh[1:])
+        assert _true_relres(U, m0, Xh2[0], B[0]) <= 1.0001e-8
     finally:
         gs.close()
         gp.close()
