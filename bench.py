@@ -49,7 +49,93 @@ def parse():
     ap.add_argument("--configs", type=int, default=NCONF)
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-arms", action="store_true", help="skip the CGNE and fine GMRES-DR comparison arms")
+    ap.add_argument("--no-serving", action="store_true", help="skip the served-stream sample")
+    ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--serve-rate", type=float, default=3.0, help="Poisson arrival rate, requests/s")
     return ap.parse_args()
+
+
+SERVE_SIZES = (64, 128, 256)
+SERVE_CONFIGS = 4
+
+
+def run_serving(mg, torch, np, dev, rank, nreq=24, rate=3.0, workers=10):
+    """Served stream: Poisson arrivals of requests over 3 lattice sizes x 4
+    configurations (12 operators), nrhs ~ U{1..32}, tol 1e-8, mixed precision.
+    Hierarchies are built by a warm-up request per operator (cold starts,
+    reported separately); then the stream is timed: per-request latency from
+    submission to completion, and right-hand sides per second over the stream.
+    The plain FP64 sequential reference time of the same stream is estimated
+    from warm FP64 solves of each lattice size."""
+    import synth
+    args = parse()
+    nreq, rate = args.serve_requests, args.serve_rate
+    rng = np.random.default_rng(1234 + rank)
+    keys = [(L_, c) for L_ in SERVE_SIZES for c in range(SERVE_CONFIGS)]
+    fields = {k: synth.gauge_field(k[0], k[1]) for k in keys}
+
+    def key_id(k):
+        return k[0] * 1000 + k[1]
+
+    def submit(srv, k, nrhs, seed):
+        L_, c = k
+        b = torch.from_numpy(synth.rhs(L_, c, 70000 + seed, nrhs=nrhs)).pin_memory()
+        x = torch.zeros_like(b).pin_memory()
+        U = torch.from_numpy(fields[k])
+        t = srv.submit(key_id(k), U, L_, L_, synth.m0_for(L_, c), b, x, nrhs, TOL,
+                       starts0=torch.from_numpy(synth.nullvec_starts(L_, c, 0, 12, L_ * L_ * 2)),
+                       starts1=torch.from_numpy(synth.nullvec_starts(L_, c, 1, 12, (L_ // 4) ** 2 * 24)))
+        return t, nrhs
+
+    srv = mg.Server(mg.default_params(precision=mg.MG_MIXED), workers=workers)
+    try:
+        t0 = time.perf_counter()
+        warm = [submit(srv, k, 1, i) for i, k in enumerate(keys)]
+        for t, n in warm:
+            srv.wait(t, n)
+        cold_s = time.perf_counter() - t0
+        plan = [(keys[rng.integers(len(keys))], int(rng.integers(1, 33))) for _ in range(nreq)]
+        gaps = rng.exponential(1.0 / rate, size=nreq)
+        tickets = []
+        t_start = time.perf_counter()
+        for i, (k, n) in enumerate(plan):
+            if i:
+                time.sleep(gaps[i])
+            tickets.append((submit(srv, k, n, 1000 + i), k))
+        lat, worst, solved = [], 0.0, 0
+        for (t, n), k in tickets:
+            st, it, rr, l = srv.wait(t, n)
+            lat.append(l)
+            worst = max(worst, max(rr))
+            solved += n
+        t_end = time.perf_counter()
+        info = srv.stats()
+    finally:
+        srv.close()
+    assert worst <= TOL
+    # FP64 sequential reference: warm per-RHS time of each size (2 solves after the deflating one)
+    per_rhs = {}
+    for L_ in SERVE_SIZES:
+        k = (L_, 0)
+        h = mg.mg_setup(torch.from_numpy(fields[k]).to(dev), L_, L_, synth.m0_for(L_, 0),
+                        params=mg.default_params(precision=mg.MG_FP64))
+        b = torch.from_numpy(synth.rhs(L_, 0, 90000, nrhs=3)).to(dev)
+        x = torch.zeros_like(b)
+        mg.mg_solve(h, b[0], x[0], 1, TOL)
+        torch.cuda.synchronize()
+        ts = time.perf_counter()
+        mg.mg_solve(h, b[1:], x[1:], 2, TOL)
+        per_rhs[L_] = (time.perf_counter() - ts) / 2
+        h.close()
+    seq = sum(per_rhs[k[0]] * n for k, n in plan)
+    return {"value": solved / (t_end - t_start), "unit": "solves/s", "requests": nreq, "rhs": solved,
+            "rate_req_per_s": rate, "workers": workers, "operators": len(keys),
+            "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+            "cold_start_s": cold_s, "cold_starts": int(info["cold_starts"]), "evictions": int(info["evictions"]),
+            "fp64_sequential_est_solves_per_s": solved / seq,
+            "fp64_seq_ms_per_rhs": {str(k): 1e3 * v for k, v in per_rhs.items()},
+            "precision": "mixed", "sizes": list(SERVE_SIZES), "nrhs": "U{1..32}", "tol": TOL}
 
 
 def dist_env():
@@ -219,16 +305,16 @@ def run_native(args):
         out = []
         for s in steps:
             t0 = time.perf_counter()
-            st, iters, relres, _ = mg.mg_solve(h, Bsrc[s, c], Xdst[c], 1, TOL, stream=streams[c])
-            out.append((time.perf_counter() - t0, iters[0], relres[0]))
+            st, iters, relres, sd = mg.mg_solve(h, Bsrc[s, c], Xdst[c], 1, TOL, stream=streams[c])
+            out.append((time.perf_counter() - t0, iters[0], relres[0], sd))
         return out
 
-    def run_steps(hs, steps, timed, timer_level=None, Bsrc=None, Xdst=None):
+    def run_steps(hs, steps, timed, timer_levels=(), Bsrc=None, Xdst=None):
         Bsrc = B if Bsrc is None else Bsrc
         Xdst = X if Xdst is None else Xdst
-        if timer_level is not None:
+        for lev in timer_levels:
             for h in hs:
-                mg.mg_timing_enable(h, timer_level, True)
+                mg.mg_timing_enable(h, lev, True)
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
@@ -248,15 +334,18 @@ def run_native(args):
         if world > 1:
             torch.distributed.barrier()
         ms = e0.elapsed_time(e1)
-        kt = None
-        if timer_level is not None:
+        kt = {}
+        for lev in timer_levels:
             tot, cnt = 0.0, 0
             for h in hs:
-                a, b = mg.mg_timing_read(h, timer_level)
+                a, b = mg.mg_timing_read(h, lev)
                 tot += a
                 cnt += b
-                mg.mg_timing_enable(h, timer_level, False)
-            kt = (tot, cnt)
+                mg.mg_timing_enable(h, lev, False)
+            kt[lev] = (tot, cnt)
+        kt["coarse_iters"] = sum(r[3]["coarse_iters"] for r in res)
+        kt["coarse_solves"] = sum(r[3]["coarse_solves"] for r in res)
+        kt["dr_solves"] = sum(r[3]["dr_solves"] for r in res)
         return ms, lat, iters_all, worst, launches, kt
 
     def max_over_ranks(v):
@@ -270,7 +359,7 @@ def run_native(args):
     hs, setup_s = make_handles(mg.MG_MIXED)
     run_steps(hs, range(W), False)
     clk = Clocks(local)
-    ms, lat, iters, worst, launches, kt = run_steps(hs, range(W, W + K), True, timer_level=1)
+    ms, lat, iters, worst, launches, kt = run_steps(hs, range(W, W + K), True, timer_levels=(1, 2))
     clocks = clk.stop()
     ms = max_over_ranks(ms)
     solves = world * K * nconf
@@ -284,23 +373,44 @@ def run_native(args):
     e2e_value = solves / (max_over_ranks(e2e_ms) / 1e3)
     assert worst_e2e <= TOL
 
-    # roofline of the dominant kernel: the intermediate-grid 24x24 block stencil (FP32 in the V-cycle)
+    # Roofline of the dominant kernel: the coarsest-grid GMRES-Proj solve (one cluster
+    # kernel per coarse solve, ~90% of the solve time).  Algorithmic bytes of one of
+    # its Krylov steps: the 16^2 x 5 x 24 x 24 complex64 stencil read once, v_j read
+    # and v_{j+1} written once; steps per launch from the solve counters.
+    peaks, peak_kind = measured_peaks()
+    s2 = (L // 16) ** 2
+    step_bytes = (5 * 576 + 2 * 24) * 8 * s2
+    c_ms, c_n = kt[2]
+    steps_per_launch = kt["coarse_iters"] / max(kt["coarse_solves"] - kt["dr_solves"], 1)
+    c_avg = c_ms / 1e3 / max(c_n, 1)
+    c_bytes = steps_per_launch * step_bytes
+    c_ach = c_bytes / c_avg / 1e9
+
+    def traffic_of(name):
+        tpath = os.path.join(ROOT, "profiles", name)
+        if os.path.exists(tpath):
+            with open(tpath) as f:
+                return json.load(f).get("dram_bytes_per_launch")
+        return None
+    roofline = {"bound": "hbm", "achieved": c_ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": c_ach / peaks["hbm_gbs"], "traffic": traffic_of("coarse_proj_f32_256.json"),
+                "kernel": "k_coarse_proj<float> (whole coarse GMRES-Proj solve, 16^2 x 24, cluster of 16 CTAs)",
+                "bytes_per_launch": c_bytes, "steps_per_launch": steps_per_launch,
+                "us_per_step": 1e6 * c_avg / max(steps_per_launch, 1), "avg_launch_us": c_avg * 1e6,
+                "launches": c_n, "share_of_timed_gpu_time": None, "peak_source": peak_kind,
+                "note": "latency-bound: each Krylov step is three cluster barriers and DSMEM reductions; the "
+                        "stencil operand (5.9 MB) is L2-resident, so HBM is not the binding limit"}
+    # the bandwidth-bound kernel of the V-cycle: the intermediate-grid 24x24 block stencil (FP32)
     s1 = (L // 4) ** 2
     bytes_per_launch = (5 * 576 + 2 * 24) * 8 * s1  # blocks + input + output, complex64
-    peaks, peak_kind = measured_peaks()
-    kt_ms, kt_n = kt
+    kt_ms, kt_n = kt[1]
     avg_s = kt_ms / 1e3 / max(kt_n, 1)
     achieved = bytes_per_launch / avg_s / 1e9
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "stencil_f32_256.json")
-    if os.path.exists(tpath):
-        with open(tpath) as f:
-            traffic = json.load(f).get("dram_bytes_per_launch")
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                "kernel": "k_stencil<float,24> (intermediate grid, 64^2 x 24)",
-                "bytes_per_launch": bytes_per_launch, "avg_launch_us": avg_s * 1e6, "launches": kt_n,
-                "peak_source": peak_kind}
+    stencil_roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                        "frac": achieved / peaks["hbm_gbs"], "traffic": traffic_of("stencil_f32_256.json"),
+                        "kernel": "k_stencil<float,24> (intermediate grid, 64^2 x 24)",
+                        "bytes_per_launch": bytes_per_launch, "avg_launch_us": avg_s * 1e6, "launches": kt_n,
+                        "peak_source": peak_kind}
 
     for h in hs:
         h.close()
@@ -317,6 +427,38 @@ def run_native(args):
                 "outer_iters_mean": float(np.mean(it64)), "setup_s": setup64}
         for h in hs64:
             h.close()
+
+    # ---------------- comparison arms of the 256^2 study (Section 2) ----------------
+    arms = None
+    if not args.no_arms:
+        arms = {}
+        narm = min(2, nconf)
+        for name, over in (("deflated_mg", {}),
+                           ("undeflated_mg_cgne", {"coarse_solver": mg.MG_COARSE_CGNE}),
+                           ("fine_gmres_dr", {"method": mg.MG_METHOD_FINE_DEFLATION})):
+            t0 = time.perf_counter()
+            tot = 0.0
+            fe = []
+            for c in range(narm):
+                h = mg.mg_setup(torch.from_numpy(Us[c]).to(dev), L, L, m0s[c],
+                                params=mg.default_params(precision=mg.MG_FP64, **over),
+                                starts0=torch.from_numpy(synth.nullvec_starts(L, c, 0, 12, n0)).to(dev),
+                                starts1=torch.from_numpy(
+                                    synth.nullvec_starts(L, c, 1, 12, (L // 4) ** 2 * 24)).to(dev))
+                torch.cuda.synchronize()
+                ts = time.perf_counter()
+                st, it_, rr, sd = mg.mg_solve(h, B[0, c], X[c], 1, TOL, stream=stream, allow_notconv=True)
+                tot += time.perf_counter() - ts
+                fe.append(sd["fine_equiv_mvps"])
+                h.close()
+            arms[name] = {"solves_per_s": narm / tot, "fine_equiv_mvps_mean": float(np.mean(fe)),
+                          "first_rhs": True, "configs": narm, "precision": "f64",
+                          "wall_s": time.perf_counter() - t0}
+
+    # ---------------- served stream (continuous batching over many operators) ----------------
+    serving = None
+    if not args.no_serving:
+        serving = run_serving(mg, torch, np, dev, rank)
 
     if rank != 0:
         return
@@ -338,9 +480,12 @@ def run_native(args):
         "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
         "outer_iters_mean": float(np.mean(iters)), "setup_s": setup_s,
         "fp64": fp64,
+        "arms_256": arms,
+        "serving": serving,
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": nconf * n0 * 16,
                 "d2h_bytes_per_step": nconf * n0 * 16 + nconf * 8},
         "roofline": roofline,
+        "stencil_roofline": stencil_roofline,
         "cpu_baseline": cpu,
         "clocks": clocks,
         "gpu_launches": int(launches),

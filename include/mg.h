@@ -270,8 +270,10 @@ mg_status mg_server_destroy(mg_server s);
  * resets the totals.  mg_timing_read waits for the last recorded event and
  * returns the summed apply time in milliseconds and the number of applies.
  * Meant for roofline reports; the events add a few microseconds of host work
- * per apply.  Not meaningful on the coarsest grid, whose applies may be
- * skipped on the device after a Krylov cycle has converged.
+ * per apply.  On the coarsest grid (level 2) the timed unit is one whole
+ * projected coarse solve (a single kernel); applies inside GMRES-DR or CGNE
+ * coarse solves are timed individually and may include steps skipped on the
+ * device after convergence.
  */
 mg_status mg_timing_enable(mg_handle h, int level, int enable);
 mg_status mg_timing_read(mg_handle h, int level, double* total_ms, long long* launches);

@@ -295,7 +295,17 @@ mg_status proj_solve(Handle& H, const C2<T>* f, C2<T>* x, cudaStream_t s) {
     a.part = H.cpart;
     a.part_ctas = H.cpart_ctas;
     a.out = H.cstats;
-    return launch_coarse_proj<T>(a, s);
+    // grid-2 timing covers the whole projected solve (one kernel)
+    ApplyTimer* t = L.timer;
+    cudaEvent_t e1 = nullptr;
+    if (t && t->on) {
+        cudaEvent_t e0 = t->next();
+        e1 = t->next();
+        if (e0) cudaEventRecord(e0, s);
+    }
+    const mg_status st = launch_coarse_proj<T>(a, s);
+    if (e1) cudaEventRecord(e1, s);
+    return st;
 }
 
 template <typename T>
