@@ -10,9 +10,9 @@
 // solves (one per stream) run side by side on different clusters.
 //
 // Work split: CTA b of the cluster owns sites [b*spc, (b+1)*spc) and their 24
-// dofs.  When it fits, the CTA keeps its rows of the Krylov basis and of the
-// deflation space in shared memory, so the Gram and update passes never leave
-// the SM; the basis is also written to global memory (L2-resident), from where
+// dofs.  When it fits, the CTA keeps its rows of the Krylov basis in shared
+// memory, so the Gram and update passes never leave the SM (the deflation
+// space, read once per cycle, stays in global memory); the basis is also written to global memory (L2-resident), from where
 // the stencil apply stages the five neighbour rows of each own site (rows of
 // other CTAs, written before the previous barrier).  Neighbour indices are
 // tabulated once per launch.
@@ -41,7 +41,7 @@ namespace {
 
 constexpr int NDOF = 24;
 constexpr int MAX_THREADS = 512;
-constexpr int MAX_SPC = 32;       // sites per apply chunk (staged neighbour rows)
+constexpr int MAX_SPC = 16;       // sites per apply chunk (staged neighbour rows)
 constexpr int MAX_NB_SITES = 256; // sites per CTA in the neighbour table
 constexpr size_t SMEM_LIMIT = 227 * 1024;
 
@@ -73,10 +73,10 @@ struct ClusterSmem {
 };
 
 // dynamic shared memory: ClusterSmem, then (optionally) the basis slice
-// Vs[(ms + 1)][rows] and the deflation slice Ws[(k + 1)][rows]
+// Vs[(ms + 1)][rows]
 template <typename T>
-__host__ __device__ inline size_t slice_bytes(int ms, int k, int rows) {
-    return (size_t)(ms + 1 + k + 1) * rows * sizeof(C2<T>);
+__host__ __device__ inline size_t slice_bytes(int ms, int rows) {
+    return (size_t)(ms + 1) * rows * sizeof(C2<T>);
 }
 
 template <typename R>
@@ -195,8 +195,11 @@ __device__ __forceinline__ long nbr_site(long s, int d, int Nx, int Nt) {
     return s;
 }
 
+// At most 80 registers a thread: two CTAs of 384 threads (16 coarse sites)
+// then fit on one SM (2 x 384 x 80 <= 65536), as do their shared-memory
+// slices, so the solves of concurrent streams can share SMs.
 template <typename T>
-__global__ void k_coarse_proj(CoopArgs<T> a) {
+__global__ void __maxnreg__(80) k_coarse_proj(CoopArgs<T> a) {
     using Z = C2<T>;
     cg::cluster_group cluster = cg::this_cluster();
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -215,25 +218,18 @@ __global__ void k_coarse_proj(CoopArgs<T> a) {
     const int LD = MSMAX + 1;
     const bool table = my_sites <= MAX_NB_SITES;
 
-    // own rows of the basis and of the deflation space: shared memory when it fits
+    // own rows of the basis: shared memory when it fits (the deflation space is
+    // read once per cycle and stays in global memory)
     Z* Vl;
-    const Z* Wl;
-    long ldv, ldw;
+    const Z* Wl = a.W + r0;
+    const long ldw = n;
+    long ldv;
     if (a.vs) {
-        const int rows_cap = a.spc * NDOF;
-        Z* Vs = reinterpret_cast<Z*>(smem_raw + sizeof(ClusterSmem<T>));
-        Z* Ws = Vs + (long)(ms + 1) * rows_cap;
-        for (int e = tid; e < (k + 1) * nrows; e += nt) {
-            const int i = e / nrows, rr = e - i * nrows;
-            Ws[(long)i * rows_cap + rr] = a.W[(long)i * n + r0 + rr];
-        }
-        Vl = Vs;
-        Wl = Ws;
-        ldv = ldw = rows_cap;
+        Vl = reinterpret_cast<Z*>(smem_raw + sizeof(ClusterSmem<T>));
+        ldv = a.spc * NDOF;
     } else {
         Vl = a.V + r0;
-        Wl = a.W + r0;
-        ldv = ldw = n;
+        ldv = n;
     }
     if (table)
         for (int e = tid; e < my_sites * 5; e += nt) S.nbt[e / 5][e % 5] = (int)nbr_site(s0 + e / 5, e % 5, a.Nx, a.Nt);
@@ -431,7 +427,7 @@ struct Geometry {
 };
 
 template <typename T>
-mg_status geometry(long nsite, int ms, int k, Geometry& g) {
+mg_status geometry(long nsite, int ms, Geometry& g) {
     static bool configured[2][16] = {};
     int dev = 0;
     MG_CUDA_TRY(cudaGetDevice(&dev));
@@ -452,7 +448,7 @@ mg_status geometry(long nsite, int ms, int k, Geometry& g) {
         int threads = ((rows + 31) / 32) * 32;
         threads = std::min(std::max(threads, 64), MAX_THREADS);
         for (int vs = 1; vs >= 0; --vs) {
-            const size_t smem = sizeof(ClusterSmem<T>) + (vs ? slice_bytes<T>(ms, k, rows) : 0);
+            const size_t smem = sizeof(ClusterSmem<T>) + (vs ? slice_bytes<T>(ms, rows) : 0);
             if (smem > SMEM_LIMIT) continue;
             cudaLaunchConfig_t cfg{};
             cudaLaunchAttribute attr[1];
@@ -493,7 +489,7 @@ mg_status launch_coarse_proj(const CoopArgs<T>& args_in, cudaStream_t s) {
         return MG_EINVAL;
     }
     Geometry g;
-    MG_TRY(geometry<T>((long)a.Nx * a.Nt, a.ms, a.k, g));
+    MG_TRY(geometry<T>((long)a.Nx * a.Nt, a.ms, g));
     a.spc = g.spc;
     a.vs = g.vs;
     cudaLaunchConfig_t cfg{};

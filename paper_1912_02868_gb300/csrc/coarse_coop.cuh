@@ -4,7 +4,7 @@
 
 namespace mg {
 
-constexpr int MSMAX = 40;  // longest GMRES cycle of a projected solve (m - k)
+constexpr int MSMAX = 24;  // longest GMRES cycle of a projected solve (m - k): (30,10) -> 20, (40,16) -> 24
 constexpr int PSTR = 64;   // stride of one CTA's partial sums
 
 // device-side counters of the projected coarse solves
