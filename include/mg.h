@@ -281,6 +281,29 @@ mg_status mg_timing_read(mg_handle h, int level, double* total_ms, long long* la
 /* Number of kernels this library has launched in this process so far. */
 unsigned long long mg_kernel_launches(void);
 
+/*
+ * Allocation-free true residual (the paper has no counterpart: it is a
+ * service for callers that may not allocate device memory, e.g. an
+ * application whose pool owns all of HBM, or a thread that must not let
+ * cudaMalloc/cudaFree synchronise the device while other streams run).
+ * Computes r = b - D(m0) x with the solver's FP64 residual kernel and
+ *   norms[0] = ||b - D x||_2,  norms[1] = ||b||_2,
+ * the quantities of the outer stopping test (Section 2).
+ *   gauge     device, complex128[L_t][L_x][2] (caller-owned, read only)
+ *   b, x      device, complex128[L_t][L_x][2] (read only)
+ *   r         device, complex128[L_t][L_x][2] (written; must not alias b or x)
+ *   norms     host, double[2] (written; the call waits for `stream`)
+ * No device memory is allocated: the reductions use a fixed 64 KB array in
+ * the library's device image, which bounds the lattice to at most 2^20 sites
+ * (1024 x 1024); larger lattices return MG_EINVAL.  The first call on each
+ * device looks up that array's address, so it should come before any stream
+ * capture begins on the device.  There is one such array per device: calls
+ * that can overlap on the GPU (other streams or host threads) race on it and
+ * must be serialised by the caller.
+ */
+mg_status mg_wilson_residual_noalloc(const void* gauge, int L_x, int L_t, double m0, const void* b, const void* x,
+                                     void* r, double* norms, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -20,7 +20,7 @@ from ._lib import (MG_COARSE_CGNE, MG_COARSE_DR_PROJ, MG_F32, MG_F64, MG_FP64, M
 __all__ = ["build", "default_params", "mg_setup", "mg_setup_from_vectors", "mg_solve", "mg_destroy",
            "mg_reset_deflation", "mg_apply", "mg_restrict", "mg_prolong", "mg_get_stencil",
            "mg_get_prolongator", "mg_get_deflation", "mg_level_shape", "mg_wilson_apply", "mg_timing_enable",
-           "mg_timing_read", "mg_kernel_launches", "Handle"]
+           "mg_timing_read", "mg_kernel_launches", "mg_wilson_residual_noalloc", "Handle"]
 
 
 def build(force: bool = False) -> str:
@@ -185,6 +185,14 @@ def mg_get_deflation(h: Handle):
 def mg_wilson_apply(gauge, Lx, Lt, m0, x, y, dagger=False, precision=MG_F64, stream=None):
     _lib.check(load().mg_wilson_apply(_ptr(gauge), Lx, Lt, float(m0), int(dagger), precision, _ptr(x), _ptr(y),
                                       _stream(stream, x)), "mg_wilson_apply")
+
+
+def mg_wilson_residual_noalloc(gauge, Lx, Lt, m0, b, x, r, stream=None):
+    """r = b - D x on the device; returns (||b - D x||, ||b||).  Allocates no device memory."""
+    norms = (ctypes.c_double * 2)()
+    _lib.check(load().mg_wilson_residual_noalloc(_ptr(gauge), Lx, Lt, float(m0), _ptr(b), _ptr(x), _ptr(r), norms,
+                                                 _stream(stream, b)), "mg_wilson_residual_noalloc")
+    return norms[0], norms[1]
 
 
 def mg_timing_enable(h: Handle, level, enable=True):

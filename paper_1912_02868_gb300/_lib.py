@@ -63,7 +63,7 @@ SYMBOLS = ("mg_default_params", "mg_setup", "mg_setup_from_vectors", "mg_solve",
            "mg_destroy", "mg_last_error", "mg_apply", "mg_restrict", "mg_prolong", "mg_get_stencil",
            "mg_get_prolongator", "mg_get_deflation", "mg_level_shape", "mg_wilson_apply",
            "mg_timing_enable", "mg_timing_read", "mg_kernel_launches", "mg_server_create", "mg_server_submit",
-           "mg_server_wait", "mg_server_stats", "mg_server_destroy")
+           "mg_server_wait", "mg_server_stats", "mg_server_destroy", "mg_wilson_residual_noalloc")
 
 
 def load(path: str | None = None) -> ctypes.CDLL:
@@ -100,6 +100,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "mg_server_wait": (i, [vp, ctypes.c_ulonglong, ctypes.POINTER(i), ctypes.POINTER(d), ctypes.POINTER(d)]),
         "mg_server_stats": (i, [vp, ctypes.POINTER(MGServerInfo)]),
         "mg_server_destroy": (i, [vp]),
+        "mg_wilson_residual_noalloc": (i, [vp, i, i, d, vp, vp, vp, ctypes.POINTER(d), vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
