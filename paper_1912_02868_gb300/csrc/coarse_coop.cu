@@ -4,7 +4,8 @@
 // The coarsest grid is small (256 sites x 24 dofs at 256^2) and its solve runs
 // ~10^3 Krylov steps per outer iteration, so a step is bound by latency, not
 // by bytes.  One cluster of up to 16 CTAs runs a whole solve: three hardware
-// cluster barriers per Arnoldi step, reductions through distributed shared
+// cluster barriers per Arnoldi step (the last one split, with the least-squares
+// update between its arrive and wait), reductions through distributed shared
 // memory, and the small least-squares work done redundantly (and identically)
 // by every CTA, so no CTA ever waits for another one's scalar result.  Several
 // solves (one per stream) run side by side on different clusters.
@@ -12,18 +13,21 @@
 // Work split: CTA b of the cluster owns sites [b*spc, (b+1)*spc) and their 24
 // dofs.  When it fits, the CTA keeps its rows of the Krylov basis in shared
 // memory, so the Gram and update passes never leave the SM (the deflation
-// space, read once per cycle, stays in global memory); the basis is also written to global memory (L2-resident), from where
-// the stencil apply stages the five neighbour rows of each own site (rows of
-// other CTAs, written before the previous barrier).  Neighbour indices are
-// tabulated once per launch.
+// space, read once per cycle, stays in global memory).  The basis is also
+// written to global memory (L2-resident), from where the stencil apply stages
+// the five neighbour rows of each own site (rows of other CTAs, written before
+// the previous barrier).  Neighbour indices are tabulated once per launch.
 //
 // Per Arnoldi step j (CGS2, as in the rest of the library):
-//   [sync] w = A v_j; h1 = V^+ w (partials)
-//   [sync] reduce h1; w -= V h1; h2 = V^+ w, n2 = ||w||^2 (partials)
-//   [sync] reduce h2, n2; w -= V h2; ||w||^2 = n2 - |h2|^2 (V orthonormal);
-//          Givens update of the least squares; v_{j+1} = w / h_{j+1,j}
+//   w = A v_j; h1 = V^+ w: partials pushed to every CTA          [barrier]
+//   reduce h1; w -= V h1; h2 = V^+ w, n2 = ||w||^2: pushed        [barrier]
+//   reduce; h_{j+1,j} = sqrt(n2 - |h2|^2) (V orthonormal);
+//   v_{j+1} = (w - V h2) / h_{j+1,j}                              [arrive]
+//   warp 0: Givens update of the least squares, residual estimate [wait]
 // Reductions add the CTAs' partials in rank order with one fixed warp tree, so
 // every CTA holds bit-identical scalars and takes identical control decisions.
+// Partials are pushed into every CTA's shared memory (distributed shared-memory
+// stores) before the barrier, so each reduction after it reads local memory.
 //
 // The small least squares runs in the precision of the vectors (FP32 in the
 // mixed-precision V-cycle, FP64 on the plain path).
@@ -43,6 +47,7 @@ constexpr int NDOF = 24;
 constexpr int MAX_THREADS = 512;
 constexpr int MAX_SPC = 16;       // sites per apply chunk (staged neighbour rows)
 constexpr int MAX_NB_SITES = 256; // sites per CTA in the neighbour table
+constexpr int MAX_CLUSTER = 16;    // CTAs of one cluster (non-portable size)
 constexpr size_t SMEM_LIMIT = 227 * 1024;
 
 template <typename R>
@@ -61,10 +66,9 @@ struct ClusterSmem {
     // partial sums and reduced values in the vectors' precision: FP64 adds run at
     // a small fraction of the FP32 rate on this GPU, and the reductions sit on the
     // critical path of every Arnoldi step
-    C2<T> part[2][PSTR];                 // this CTA's partial sums (read by the whole cluster)
+    C2<T> inbox[2][MAX_CLUSTER][PSTR];   // partial sums pushed here by every CTA of the cluster
     C2<T> red[PSTR];                     // reduced values (identical in every CTA)
     C2<T> h1[MSMAX + 1];
-    C2<T> h2[MSMAX + 1];
     C2<T> xs[MAX_SPC][5][NDOF];          // staged neighbour rows
     int nbt[MAX_NB_SITES][5];            // neighbour site of each own site and direction
     Small<T> st;
@@ -114,10 +118,14 @@ __device__ __forceinline__ void rot_(R c, C2<R> s, C2<R>& up, C2<R>& uq) {
 
 // Partials of nd inner products conj(X[i]) . y over the CTA's rows (X, y point
 // at the own rows; warp per product, lanes over rows), plus optionally ||y||^2
-// in slot nd.
+// in slot nd.  Each partial is pushed into every CTA's inbox (row = this CTA's
+// rank), so after the next cluster barrier every CTA reduces from its own
+// shared memory instead of fetching from 16 remote ones.
 template <typename T>
-__device__ void partial_gram(const C2<T>* X, long ldx, int nd, const C2<T>* y, int nrows, bool norm, C2<T>* part) {
+__device__ void push_gram(cg::cluster_group& cluster, const C2<T>* X, long ldx, int nd, const C2<T>* y, int nrows,
+                          bool norm, C2<T>* inbox) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int nr = (int)cluster.num_blocks(), me = (int)cluster.block_rank();
     const int ntot = nd + (norm ? 1 : 0);
     for (int i = warp; i < ntot; i += nw) {
         // four independent accumulators keep four loads per lane in flight
@@ -144,7 +152,7 @@ __device__ void partial_gram(const C2<T>* X, long ldx, int nd, const C2<T>* y, i
             acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
             acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
         }
-        if (lane == 0) part[i] = acc;
+        if (lane < nr) *cluster.map_shared_rank(inbox + me * PSTR + i, lane) = acc;
     }
 }
 
@@ -167,15 +175,15 @@ __device__ __forceinline__ C2<T> accum_rows(C2<T> acc, const C2<T>* X, long ldx,
     return acc;
 }
 
-// Sum the partials of all CTAs of the cluster in rank order (every CTA gets the
-// same result): red[i] = sum_r part_r[i], i < n.
+// Sum the pushed partials of all CTAs of the cluster in rank order (every CTA
+// gets the same result): red[i] = sum_r inbox[r][i], i < n.  Called after the
+// cluster barrier that follows the pushes.
 template <typename T>
-__device__ void reduce_partials(cg::cluster_group& cluster, C2<T>* part, int n, C2<T>* red) {
+__device__ void reduce_inbox(const C2<T>* inbox, int nr, int n, C2<T>* red) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int nr = (int)cluster.num_blocks();
     for (int i = warp; i < n; i += nw) {
         C2<T> a = mk<T>(0, 0);
-        if (lane < nr) a = *cluster.map_shared_rank(part + i, lane);
+        if (lane < nr) a = inbox[lane * PSTR + i];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             a.x += __shfl_xor_sync(0xffffffffu, a.x, o);
@@ -185,6 +193,12 @@ __device__ void reduce_partials(cg::cluster_group& cluster, C2<T>* part, int n, 
     }
     __syncthreads();
 }
+
+// Split cluster barrier: arrive (releasing this thread's writes, shared and
+// global, to the cluster) and wait (acquiring everyone's).  Work placed between
+// the two overlaps the barrier's latency.  Every thread of a warp executes both.
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory"); }
 
 __device__ __forceinline__ long nbr_site(long s, int d, int Nx, int Nt) {
     const int xx = (int)(s % Nx), tt = (int)(s / Nx);
@@ -242,17 +256,18 @@ __global__ void __maxnreg__(80) k_coarse_proj(CoopArgs<T> a) {
         rl[e] = a.f[r0 + e];
     }
     __syncthreads();
-    partial_gram<T>(rl, 0, 0, rl, nrows, true, S.part[0]);
+    const int ncta = (int)cluster.num_blocks();
+    push_gram<T>(cluster, rl, 0, 0, rl, nrows, true, &S.inbox[0][0][0]);
     cluster.sync();
-    reduce_partials<T>(cluster, S.part[0], 1, S.red);
+    reduce_inbox<T>(&S.inbox[0][0][0], ncta, 1, S.red);
     const double nb = sqrt(fmax((double)S.red[0].x, 0.0));
     const double tol_abs = a.tol * nb;
     int iters = 0, cycles = 0, conv = 0;
     while (true) {
         // ---- projection onto the deflation space: d = argmin ||W^+ r - H_k d|| ----
-        partial_gram<T>(Wl, ldw, k + 1, rl, nrows, false, S.part[1]);
+        push_gram<T>(cluster, Wl, ldw, k + 1, rl, nrows, false, &S.inbox[1][0][0]);
         cluster.sync();
-        reduce_partials<T>(cluster, S.part[1], k + 1, S.red);
+        reduce_inbox<T>(&S.inbox[1][0][0], ncta, k + 1, S.red);
         if (tid == 0) {
             const KState* P = a.pls;
             Z g[KLD];
@@ -276,9 +291,9 @@ __global__ void __maxnreg__(80) k_coarse_proj(CoopArgs<T> a) {
             rl[e] = accum_rows<T, true>(rl[e], Wl, ldw, e, st.pu, k + 1);
         }
         __syncthreads();
-        partial_gram<T>(rl, 0, 0, rl, nrows, true, S.part[0]);
+        push_gram<T>(cluster, rl, 0, 0, rl, nrows, true, &S.inbox[0][0][0]);
         cluster.sync();
-        reduce_partials<T>(cluster, S.part[0], 1, S.red);
+        reduce_inbox<T>(&S.inbox[0][0][0], ncta, 1, S.red);
         const double beta = sqrt(fmax((double)S.red[0].x, 0.0));
         if (beta <= tol_abs || beta == 0.0) {
             conv = 1;
@@ -306,9 +321,9 @@ __global__ void __maxnreg__(80) k_coarse_proj(CoopArgs<T> a) {
                 if (a.vs) a.V[r0 + e] = v;
             }
         }
+        cluster.sync();  // v_0 complete in every CTA
         int j = 0, stop = 0;
         for (; j < ms && !stop; ++j) {
-            cluster.sync();  // v_j complete in every CTA
             const Z* vj = a.V + (long)j * n;
             Z* wl = Vl + (long)(j + 1) * ldv;
             // w = A v_j on the CTA's rows (column-major 24x24 blocks), MAX_SPC sites at a
@@ -335,58 +350,68 @@ __global__ void __maxnreg__(80) k_coarse_proj(CoopArgs<T> a) {
                 }
                 __syncthreads();
             }
-            partial_gram<T>(Vl, ldv, j + 1, wl, nrows, false, S.part[1]);
+            push_gram<T>(cluster, Vl, ldv, j + 1, wl, nrows, false, &S.inbox[1][0][0]);
             cluster.sync();
-            reduce_partials<T>(cluster, S.part[1], j + 1, S.red);
+            reduce_inbox<T>(&S.inbox[1][0][0], ncta, j + 1, S.red);
             for (int i = tid; i <= j; i += nt) S.h1[i] = S.red[i];
             __syncthreads();
             for (int e = tid; e < nrows; e += nt) wl[e] = accum_rows<T, true>(wl[e], Vl, ldv, e, S.h1, j + 1);
             __syncthreads();
-            partial_gram<T>(Vl, ldv, j + 1, wl, nrows, true, S.part[0]);
+            push_gram<T>(cluster, Vl, ldv, j + 1, wl, nrows, true, &S.inbox[0][0][0]);
             cluster.sync();
-            reduce_partials<T>(cluster, S.part[0], j + 2, S.red);
-            for (int i = tid; i <= j; i += nt) S.h2[i] = S.red[i];
-            if (tid == 0) {
-                T h2n = 0;
-                for (int i = 0; i <= j; ++i) {
-                    const Z h2 = S.red[i];
-                    const Z hh = cadd(S.h1[i], h2);
-                    st.H[i + LD * j] = hh;
-                    st.Rm[i + LD * j] = hh;
-                    h2n += h2.x * h2.x + h2.y * h2.y;
-                }
-                const T hn = sqrt(fmax((T)S.red[j + 1].x - h2n, T(0)));
-                st.H[(j + 1) + LD * j] = mk<T>(hn, 0);
-                st.Rm[(j + 1) + LD * j] = mk<T>(hn, 0);
-                Z* Rc = st.Rm + LD * j;
-                for (int t = 0; t < j; ++t) rot_<T>(st.rc[t], st.rs[t], Rc[t], Rc[t + 1]);
-                T cc;
-                Z ss, rr;
-                givens_<T>(Rc[j], Rc[j + 1], cc, ss, rr);
-                Rc[j] = rr;
-                Rc[j + 1] = mk<T>(0, 0);
-                st.rc[j] = cc;
-                st.rs[j] = ss;
-                rot_<T>(cc, ss, st.g[j], st.g[j + 1]);
-                const double res = (double)cabs_<T>(st.g[j + 1]);
-                S.ctl[0] = (res <= tol_abs) ? 1 : 0;
-                S.ctl[1] = (hn == T(0)) ? 1 : 0;
-                S.scal[1] = hn > T(0) ? T(1) / hn : T(0);
-            }
-            __syncthreads();
+            reduce_inbox<T>(&S.inbox[0][0][0], ncta, j + 2, S.red);
+            // h_{j+1,j} = ||w - V h2|| = sqrt(n2 - |h2|^2) (V orthonormal), computed
+            // identically by every thread; then v_{j+1} = (w - V h2) / h_{j+1,j}
+            T h2n = 0;
+            for (int i = 0; i <= j; ++i) h2n += S.red[i].x * S.red[i].x + S.red[i].y * S.red[i].y;
+            const T hn = sqrt(fmax((T)S.red[j + 1].x - h2n, T(0)));
             {
-                const T sc = S.scal[1];
+                const T sc = hn > T(0) ? T(1) / hn : T(0);
                 Z* wg = a.V + (long)(j + 1) * n + r0;
                 for (int e = tid; e < nrows; e += nt) {
-                    const Z v = cscale(accum_rows<T, true>(wl[e], Vl, ldv, e, S.h2, j + 1), sc);
+                    const Z v = cscale(accum_rows<T, true>(wl[e], Vl, ldv, e, S.red, j + 1), sc);
                     wl[e] = v;
                     if (a.vs) wg[e] = v;
                 }
             }
+            __syncwarp();
+            cluster_arrive();  // v_{j+1} complete in this CTA
+            // meanwhile warp 0 updates the least squares: column j of H (h1 + h2,
+            // h_{j+1,j}), the previous rotations applied to it, the new rotation, and
+            // the residual estimate |g_{j+1}|
+            if (tid < 32) {
+                for (int i = tid; i <= j; i += 32) st.H[i + LD * j] = cadd(S.h1[i], S.red[i]);
+                if (tid == 0) st.H[(j + 1) + LD * j] = mk<T>(hn, 0);
+                __syncwarp();
+                if (tid == 0) {
+                    Z* Hc = st.H + LD * j;
+                    Z* Rc = st.Rm + LD * j;
+                    Z p = Hc[0];
+#pragma unroll 4
+                    for (int t = 0; t < j; ++t) {
+                        Z q = Hc[t + 1];
+                        rot_<T>(st.rc[t], st.rs[t], p, q);
+                        Rc[t] = p;
+                        p = q;
+                    }
+                    T cc;
+                    Z ss, rr;
+                    givens_<T>(p, mk<T>(hn, 0), cc, ss, rr);
+                    Rc[j] = rr;
+                    st.rc[j] = cc;
+                    st.rs[j] = ss;
+                    rot_<T>(cc, ss, st.g[j], st.g[j + 1]);
+                    const double res = (double)cabs_<T>(st.g[j + 1]);
+                    S.ctl[0] = (res <= tol_abs) ? 1 : 0;
+                    S.ctl[1] = (hn == T(0)) ? 1 : 0;
+                }
+                __syncwarp();
+            }
+            cluster_wait();  // v_{j+1} complete in every CTA
+            __syncthreads();
             ++iters;
             conv = S.ctl[0];
             stop = S.ctl[0] | S.ctl[1];
-            __syncthreads();
         }
         // ---- finish the cycle: d = R^{-1} g, rho = c - H d, x += V d, r = V rho ----
         const int jj = j;
