@@ -71,6 +71,7 @@ struct ClusterSmem {
     C2<T> h1[MSMAX + 1];
     C2<T> xs[MAX_SPC][5][NDOF];          // staged neighbour rows
     int nbt[MAX_NB_SITES][5];            // neighbour site of each own site and direction
+    int pusht[MAX_SPC][5];               // where each own row goes: (CTA, site, direction) of xs
     Small<T> st;
     T scal[8];
     int ctl[8];
@@ -212,6 +213,19 @@ __device__ __forceinline__ long nbr_site(long s, int d, int Nx, int Nt) {
 // At most 80 registers a thread: two CTAs of 384 threads (16 coarse sites)
 // then fit on one SM (2 x 384 x 80 <= 65536), as do their shared-memory
 // slices, so the solves of concurrent streams can share SMs.
+// Write element k of own row (site ls) of a new basis vector into the five
+// staging slots that read it (push mode).
+template <typename T>
+__device__ __forceinline__ void push_row(cg::cluster_group& cluster, ClusterSmem<T>& S, int e, C2<T> v) {
+    const int ls = e / NDOF, kk = e - ls * NDOF;
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        const int code = S.pusht[ls][q];
+        C2<T>* dst = &S.xs[(code >> 3) & 0x1fff][code & 7][kk];
+        *cluster.map_shared_rank(dst, code >> 16) = v;
+    }
+}
+
 template <typename T>
 __global__ void __maxnreg__(80) k_coarse_proj(CoopArgs<T> a) {
     using Z = C2<T>;
@@ -247,6 +261,23 @@ __global__ void __maxnreg__(80) k_coarse_proj(CoopArgs<T> a) {
     }
     if (table)
         for (int e = tid; e < my_sites * 5; e += nt) S.nbt[e / 5][e % 5] = (int)nbr_site(s0 + e / 5, e % 5, a.Nx, a.Nt);
+    // Push mode (the basis slice in shared memory and every CTA's sites in one
+    // staging chunk): each new basis row is written straight into the staging
+    // slots xs of the five sites that read it (self, -x, +x, -t, +t neighbours;
+    // other CTAs' through distributed shared memory), so the apply after the
+    // next barrier reads only local shared memory and the basis never goes
+    // through global memory.  Slot q of own site u: the site w whose xs[w][d]
+    // holds v(u), i.e. u = nbr(w, d).
+    const bool push = a.vs && a.spc <= MAX_SPC;
+    if (push)
+        for (int e = tid; e < my_sites * 5; e += nt) {
+            const int ls = e / 5, q = e - ls * 5;
+            const long u = s0 + ls;
+            const int from[5] = {0, 2, 1, 4, 3};  // w = nbr(u, from[q]), d = q
+            const long w = nbr_site(u, from[q], a.Nx, a.Nt);
+            const int owner = (int)(w / a.spc);
+            S.pusht[ls][q] = (owner << 16) | ((int)(w - (long)owner * a.spc) << 3) | q;
+        }
 
     Z* xl = a.x + r0;
     Z* rl = a.r + r0;
@@ -318,7 +349,10 @@ __global__ void __maxnreg__(80) k_coarse_proj(CoopArgs<T> a) {
             for (int e = tid; e < nrows; e += nt) {
                 const Z v = cscale(rl[e], sc);
                 Vl[e] = v;
-                if (a.vs) a.V[r0 + e] = v;
+                if (push)
+                    push_row<T>(cluster, S, e, v);
+                else if (a.vs)
+                    a.V[r0 + e] = v;
             }
         }
         cluster.sync();  // v_0 complete in every CTA
@@ -330,12 +364,14 @@ __global__ void __maxnreg__(80) k_coarse_proj(CoopArgs<T> a) {
             // time: stage the five neighbour rows of each site (other CTAs' rows: through L2)
             for (int c0 = 0; c0 < my_sites; c0 += MAX_SPC) {
                 const int cs = min(MAX_SPC, my_sites - c0);
-                for (int e = tid; e < cs * 5 * NDOF; e += nt) {
-                    const int ls = e / (5 * NDOF), rem = e - ls * 5 * NDOF, d = rem / NDOF, l = rem - d * NDOF;
-                    const long nbs = table ? (long)S.nbt[c0 + ls][d] : nbr_site(s0 + c0 + ls, d, a.Nx, a.Nt);
-                    S.xs[ls][d][l] = __ldcg(vj + nbs * NDOF + l);
+                if (!push) {
+                    for (int e = tid; e < cs * 5 * NDOF; e += nt) {
+                        const int ls = e / (5 * NDOF), rem = e - ls * 5 * NDOF, d = rem / NDOF, l = rem - d * NDOF;
+                        const long nbs = table ? (long)S.nbt[c0 + ls][d] : nbr_site(s0 + c0 + ls, d, a.Nx, a.Nt);
+                        S.xs[ls][d][l] = __ldcg(vj + nbs * NDOF + l);
+                    }
+                    __syncthreads();
                 }
-                __syncthreads();
                 for (int e = tid; e < cs * NDOF; e += nt) {
                     const int ls = e / NDOF, kk = e - ls * NDOF;
                     const Z* Ab = a.A + (s0 + c0 + ls) * (5L * NDOF * NDOF) + kk;
@@ -371,7 +407,10 @@ __global__ void __maxnreg__(80) k_coarse_proj(CoopArgs<T> a) {
                 for (int e = tid; e < nrows; e += nt) {
                     const Z v = cscale(accum_rows<T, true>(wl[e], Vl, ldv, e, S.red, j + 1), sc);
                     wl[e] = v;
-                    if (a.vs) wg[e] = v;
+                    if (push)
+                        push_row<T>(cluster, S, e, v);
+                    else if (a.vs)
+                        wg[e] = v;
                 }
             }
             __syncwarp();
