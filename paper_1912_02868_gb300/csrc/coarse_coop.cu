@@ -46,7 +46,7 @@ namespace {
 constexpr int NDOF = 24;
 constexpr int MAX_THREADS = 512;
 constexpr int MAX_SPC = 16;       // sites per apply chunk (staged neighbour rows)
-constexpr int MAX_NB_SITES = 256; // sites per CTA in the neighbour table
+constexpr int MAX_NB_SITES = 64;  // sites per CTA in the neighbour table
 constexpr int MAX_CLUSTER = 16;    // CTAs of one cluster (non-portable size)
 constexpr size_t SMEM_LIMIT = 227 * 1024;
 
@@ -78,10 +78,15 @@ struct ClusterSmem {
 };
 
 // dynamic shared memory: ClusterSmem, then (optionally) the basis slice
-// Vs[(ms + 1)][rows]
+// Vs[(ms + 1)][rows], then the projection matrices M (k x (k+1)) and
+// N ((k+1) x (k+1)), both column-major
 template <typename T>
 __host__ __device__ inline size_t slice_bytes(int ms, int rows) {
     return (size_t)(ms + 1) * rows * sizeof(C2<T>);
+}
+template <typename T>
+__host__ __device__ inline size_t proj_bytes(int k) {
+    return (size_t)(k * (k + 1) + (k + 1) * (k + 1)) * sizeof(C2<T>);
 }
 
 template <typename R>
@@ -97,17 +102,18 @@ __device__ __forceinline__ C2<R> cdiv_(C2<R> a, C2<R> b) {
     return mk<R>((a.x * r + a.y) / den, (a.y * r - a.x) / den);
 }
 
-// Complex Givens rotation G = [[c, s], [-conj(s), c]] with G [a; b] = [r; 0].
+// Complex Givens rotation G = [[c, s], [-conj(s), c]] with G [a; h] = [r; 0]
+// for a real, non-negative h (the new subdiagonal entry).
 template <typename R>
-__device__ __forceinline__ void givens_(C2<R> a, C2<R> b, R& c, C2<R>& s, C2<R>& r) {
-    const R ab = cabs_<R>(b);
-    if (ab == R(0)) { c = R(1); s = mk<R>(0, 0); r = a; return; }
+__device__ __forceinline__ void givens_real_(C2<R> a, R h, R& c, C2<R>& s, C2<R>& r) {
+    if (h == R(0)) { c = R(1); s = mk<R>(0, 0); r = a; return; }
     const R aa = cabs_<R>(a);
-    if (aa == R(0)) { c = R(0); s = mk<R>(b.x / ab, -b.y / ab); r = mk<R>(ab, 0); return; }
-    const R rh = hypot(aa, ab);
-    c = aa / rh;
-    const C2<R> ph = mk<R>(a.x / aa, a.y / aa);
-    s = cscale(cmul(ph, conj_(b)), R(1) / rh);
+    if (aa == R(0)) { c = R(0); s = mk<R>(1, 0); r = mk<R>(h, 0); return; }
+    const R rh = sqrt(aa * aa + h * h);
+    const R inv_aa = R(1) / aa, inv_rh = R(1) / rh;
+    c = aa * inv_rh;
+    const C2<R> ph = mk<R>(a.x * inv_aa, a.y * inv_aa);
+    s = cscale(ph, h * inv_rh);
     r = cscale(ph, rh);
 }
 template <typename R>
@@ -185,8 +191,9 @@ __device__ void reduce_inbox(const C2<T>* inbox, int nr, int n, C2<T>* red) {
     for (int i = warp; i < n; i += nw) {
         C2<T> a = mk<T>(0, 0);
         if (lane < nr) a = inbox[lane * PSTR + i];
+        // at most MAX_CLUSTER = 16 partials: lanes 16..31 hold zeros
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
+        for (int o = MAX_CLUSTER / 2; o > 0; o >>= 1) {
             a.x += __shfl_xor_sync(0xffffffffu, a.x, o);
             a.y += __shfl_xor_sync(0xffffffffu, a.y, o);
         }
@@ -279,6 +286,35 @@ __global__ void __maxnreg__(80) k_coarse_proj(CoopArgs<T> a) {
             S.pusht[ls][q] = (owner << 16) | ((int)(w - (long)owner * a.spc) << 3) | q;
         }
 
+    // Projection onto the deflation space, d = argmin ||W^+ r - H_k d||, as two
+    // small matrices fixed for the whole solve: d = M g and H_k d = N g with
+    // g = W^+ r, M = R^{-1} Q^+ from the QR factorisation of H_k (the stored
+    // rotations and R), N = H_k M.  Warp 0 builds column l of both by solving
+    // for g = e_l.
+    Z* Mp = reinterpret_cast<Z*>(smem_raw + sizeof(ClusterSmem<T>) +
+                                 (a.vs ? slice_bytes<T>(ms, a.spc * NDOF) : 0));
+    Z* Np = Mp + k * (k + 1);
+    if (tid < 32) {
+        const KState* P = a.pls;
+        for (int l = tid; l <= k; l += 32) {
+            Z g[KLD], dd[KMAX];
+            for (int i = 0; i <= k; ++i) g[i] = mk<T>(i == l ? T(1) : T(0), 0);
+            for (int t = 0; t < P->nrot; ++t)
+                rot_<T>((T)P->rc[t], from_d2<T>(P->rs[t]), g[P->ra[t]], g[P->rb[t]]);
+            for (int i = k - 1; i >= 0; --i) {
+                Z acc = g[i];
+                for (int m = i + 1; m < k; ++m) acc = csub(acc, cmul(from_d2<T>(P->R[i + KLD * m]), dd[m]));
+                dd[i] = cdiv_<T>(acc, from_d2<T>(P->R[i + KLD * i]));
+            }
+            for (int i = 0; i < k; ++i) Mp[i + k * l] = dd[i];
+            for (int i = 0; i <= k; ++i) {
+                Z acc = mk<T>(0, 0);
+                for (int m = 0; m < k; ++m) acc = cfma(from_d2<T>(P->H[i + KLD * m]), dd[m], acc);
+                Np[i + (k + 1) * l] = acc;
+            }
+        }
+    }
+
     Z* xl = a.x + r0;
     Z* rl = a.r + r0;
     // x = 0, r = f, ||f||^2
@@ -299,22 +335,15 @@ __global__ void __maxnreg__(80) k_coarse_proj(CoopArgs<T> a) {
         push_gram<T>(cluster, Wl, ldw, k + 1, rl, nrows, false, &S.inbox[1][0][0]);
         cluster.sync();
         reduce_inbox<T>(&S.inbox[1][0][0], ncta, k + 1, S.red);
-        if (tid == 0) {
-            const KState* P = a.pls;
-            Z g[KLD];
-            for (int i = 0; i <= k; ++i) g[i] = S.red[i];
-            for (int t = 0; t < P->nrot; ++t)
-                rot_<T>((T)P->rc[t], from_d2<T>(P->rs[t]), g[P->ra[t]], g[P->rb[t]]);
-            for (int i = k - 1; i >= 0; --i) {
-                Z acc = g[i];
-                for (int l = i + 1; l < k; ++l) acc = csub(acc, cmul(from_d2<T>(P->R[i + KLD * l]), st.pd[l]));
-                st.pd[i] = cdiv_<T>(acc, from_d2<T>(P->R[i + KLD * i]));
+        for (int i = tid; i <= k; i += nt) {
+            Z pdv = mk<T>(0, 0), puv = mk<T>(0, 0);
+            for (int l = 0; l <= k; ++l) {
+                const Z gl = S.red[l];
+                if (i < k) pdv = cfma(Mp[i + k * l], gl, pdv);
+                puv = cfma(Np[i + (k + 1) * l], gl, puv);
             }
-            for (int i = 0; i <= k; ++i) {
-                Z acc = mk<T>(0, 0);
-                for (int l = 0; l < k; ++l) acc = cfma(from_d2<T>(P->H[i + KLD * l]), st.pd[l], acc);
-                st.pu[i] = acc;
-            }
+            if (i < k) st.pd[i] = pdv;
+            st.pu[i] = puv;
         }
         __syncthreads();
         for (int e = tid; e < nrows; e += nt) {
@@ -388,9 +417,7 @@ __global__ void __maxnreg__(80) k_coarse_proj(CoopArgs<T> a) {
             }
             push_gram<T>(cluster, Vl, ldv, j + 1, wl, nrows, false, &S.inbox[1][0][0]);
             cluster.sync();
-            reduce_inbox<T>(&S.inbox[1][0][0], ncta, j + 1, S.red);
-            for (int i = tid; i <= j; i += nt) S.h1[i] = S.red[i];
-            __syncthreads();
+            reduce_inbox<T>(&S.inbox[1][0][0], ncta, j + 1, S.h1);
             for (int e = tid; e < nrows; e += nt) wl[e] = accum_rows<T, true>(wl[e], Vl, ldv, e, S.h1, j + 1);
             __syncthreads();
             push_gram<T>(cluster, Vl, ldv, j + 1, wl, nrows, true, &S.inbox[0][0][0]);
@@ -435,7 +462,7 @@ __global__ void __maxnreg__(80) k_coarse_proj(CoopArgs<T> a) {
                     }
                     T cc;
                     Z ss, rr;
-                    givens_<T>(p, mk<T>(hn, 0), cc, ss, rr);
+                    givens_real_<T>(p, hn, cc, ss, rr);
                     Rc[j] = rr;
                     st.rc[j] = cc;
                     st.rs[j] = ss;
@@ -461,11 +488,12 @@ __global__ void __maxnreg__(80) k_coarse_proj(CoopArgs<T> a) {
                 const Z piv = st.Rm[i + LD * i];
                 st.d[i] = (piv.x == T(0) && piv.y == T(0)) ? mk<T>(0, 0) : cdiv_<T>(acc, piv);
             }
-            for (int i = 0; i <= jj; ++i) {
-                Z acc = st.c[i];
-                for (int l = 0; l < jj; ++l) acc = csub(acc, cmul(st.H[i + LD * l], st.d[l]));
-                st.rho[i] = acc;
-            }
+        }
+        __syncthreads();
+        for (int i = tid; i <= jj; i += nt) {
+            Z acc = st.c[i];
+            for (int l = 0; l < jj; ++l) acc = csub(acc, cmul(st.H[i + LD * l], st.d[l]));
+            st.rho[i] = acc;
         }
         __syncthreads();
         for (int e = tid; e < nrows; e += nt) {
@@ -491,7 +519,7 @@ struct Geometry {
 };
 
 template <typename T>
-mg_status geometry(long nsite, int ms, Geometry& g) {
+mg_status geometry(long nsite, int ms, int k, Geometry& g) {
     static bool configured[2][16] = {};
     int dev = 0;
     MG_CUDA_TRY(cudaGetDevice(&dev));
@@ -512,7 +540,7 @@ mg_status geometry(long nsite, int ms, Geometry& g) {
         int threads = ((rows + 31) / 32) * 32;
         threads = std::min(std::max(threads, 64), MAX_THREADS);
         for (int vs = 1; vs >= 0; --vs) {
-            const size_t smem = sizeof(ClusterSmem<T>) + (vs ? slice_bytes<T>(ms, rows) : 0);
+            const size_t smem = sizeof(ClusterSmem<T>) + (vs ? slice_bytes<T>(ms, rows) : 0) + proj_bytes<T>(k);
             if (smem > SMEM_LIMIT) continue;
             cudaLaunchConfig_t cfg{};
             cudaLaunchAttribute attr[1];
@@ -553,7 +581,7 @@ mg_status launch_coarse_proj(const CoopArgs<T>& args_in, cudaStream_t s) {
         return MG_EINVAL;
     }
     Geometry g;
-    MG_TRY(geometry<T>((long)a.Nx * a.Nt, a.ms, g));
+    MG_TRY(geometry<T>((long)a.Nx * a.Nt, a.ms, a.k, g));
     a.spc = g.spc;
     a.vs = g.vs;
     cudaLaunchConfig_t cfg{};
