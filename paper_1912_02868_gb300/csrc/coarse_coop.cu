@@ -450,13 +450,17 @@ __global__ void __maxnreg__(80) k_coarse_proj(CoopArgs<T> a) {
                 if (tid == 0) st.H[(j + 1) + LD * j] = mk<T>(hn, 0);
                 __syncwarp();
                 if (tid == 0) {
-                    Z* Hc = st.H + LD * j;
-                    Z* Rc = st.Rm + LD * j;
+                    // distinct arrays: the loads of later rotations need not wait
+                    // for the stores of earlier ones
+                    const Z* __restrict__ Hc = st.H + LD * j;
+                    Z* __restrict__ Rc = st.Rm + LD * j;
+                    const T* __restrict__ rcs = st.rc;
+                    const Z* __restrict__ rss = st.rs;
                     Z p = Hc[0];
-#pragma unroll 4
+#pragma unroll 8
                     for (int t = 0; t < j; ++t) {
                         Z q = Hc[t + 1];
-                        rot_<T>(st.rc[t], st.rs[t], p, q);
+                        rot_<T>(rcs[t], rss[t], p, q);
                         Rc[t] = p;
                         p = q;
                     }
