@@ -139,7 +139,8 @@ def run_serving(mg, torch, np, dev, rank, nreq=24, rate=3.0, workers=10):
 
 
 def dist_env():
-    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+    from paper_1912_02868_gb300 import replicas
+    return replicas.rank_env()
 
 
 def measured_peaks():
@@ -291,8 +292,10 @@ def run_native(args):
         torch.cuda.synchronize()
         return hs, time.perf_counter() - t0
 
-    # right-hand sides: step s, config c, rank r -> seed (L, c, 100000 r + s); resident in HBM
-    B = torch.stack([torch.stack([torch.from_numpy(synth.rhs(L, c, 100000 * rank + s)[0]) for c in range(nconf)])
+    # right-hand sides: step s, config c, rank r -> seed (L, c, rhs_index(r, s)); resident in HBM
+    from paper_1912_02868_gb300 import replicas
+    B = torch.stack([torch.stack([torch.from_numpy(synth.rhs(L, c, replicas.rhs_index(rank, s))[0])
+                                  for c in range(nconf)])
                      for s in range(W + K)]).to(dev)
     X = torch.zeros((nconf,) + B.shape[2:], dtype=torch.complex128, device=dev)
 
@@ -349,11 +352,7 @@ def run_native(args):
         return ms, lat, iters_all, worst, launches, kt
 
     def max_over_ranks(v):
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+        return replicas.max_over_ranks(v, device=dev)
 
     # ---------------- mixed precision (headline) ----------------
     hs, setup_s = make_handles(mg.MG_MIXED)
@@ -362,7 +361,7 @@ def run_native(args):
     ms, lat, iters, worst, launches, kt = run_steps(hs, range(W, W + K), True, timer_levels=(1, 2))
     clocks = clk.stop()
     ms = max_over_ranks(ms)
-    solves = world * K * nconf
+    solves = replicas.total_units(world, K, nconf)
     value = solves / (ms / 1e3)
     assert worst <= TOL, f"a solve missed the tolerance: {worst}"
 
