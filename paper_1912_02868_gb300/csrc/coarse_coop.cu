@@ -13,10 +13,12 @@
 // Work split: CTA b of the cluster owns sites [b*spc, (b+1)*spc) and their 24
 // dofs.  When it fits, the CTA keeps its rows of the Krylov basis in shared
 // memory, so the Gram and update passes never leave the SM (the deflation
-// space, read once per cycle, stays in global memory).  The basis is also
-// written to global memory (L2-resident), from where the stencil apply stages
-// the five neighbour rows of each own site (rows of other CTAs, written before
-// the previous barrier).  Neighbour indices are tabulated once per launch.
+// space, read once per cycle, stays in global memory).  Each new basis row is
+// then pushed straight into the staging slots of the five sites whose apply
+// reads it (push mode, other CTAs' slots by distributed shared-memory stores).
+// Otherwise the basis goes through global memory (L2-resident), from where the
+// apply stages the five neighbour rows of each own site.  Neighbour and push
+// tables are built once per launch.
 //
 // Per Arnoldi step j (CGS2, as in the rest of the library):
 //   w = A v_j; h1 = V^+ w: partials pushed to every CTA          [barrier]
@@ -102,25 +104,51 @@ __device__ __forceinline__ C2<R> cdiv_(C2<R> a, C2<R> b) {
     return mk<R>((a.x * r + a.y) / den, (a.y * r - a.x) / den);
 }
 
+template <typename R>
+__device__ __forceinline__ R rsqrt_(R x) {
+    if constexpr (std::is_same<R, float>::value)
+        return rsqrtf(x);
+    else
+        return rsqrt(x);
+}
+
 // Complex Givens rotation G = [[c, s], [-conj(s), c]] with G [a; h] = [r; 0]
 // for a real, non-negative h (the new subdiagonal entry).
 template <typename R>
 __device__ __forceinline__ void givens_real_(C2<R> a, R h, R& c, C2<R>& s, C2<R>& r) {
     if (h == R(0)) { c = R(1); s = mk<R>(0, 0); r = a; return; }
-    const R aa = cabs_<R>(a);
-    if (aa == R(0)) { c = R(0); s = mk<R>(1, 0); r = mk<R>(h, 0); return; }
-    const R rh = sqrt(aa * aa + h * h);
-    const R inv_aa = R(1) / aa, inv_rh = R(1) / rh;
-    c = aa * inv_rh;
+    const R aa2 = a.x * a.x + a.y * a.y;
+    if (aa2 == R(0)) { c = R(0); s = mk<R>(1, 0); r = mk<R>(h, 0); return; }
+    // reciprocal square roots only: no divide on this serial path
+    const R rh2 = aa2 + h * h;
+    const R inv_aa = rsqrt_(aa2), inv_rh = rsqrt_(rh2);
+    c = aa2 * inv_aa * inv_rh;
     const C2<R> ph = mk<R>(a.x * inv_aa, a.y * inv_aa);
     s = cscale(ph, h * inv_rh);
-    r = cscale(ph, rh);
+    r = cscale(ph, rh2 * inv_rh);
 }
 template <typename R>
 __device__ __forceinline__ void rot_(R c, C2<R> s, C2<R>& up, C2<R>& uq) {
     const C2<R> p = up, q = uq;
     up = cadd(cscale(p, c), cmul(s, q));
     uq = csub(cscale(q, c), cmul(conj_(s), p));
+}
+
+// Store v at the address dst has in the shared memory of CTA `rank` of the
+// cluster (a plain shared-memory store when rank == me).
+template <typename T>
+__device__ __forceinline__ void st_rank(C2<T>* dst, int rank, int me, C2<T> v) {
+    if (rank == me) {
+        *dst = v;
+        return;
+    }
+    const unsigned la = (unsigned)__cvta_generic_to_shared(dst);
+    unsigned ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(ra) : "r"(la), "r"(rank));
+    if constexpr (std::is_same<T, float>::value)
+        asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};\n" ::"r"(ra), "f"(v.x), "f"(v.y) : "memory");
+    else
+        asm volatile("st.shared::cluster.v2.f64 [%0], {%1, %2};\n" ::"r"(ra), "d"(v.x), "d"(v.y) : "memory");
 }
 
 // Partials of nd inner products conj(X[i]) . y over the CTA's rows (X, y point
@@ -217,24 +245,24 @@ __device__ __forceinline__ long nbr_site(long s, int d, int Nx, int Nt) {
     return s;
 }
 
-// At most 80 registers a thread: two CTAs of 384 threads (16 coarse sites)
-// then fit on one SM (2 x 384 x 80 <= 65536), as do their shared-memory
-// slices, so the solves of concurrent streams can share SMs.
 // Write element k of own row (site ls) of a new basis vector into the five
 // staging slots that read it (push mode).
 template <typename T>
-__device__ __forceinline__ void push_row(cg::cluster_group& cluster, ClusterSmem<T>& S, int e, C2<T> v) {
+__device__ __forceinline__ void push_row(ClusterSmem<T>& S, int me, int e, C2<T> v) {
     const int ls = e / NDOF, kk = e - ls * NDOF;
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
         const int code = S.pusht[ls][q];
-        C2<T>* dst = &S.xs[(code >> 3) & 0x1fff][code & 7][kk];
-        *cluster.map_shared_rank(dst, code >> 16) = v;
+        st_rank<T>(&S.xs[(code >> 3) & 0x1fff][code & 7][kk], code >> 16, me, v);
     }
 }
 
+// At most 128 registers a thread, so that a CTA of up to 512 threads fits one
+// SM (512 x 128 = 65536).  A solve is latency-bound; the registers go to more
+// operator loads in flight in the apply, which was measured faster, also with
+// ten concurrent solves, than fitting two CTAs per SM with 80 registers.
 template <typename T>
-__global__ void __maxnreg__(80) k_coarse_proj(CoopArgs<T> a) {
+__global__ void __maxnreg__(128) k_coarse_proj(CoopArgs<T> a) {
     using Z = C2<T>;
     cg::cluster_group cluster = cg::this_cluster();
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -379,7 +407,7 @@ __global__ void __maxnreg__(80) k_coarse_proj(CoopArgs<T> a) {
                 const Z v = cscale(rl[e], sc);
                 Vl[e] = v;
                 if (push)
-                    push_row<T>(cluster, S, e, v);
+                    push_row<T>(S, rank, e, v);
                 else if (a.vs)
                     a.V[r0 + e] = v;
             }
@@ -425,8 +453,10 @@ __global__ void __maxnreg__(80) k_coarse_proj(CoopArgs<T> a) {
             reduce_inbox<T>(&S.inbox[0][0][0], ncta, j + 2, S.red);
             // h_{j+1,j} = ||w - V h2|| = sqrt(n2 - |h2|^2) (V orthonormal), computed
             // identically by every thread; then v_{j+1} = (w - V h2) / h_{j+1,j}
-            T h2n = 0;
-            for (int i = 0; i <= j; ++i) h2n += S.red[i].x * S.red[i].x + S.red[i].y * S.red[i].y;
+            T h2n = 0;  // warp butterfly: the same value in every lane and warp
+            for (int i = tid & 31; i <= j; i += 32) h2n += S.red[i].x * S.red[i].x + S.red[i].y * S.red[i].y;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) h2n += __shfl_xor_sync(0xffffffffu, h2n, o);
             const T hn = sqrt(fmax((T)S.red[j + 1].x - h2n, T(0)));
             {
                 const T sc = hn > T(0) ? T(1) / hn : T(0);
@@ -435,7 +465,7 @@ __global__ void __maxnreg__(80) k_coarse_proj(CoopArgs<T> a) {
                     const Z v = cscale(accum_rows<T, true>(wl[e], Vl, ldv, e, S.red, j + 1), sc);
                     wl[e] = v;
                     if (push)
-                        push_row<T>(cluster, S, e, v);
+                        push_row<T>(S, rank, e, v);
                     else if (a.vs)
                         wg[e] = v;
                 }
@@ -471,8 +501,8 @@ __global__ void __maxnreg__(80) k_coarse_proj(CoopArgs<T> a) {
                     st.rc[j] = cc;
                     st.rs[j] = ss;
                     rot_<T>(cc, ss, st.g[j], st.g[j + 1]);
-                    const double res = (double)cabs_<T>(st.g[j + 1]);
-                    S.ctl[0] = (res <= tol_abs) ? 1 : 0;
+                    const Z gn = st.g[j + 1];
+                    S.ctl[0] = ((double)(gn.x * gn.x + gn.y * gn.y) <= tol_abs * tol_abs) ? 1 : 0;
                     S.ctl[1] = (hn == T(0)) ? 1 : 0;
                 }
                 __syncwarp();
