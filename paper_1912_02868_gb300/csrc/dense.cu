@@ -14,38 +14,41 @@ namespace mg {
 namespace {
 
 __device__ __forceinline__ double cabsd(double2 a) { return sqrt(a.x * a.x + a.y * a.y); }
+__device__ __forceinline__ double cabs2d(double2 a) { return a.x * a.x + a.y * a.y; }
+__device__ __forceinline__ double cabs1d(double2 a) { return fabs(a.x) + fabs(a.y); }
+// a / b = a conj(b) / |b|^2 with one real reciprocal: FP64 divides and square
+// roots are long dependent sequences at this GPU's FP64 rate, and these sit on
+// serial paths.  (The entries here are O(1e-16..1e2), far from overflow.)
 __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
-    // Smith's algorithm
-    if (fabs(b.x) >= fabs(b.y)) {
-        double r = b.y / b.x, den = b.x + b.y * r;
-        return make_double2((a.x + a.y * r) / den, (a.y - a.x * r) / den);
-    }
-    double r = b.x / b.y, den = b.x * r + b.y;
-    return make_double2((a.x * r + a.y) / den, (a.y * r - a.x) / den);
+    const double inv = 1.0 / cabs2d(b);
+    return make_double2((a.x * b.x + a.y * b.y) * inv, (a.y * b.x - a.x * b.y) * inv);
 }
 __device__ __forceinline__ double2 z0() { return make_double2(0.0, 0.0); }
 
 // Complex Givens rotation G = [[c, s], [-conj(s), c]] with G [a; b] = [r; 0].
+// (reciprocal square roots only, no divide)
 __device__ __forceinline__ void givens(double2 a, double2 b, double& c, double2& s, double2& r) {
-    const double ab = cabsd(b);
-    if (ab == 0.0) {
+    const double ab2 = cabs2d(b);
+    if (ab2 == 0.0) {
         c = 1.0;
         s = z0();
         r = a;
         return;
     }
-    const double aa = cabsd(a);
-    if (aa == 0.0) {
+    const double aa2 = cabs2d(a);
+    if (aa2 == 0.0) {
+        const double inv_ab = rsqrt(ab2);
         c = 0.0;
-        s = make_double2(b.x / ab, -b.y / ab);
-        r = make_double2(ab, 0.0);
+        s = make_double2(b.x * inv_ab, -b.y * inv_ab);
+        r = make_double2(ab2 * inv_ab, 0.0);
         return;
     }
-    const double rho = hypot(aa, ab);
-    c = aa / rho;
-    const double2 ph = make_double2(a.x / aa, a.y / aa);
-    s = cscale(cmul(ph, conj_(b)), 1.0 / rho);
-    r = cscale(ph, rho);
+    const double rho2 = aa2 + ab2;
+    const double inv_aa = rsqrt(aa2), inv_rho = rsqrt(rho2);
+    c = aa2 * inv_aa * inv_rho;
+    const double2 ph = make_double2(a.x * inv_aa, a.y * inv_aa);
+    s = cscale(cmul(ph, conj_(b)), inv_rho);
+    r = cscale(ph, rho2 * inv_rho);
 }
 __device__ __forceinline__ void rot_apply(double c, double2 s, double2& up, double2& uq) {
     const double2 p = up, q = uq;
@@ -284,20 +287,19 @@ struct DRSmem {
 };
 
 __device__ double2 block_dot(const double2* a, const double2* b, int n, DRSmem& S) {
-    // sum_i conj(a_i) b_i over the CTA, returned to every thread
+    // sum_i conj(a_i) b_i (n <= KLD), returned to every thread: each warp
+    // computes it alone with a butterfly, so every lane of every warp holds the
+    // same value and no block barrier is needed
+    (void)S;
+    const int lane = threadIdx.x & 31;
     double2 acc = z0();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) acc = cfmac(a[i], b[i], acc);
-    S.redz[threadIdx.x] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double2 t = z0();
-        for (int i = 0; i < (int)blockDim.x; ++i) t = cadd(t, S.redz[i]);
-        S.redz[0] = t;
+    for (int i = lane; i < n; i += 32) acc = cfmac(a[i], b[i], acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
     }
-    __syncthreads();
-    const double2 r = S.redz[0];
-    __syncthreads();
-    return r;
+    return acc;
 }
 
 __global__ void __launch_bounds__(DR_THREADS) k_dr_restart(const KState* __restrict__ ks, DRState* dr, int k) {
@@ -320,9 +322,9 @@ __global__ void __launch_bounds__(DR_THREADS) k_dr_restart(const KState* __restr
     for (int p = 0; p < n; ++p) {
         if (tid == 0) {
             int best = p;
-            double bv = cabsd(S.Q[p + LDS * p]);
+            double bv = cabs2d(S.Q[p + LDS * p]);
             for (int r = p + 1; r < n; ++r) {
-                const double v = cabsd(S.Q[r + LDS * p]);
+                const double v = cabs2d(S.Q[r + LDS * p]);
                 if (v > bv) { bv = v; best = r; }
             }
             S.ctl[0] = best;
@@ -429,8 +431,9 @@ __global__ void __launch_bounds__(DR_THREADS) k_dr_restart(const KState* __restr
             while (hi > 0) {
                 l = hi;
                 while (l > 0) {
-                    const double sub = cabsd(S.T[l + LDS * (l - 1)]);
-                    const double dsum = cabsd(S.T[(l - 1) + LDS * (l - 1)]) + cabsd(S.T[l + LDS * l]);
+                    // magnitudes |re| + |im| (within a factor sqrt(2) of the modulus)
+                    const double sub = cabs1d(S.T[l + LDS * (l - 1)]);
+                    const double dsum = cabs1d(S.T[(l - 1) + LDS * (l - 1)]) + cabs1d(S.T[l + LDS * l]);
                     if (sub <= eps * dsum || sub < 1e-300) break;
                     --l;
                 }
@@ -460,7 +463,7 @@ __global__ void __launch_bounds__(DR_THREADS) k_dr_restart(const KState* __restr
                     sq.y = (disc2.y >= 0.0 ? 1.0 : -1.0) * sqrt(fmax(0.5 * (m - disc2.x), 0.0));
                     const double2 mid = cscale(cadd(a, d), 0.5);
                     const double2 m1 = cadd(mid, sq), m2 = csub(mid, sq);
-                    mu = (cabsd(csub(m1, d)) <= cabsd(csub(m2, d))) ? m1 : m2;
+                    mu = (cabs2d(csub(m1, d)) <= cabs2d(csub(m2, d))) ? m1 : m2;
                 }
                 S.mu = mu;
                 S.ctl[2] += 1;
@@ -514,9 +517,9 @@ __global__ void __launch_bounds__(DR_THREADS) k_dr_restart(const KState* __restr
         for (int i = 0; i < n; ++i) idx[i] = i;
         for (int i = 1; i < n; ++i) {  // insertion sort: stable
             const int t = idx[i];
-            const double vt = cabsd(S.T[t + LDS * t]);
+            const double vt = cabs2d(S.T[t + LDS * t]);
             int q = i - 1;
-            while (q >= 0 && cabsd(S.T[idx[q] + LDS * idx[q]]) > vt) {
+            while (q >= 0 && cabs2d(S.T[idx[q] + LDS * idx[q]]) > vt) {
                 idx[q + 1] = idx[q];
                 --q;
             }
@@ -530,9 +533,17 @@ __global__ void __launch_bounds__(DR_THREADS) k_dr_restart(const KState* __restr
     __syncthreads();
     // (g) eigenvectors: back substitution in T, then g = Q y (column a of G)
     {
-        double tnorm = 0.0;
-        for (int e = 0; e < n * n; ++e) tnorm = fmax(tnorm, cabsd(S.T[(e % n) + LDS * (e / n)]));
-        const double small = fmax(eps * tnorm, 1e-300);
+        // max |T_ij|, shared out over the CTA: strided maxima of |T_ij|^2, a warp
+        // butterfly, then the warps' maxima
+        double t2 = 0.0;
+        for (int e = tid; e < n * n; e += nt) t2 = fmax(t2, cabs2d(S.T[(e % n) + LDS * (e / n)]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t2 = fmax(t2, __shfl_xor_sync(0xffffffffu, t2, o));
+        if ((tid & 31) == 0) S.red[tid >> 5] = t2;
+        __syncthreads();
+        double tmax2 = 0.0;
+        for (int w = 0; w < (nt >> 5); ++w) tmax2 = fmax(tmax2, S.red[w]);
+        const double small = fmax(eps * sqrt(tmax2), 1e-300);
         for (int a = tid; a < k; a += nt) {
             const int q = S.sel[a];
             const double2 th = S.T[q + LDS * q];
@@ -543,7 +554,8 @@ __global__ void __launch_bounds__(DR_THREADS) k_dr_restart(const KState* __restr
                 double2 s = z0();
                 for (int m = r + 1; m <= q; ++m) s = cfma(S.T[r + LDS * m], y[m], s);
                 double2 den = csub(S.T[r + LDS * r], th);
-                if (cabsd(den) < small) den = make_double2(small, 0.0);
+                const double dd = cabs2d(den);
+                if (dd < small * small || dd == 0.0) den = make_double2(small, 0.0);
                 y[r] = cneg(cdiv(s, den));
             }
             for (int r = 0; r < n; ++r) {
