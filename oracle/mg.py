@@ -17,6 +17,17 @@ V-cycle on level l with right-hand side f (reading of Section 2):
     x += P (cycle or solve on level l+1 with P^+ r)
     r = f - A x                   (one operator application)
     x += S(r)
+
+Partial intermediate solve (Section 2, the variant with a partial solve on the
+intermediate grid).  The cycle on the intermediate grid is replaced by a solve
+of the intermediate system to relative residual 0.2.  Readings (the solver is
+not named in the paper):
+  * the solve is FGMRES(m) on the intermediate operator, with the same m as the
+    outer solver, preconditioned by the two-grid cycle above (smoothing on the
+    intermediate grid, coarse solve, smoothing);
+  * coarse solves inside the first outer iteration of a right-hand side go to
+    1e-8 (the first one of all by GMRES-DR, which builds the deflation space);
+    every later coarse solve is a projected solve to 1e-2.
 """
 from __future__ import annotations
 
@@ -28,7 +39,7 @@ from . import krylov
 class Params:
     def __init__(self, fgmres_m=8, smooth_steps=2, coarse="dr_proj", dr_m=30, dr_k=10,
                  coarse_tol_first=1e-14, coarse_tol_rest=1e-8, dr_max_cycles=100, max_outer=500,
-                 proj_max_cycles=1000):
+                 proj_max_cycles=1000, partial_tol=None, coarse_tol_partial=1e-2, partial_max_iters=200):
         self.fgmres_m = fgmres_m
         self.smooth_steps = smooth_steps
         self.coarse = coarse  # "dr_proj" | "cgne"
@@ -38,6 +49,9 @@ class Params:
         self.dr_max_cycles = dr_max_cycles
         self.max_outer = max_outer
         self.proj_max_cycles = proj_max_cycles
+        self.partial_tol = partial_tol  # None: V-cycle; else the intermediate partial solve's tolerance
+        self.coarse_tol_partial = coarse_tol_partial
+        self.partial_max_iters = partial_max_iters
 
 
 class MGSolver:
@@ -50,6 +64,9 @@ class MGSolver:
         self.counter = krylov.Counter(3)
         self.deflation = None
         self.coarse_solves = []  # (kind, iters) per coarse solve
+        self.coarse_tols = []    # tolerance of each coarse solve
+        self.partial_solves = []  # (iters, relres) per intermediate partial solve
+        self._precond_calls = 0  # preconditioner applications in the current solve
 
     def _op(self, level):
         shape = self.h.shapes[level]
@@ -67,19 +84,48 @@ class MGSolver:
         if p.coarse == "cgne":
             x, info = krylov.cgne(A2, self._op_dag(2), f, p.coarse_tol_rest)
             self.coarse_solves.append(("cgne", info.iters))
+            self.coarse_tols.append(p.coarse_tol_rest)
             return x
+        if p.partial_tol is None:
+            tol_dr, tol_proj = p.coarse_tol_first, p.coarse_tol_rest
+        else:  # first outer iteration of this right-hand side: 1e-8, later 1e-2
+            tol_dr = p.coarse_tol_rest
+            tol_proj = p.coarse_tol_rest if self._precond_calls <= 1 else p.coarse_tol_partial
         if self.deflation is None:
-            x, info, defl = krylov.gmres_dr(A2, f, p.dr_m, p.dr_k, p.coarse_tol_first, p.dr_max_cycles)
+            x, info, defl = krylov.gmres_dr(A2, f, p.dr_m, p.dr_k, tol_dr, p.dr_max_cycles)
             self.deflation = defl
             self.coarse_solves.append(("dr", info.iters))
+            self.coarse_tols.append(tol_dr)
             return x
-        x, info = krylov.gmres_proj(A2, f, self.deflation, p.dr_m, p.coarse_tol_rest, p.proj_max_cycles)
+        x, info = krylov.gmres_proj(A2, f, self.deflation, p.dr_m, tol_proj, p.proj_max_cycles)
         self.coarse_solves.append(("proj", info.iters))
+        self.coarse_tols.append(tol_proj)
+        return x
+
+    def twogrid(self, f):
+        """The cycle on the intermediate grid: smoothing there, coarse solve, smoothing."""
+        A = self._op(1)
+        shape = self.h.shapes[1]
+        x, r = krylov.smoother(A, f, self.p.smooth_steps)
+        ec = self.coarse_solve(self.h.restrict(1, r.reshape(shape)).ravel())
+        x = x + self.h.prolong(1, ec.reshape(self.h.shapes[2])).ravel()
+        r = f - A(x)
+        e, _ = krylov.smoother(A, r, self.p.smooth_steps)
+        return x + e
+
+    def partial_solve(self, f):
+        """Intermediate system solved to ||f - A x|| <= partial_tol ||f|| by FGMRES
+        preconditioned with the two-grid cycle."""
+        x, info = krylov.fgmres(self._op(1), f, self.twogrid, self.p.partial_tol, m=self.p.fgmres_m,
+                                max_iters=self.p.partial_max_iters)
+        self.partial_solves.append((info.iters, info.relres))
         return x
 
     def vcycle(self, level, f):
         if level == 2:
             return self.coarse_solve(f)
+        if level == 1 and self.p.partial_tol is not None:
+            return self.partial_solve(f)
         A = self._op(level)
         shape = self.h.shapes[level]
         x, r = krylov.smoother(A, f, self.p.smooth_steps)
@@ -94,8 +140,13 @@ class MGSolver:
         """Solve D x = b (b complex[L_t][L_x][2]) to true relative residual tol."""
         shape = self.h.shapes[0]
         bf = np.asarray(b, dtype=np.complex128).ravel()
-        x, info = krylov.fgmres(self._op(0), bf, lambda v: self.vcycle(0, v), tol, m=self.p.fgmres_m,
-                                max_iters=self.p.max_outer)
+        self._precond_calls = 0
+
+        def precond(v):
+            self._precond_calls += 1
+            return self.vcycle(0, v)
+
+        x, info = krylov.fgmres(self._op(0), bf, precond, tol, m=self.p.fgmres_m, max_iters=self.p.max_outer)
         return x.reshape(shape), info
 
     def fine_equivalent_mvps(self):

@@ -5,7 +5,12 @@
 * the CGNE comparison arm solves the same system;
 * the deflation space is built by the first coarse solve and reused (GMRES-Proj)
   by every later coarse solve, also for a second right-hand side;
-* Eq. 1's dimension ratios n_int / n_fine = 0.75 and n_coarse / n_fine = 3/64.
+* Eq. 1's dimension ratios n_int / n_fine = 0.75 and n_coarse / n_fine = 3/64;
+* the partial intermediate solve (Section 2's variant): each intermediate solve
+  meets ||f - P^+ D P x|| <= 0.2 ||f|| with the product of independently
+  assembled dense matrices; the whole solve still agrees with a direct solve;
+  and the coarse tolerances follow the schedule: 1e-8 within a right-hand
+  side's first outer iteration (GMRES-DR first), 1e-2 after it.
 """
 import numpy as np
 import pytest
@@ -91,3 +96,38 @@ def test_fine_equivalent_mvps_ratios():
     s = mg.MGSolver(h)
     s.counter.mvps = [10, 100, 1000]
     assert s.fine_equivalent_mvps() == 10 + 75 + 1000 * 3 / 64
+
+
+def test_partial_intermediate_solve(h16):
+    U, m0, h = h16
+    L = 16
+    # dense P^+ D P, assembled from the fine operator and the prolongator matrix
+    D = dirac.dense_from_apply(lambda v: dirac.wilson(U, v, m0), (L, L, 2))
+    P = hierarchy.dense_prolongator(h.Q0, (L, L, 2))
+    A1 = P.conj().T @ D @ P
+    s = mg.MGSolver(h, mg.Params(partial_tol=0.2))
+    b = synth.rhs(16, 0, 3)[0]
+    x, info = s.solve(b, 1e-10)
+    xs, A = _direct(U, m0, b)
+    assert info.converged and np.linalg.norm(A @ x.ravel() - b.ravel()) <= 1e-10 * np.linalg.norm(b)
+    smin = np.linalg.svd(A.toarray(), compute_uv=False)[-1]
+    kappa = np.linalg.norm(A.toarray(), 2) / smin
+    assert np.linalg.norm(x.ravel() - xs) <= kappa * 1e-10 * np.linalg.norm(xs)
+    assert s.partial_solves and all(rr <= 0.2 for _, rr in s.partial_solves)
+    # one intermediate solve by itself, checked with the dense operator
+    f = synth.complex_gaussian((A1.shape[0],), 7, 3)
+    x1 = s.partial_solve(f)
+    assert np.linalg.norm(f - A1 @ x1) <= 0.2 * np.linalg.norm(f)
+    # tolerance schedule of the coarse solves
+    kinds = [k for k, _ in s.coarse_solves]
+    assert kinds[0] == "dr" and s.coarse_tols[0] == 1e-8
+    assert 1e-2 in s.coarse_tols
+    first_loose = s.coarse_tols.index(1e-2)
+    assert all(t == 1e-8 for t in s.coarse_tols[:first_loose])
+    assert all(t == 1e-2 for t in s.coarse_tols[first_loose:])
+    # a second right-hand side: projected solves only, 1e-8 again in its first outer iteration
+    n0 = len(s.coarse_tols)
+    x2, info2 = s.solve(synth.rhs(16, 0, 4)[0], 1e-10)
+    assert info2.converged
+    assert all(k == "proj" for k, _ in s.coarse_solves[n0:])
+    assert s.coarse_tols[n0] == 1e-8 and s.coarse_tols[-1] == 1e-2
