@@ -158,8 +158,9 @@ __device__ __forceinline__ void st_rank(C2<T>* dst, int rank, int me, C2<T> v) {
 // shared memory instead of fetching from 16 remote ones.
 template <typename T>
 __device__ void push_gram(cg::cluster_group& cluster, const C2<T>* X, long ldx, int nd, const C2<T>* y, int nrows,
-                          bool norm, C2<T>* inbox) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+                          bool norm, C2<T>* inbox, int nw) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (warp >= nw) return;  // the least-squares warp takes no products
     const int nr = (int)cluster.num_blocks(), me = (int)cluster.block_rank();
     const int ntot = nd + (norm ? 1 : 0);
     for (int i = warp; i < ntot; i += nw) {
@@ -214,9 +215,9 @@ __device__ __forceinline__ C2<T> accum_rows(C2<T> acc, const C2<T>* X, long ldx,
 // gets the same result): red[i] = sum_r inbox[r][i], i < n.  Called after the
 // cluster barrier that follows the pushes.
 template <typename T>
-__device__ void reduce_inbox(const C2<T>* inbox, int nr, int n, C2<T>* red) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int i = warp; i < n; i += nw) {
+__device__ void reduce_inbox(const C2<T>* inbox, int nr, int n, C2<T>* red, int nw) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = warp; i < n && warp < nw; i += nw) {
         C2<T> a = mk<T>(0, 0);
         if (lane < nr) a = inbox[lane * PSTR + i];
         // at most MAX_CLUSTER = 16 partials: lanes 16..31 hold zeros
@@ -279,6 +280,10 @@ __global__ void __maxnreg__(128) k_coarse_proj(CoopArgs<T> a) {
     const int nrows = my_sites * NDOF;
     const int k = a.k, ms = a.ms;
     const int LD = MSMAX + 1;
+    // with a.lsw the last warp owns no rows: it runs the least-squares update of
+    // step j while the other (row) warps already apply A for step j + 1
+    const int nwr = (int)(blockDim.x >> 5) - (a.lsw ? 1 : 0);
+    const bool ls_warp = a.lsw && (tid >> 5) == nwr;
     const bool table = my_sites <= MAX_NB_SITES;
 
     // own rows of the basis: shared memory when it fits (the deflation space is
@@ -352,17 +357,53 @@ __global__ void __maxnreg__(128) k_coarse_proj(CoopArgs<T> a) {
     }
     __syncthreads();
     const int ncta = (int)cluster.num_blocks();
-    push_gram<T>(cluster, rl, 0, 0, rl, nrows, true, &S.inbox[0][0][0]);
+    push_gram<T>(cluster, rl, 0, 0, rl, nrows, true, &S.inbox[0][0][0], nwr);
     cluster.sync();
-    reduce_inbox<T>(&S.inbox[0][0][0], ncta, 1, S.red);
+    reduce_inbox<T>(&S.inbox[0][0][0], ncta, 1, S.red, nwr);
     const double nb = sqrt(fmax((double)S.red[0].x, 0.0));
     const double tol_abs = a.tol * nb;
     int iters = 0, cycles = 0, conv = 0;
+    // Least-squares update of step jc by one warp (lane = 0..31): column jc of H
+    // (h1 + h2, h_{jc+1,jc}), the previous rotations applied to it, the new
+    // rotation, and the stop flags from the residual estimate |g_{jc+1}|.  Reads
+    // S.h1 and S.red, which the step after jc overwrites only after its apply.
+    auto ls_update = [&](int lane, int jc, T hnv) {
+        for (int i = lane; i <= jc; i += 32) st.H[i + LD * jc] = cadd(S.h1[i], S.red[i]);
+        if (lane == 0) st.H[(jc + 1) + LD * jc] = mk<T>(hnv, 0);
+        __syncwarp();
+        if (lane == 0) {
+            // distinct arrays: the loads of later rotations need not wait for the
+            // stores of earlier ones
+            const Z* __restrict__ Hc = st.H + LD * jc;
+            Z* __restrict__ Rc = st.Rm + LD * jc;
+            const T* __restrict__ rcs = st.rc;
+            const Z* __restrict__ rss = st.rs;
+            Z p = Hc[0];
+#pragma unroll 8
+            for (int t = 0; t < jc; ++t) {
+                Z q = Hc[t + 1];
+                rot_<T>(rcs[t], rss[t], p, q);
+                Rc[t] = p;
+                p = q;
+            }
+            T cc;
+            Z ss, rr;
+            givens_real_<T>(p, hnv, cc, ss, rr);
+            Rc[jc] = rr;
+            st.rc[jc] = cc;
+            st.rs[jc] = ss;
+            rot_<T>(cc, ss, st.g[jc], st.g[jc + 1]);
+            const Z gn = st.g[jc + 1];
+            S.ctl[0] = ((double)(gn.x * gn.x + gn.y * gn.y) <= tol_abs * tol_abs) ? 1 : 0;
+            S.ctl[1] = (hnv == T(0)) ? 1 : 0;
+        }
+        __syncwarp();
+    };
     while (true) {
         // ---- projection onto the deflation space: d = argmin ||W^+ r - H_k d|| ----
-        push_gram<T>(cluster, Wl, ldw, k + 1, rl, nrows, false, &S.inbox[1][0][0]);
+        push_gram<T>(cluster, Wl, ldw, k + 1, rl, nrows, false, &S.inbox[1][0][0], nwr);
         cluster.sync();
-        reduce_inbox<T>(&S.inbox[1][0][0], ncta, k + 1, S.red);
+        reduce_inbox<T>(&S.inbox[1][0][0], ncta, k + 1, S.red, nwr);
         for (int i = tid; i <= k; i += nt) {
             Z pdv = mk<T>(0, 0), puv = mk<T>(0, 0);
             for (int l = 0; l <= k; ++l) {
@@ -379,9 +420,9 @@ __global__ void __maxnreg__(128) k_coarse_proj(CoopArgs<T> a) {
             rl[e] = accum_rows<T, true>(rl[e], Wl, ldw, e, st.pu, k + 1);
         }
         __syncthreads();
-        push_gram<T>(cluster, rl, 0, 0, rl, nrows, true, &S.inbox[0][0][0]);
+        push_gram<T>(cluster, rl, 0, 0, rl, nrows, true, &S.inbox[0][0][0], nwr);
         cluster.sync();
-        reduce_inbox<T>(&S.inbox[0][0][0], ncta, 1, S.red);
+        reduce_inbox<T>(&S.inbox[0][0][0], ncta, 1, S.red, nwr);
         const double beta = sqrt(fmax((double)S.red[0].x, 0.0));
         if (beta <= tol_abs || beta == 0.0) {
             conv = 1;
@@ -443,14 +484,18 @@ __global__ void __maxnreg__(128) k_coarse_proj(CoopArgs<T> a) {
                 }
                 __syncthreads();
             }
-            push_gram<T>(cluster, Vl, ldv, j + 1, wl, nrows, false, &S.inbox[1][0][0]);
+            if (a.lsw && j > 0) {  // step j - 1's update is complete (apply barrier)
+                conv = S.ctl[0];
+                if (S.ctl[0] | S.ctl[1]) break;  // step j is discarded: j columns
+            }
+            push_gram<T>(cluster, Vl, ldv, j + 1, wl, nrows, false, &S.inbox[1][0][0], nwr);
             cluster.sync();
-            reduce_inbox<T>(&S.inbox[1][0][0], ncta, j + 1, S.h1);
+            reduce_inbox<T>(&S.inbox[1][0][0], ncta, j + 1, S.h1, nwr);
             for (int e = tid; e < nrows; e += nt) wl[e] = accum_rows<T, true>(wl[e], Vl, ldv, e, S.h1, j + 1);
             __syncthreads();
-            push_gram<T>(cluster, Vl, ldv, j + 1, wl, nrows, true, &S.inbox[0][0][0]);
+            push_gram<T>(cluster, Vl, ldv, j + 1, wl, nrows, true, &S.inbox[0][0][0], nwr);
             cluster.sync();
-            reduce_inbox<T>(&S.inbox[0][0][0], ncta, j + 2, S.red);
+            reduce_inbox<T>(&S.inbox[0][0][0], ncta, j + 2, S.red, nwr);
             // h_{j+1,j} = ||w - V h2|| = sqrt(n2 - |h2|^2) (V orthonormal), computed
             // identically by every thread; then v_{j+1} = (w - V h2) / h_{j+1,j}
             T h2n = 0;  // warp butterfly: the same value in every lane and warp
@@ -472,46 +517,25 @@ __global__ void __maxnreg__(128) k_coarse_proj(CoopArgs<T> a) {
             }
             __syncwarp();
             cluster_arrive();  // v_{j+1} complete in this CTA
-            // meanwhile warp 0 updates the least squares: column j of H (h1 + h2,
-            // h_{j+1,j}), the previous rotations applied to it, the new rotation, and
-            // the residual estimate |g_{j+1}|
-            if (tid < 32) {
-                for (int i = tid; i <= j; i += 32) st.H[i + LD * j] = cadd(S.h1[i], S.red[i]);
-                if (tid == 0) st.H[(j + 1) + LD * j] = mk<T>(hn, 0);
-                __syncwarp();
-                if (tid == 0) {
-                    // distinct arrays: the loads of later rotations need not wait
-                    // for the stores of earlier ones
-                    const Z* __restrict__ Hc = st.H + LD * j;
-                    Z* __restrict__ Rc = st.Rm + LD * j;
-                    const T* __restrict__ rcs = st.rc;
-                    const Z* __restrict__ rss = st.rs;
-                    Z p = Hc[0];
-#pragma unroll 8
-                    for (int t = 0; t < j; ++t) {
-                        Z q = Hc[t + 1];
-                        rot_<T>(rcs[t], rss[t], p, q);
-                        Rc[t] = p;
-                        p = q;
-                    }
-                    T cc;
-                    Z ss, rr;
-                    givens_real_<T>(p, hn, cc, ss, rr);
-                    Rc[j] = rr;
-                    st.rc[j] = cc;
-                    st.rs[j] = ss;
-                    rot_<T>(cc, ss, st.g[j], st.g[j + 1]);
-                    const Z gn = st.g[j + 1];
-                    S.ctl[0] = ((double)(gn.x * gn.x + gn.y * gn.y) <= tol_abs * tol_abs) ? 1 : 0;
-                    S.ctl[1] = (hn == T(0)) ? 1 : 0;
-                }
-                __syncwarp();
+            if (a.lsw) {
+                cluster_wait();  // v_{j+1} complete in every CTA
+                // the least-squares warp updates step j while the row warps go on to
+                // step j + 1; its stop flags are read after that step's apply
+                if (ls_warp) ls_update(tid & 31, j, hn);
+                ++iters;
+            } else {
+                // warp 0 updates the least squares between arrive and wait
+                if (tid < 32) ls_update(tid, j, hn);
+                cluster_wait();  // v_{j+1} complete in every CTA
+                __syncthreads();
+                ++iters;
+                conv = S.ctl[0];
+                stop = S.ctl[0] | S.ctl[1];
             }
-            cluster_wait();  // v_{j+1} complete in every CTA
+        }
+        if (a.lsw && j == ms) {  // the last step's update, when no stop came before
             __syncthreads();
-            ++iters;
             conv = S.ctl[0];
-            stop = S.ctl[0] | S.ctl[1];
         }
         // ---- finish the cycle: d = R^{-1} g, rho = c - H d, x += V d, r = V rho ----
         const int jj = j;
@@ -548,7 +572,7 @@ __global__ void __maxnreg__(128) k_coarse_proj(CoopArgs<T> a) {
 }
 
 struct Geometry {
-    int cluster = 1, spc = 1, threads = 32, vs = 0;
+    int cluster = 1, spc = 1, threads = 32, vs = 0, lsw = 0;
     size_t smem = 0;
 };
 
@@ -576,6 +600,10 @@ mg_status geometry(long nsite, int ms, int k, Geometry& g) {
         for (int vs = 1; vs >= 0; --vs) {
             const size_t smem = sizeof(ClusterSmem<T>) + (vs ? slice_bytes<T>(ms, rows) : 0) + proj_bytes<T>(k);
             if (smem > SMEM_LIMIT) continue;
+            // push mode (basis in shared memory, one staging chunk) gets the extra
+            // least-squares warp
+            const int lsw = (vs && spc <= MAX_SPC) ? 1 : 0;
+            const int thr = threads + 32 * lsw;
             cudaLaunchConfig_t cfg{};
             cudaLaunchAttribute attr[1];
             attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -583,7 +611,7 @@ mg_status geometry(long nsite, int ms, int k, Geometry& g) {
             attr[0].val.clusterDim.y = 1;
             attr[0].val.clusterDim.z = 1;
             cfg.gridDim = dim3(ctas);
-            cfg.blockDim = dim3(threads);
+            cfg.blockDim = dim3(thr);
             cfg.dynamicSmemBytes = smem;
             cfg.attrs = attr;
             cfg.numAttrs = 1;
@@ -595,8 +623,9 @@ mg_status geometry(long nsite, int ms, int k, Geometry& g) {
             if (nclusters < 1) continue;
             g.cluster = ctas;
             g.spc = (int)spc;
-            g.threads = threads;
+            g.threads = thr;
             g.vs = vs;
+            g.lsw = lsw;
             g.smem = smem;
             return MG_OK;
         }
@@ -618,6 +647,7 @@ mg_status launch_coarse_proj(const CoopArgs<T>& args_in, cudaStream_t s) {
     MG_TRY(geometry<T>((long)a.Nx * a.Nt, a.ms, a.k, g));
     a.spc = g.spc;
     a.vs = g.vs;
+    a.lsw = g.lsw;
     cudaLaunchConfig_t cfg{};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;

@@ -30,6 +30,7 @@ struct CoopArgs {
     CoopStats* out;
     int spc;           // sites per CTA (set by the launcher)
     int vs;            // 1: own basis rows kept in shared memory (set by the launcher)
+    int lsw;           // 1: one extra warp runs the least-squares updates (set by the launcher)
 };
 
 template <typename T>
