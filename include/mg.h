@@ -79,6 +79,15 @@ typedef struct {
                               with > 1, the first right-hand side of a handle builds the
                               deflation space alone, then up to `parallel` solve contexts
                               (shared hierarchy, own workspaces and streams) share the rest */
+    double partial_tol;    /* 0 (default): V-cycle.  > 0: partial intermediate solve (Section 2
+                              variant): the intermediate system is solved to this relative
+                              residual (the paper: 0.2) by FGMRES(fgmres_m) preconditioned
+                              with the two-grid cycle; coarse solves then go to coarse_tol_rest
+                              within a right-hand side's first outer iteration (GMRES-DR
+                              first) and to coarse_tol_partial after it */
+    double coarse_tol_partial; /* coarse tolerance after the first outer iteration in the
+                                  partial mode: 1e-2 */
+    int partial_max_iters; /* FGMRES iteration limit of one partial intermediate solve (200) */
 } mg_params;
 
 /* solver of mg_solve (Section 2 compares both) */

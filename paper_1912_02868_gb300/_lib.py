@@ -30,7 +30,8 @@ class MGParams(ctypes.Structure):
         ("cgne_max_iters", ctypes.c_int), ("nullvec_max_iters", ctypes.c_int),
         ("nullvec_tol", ctypes.c_double), ("coarse_tol_first", ctypes.c_double),
         ("coarse_tol_rest", ctypes.c_double), ("precision", ctypes.c_int), ("seed", ctypes.c_ulonglong),
-        ("method", ctypes.c_int), ("parallel", ctypes.c_int),
+        ("method", ctypes.c_int), ("parallel", ctypes.c_int), ("partial_tol", ctypes.c_double),
+        ("coarse_tol_partial", ctypes.c_double), ("partial_max_iters", ctypes.c_int),
     ]
 
 

@@ -107,6 +107,13 @@ mg_status check_params(const mg_params& p) {
         return set_error("unknown method %d", p.method), MG_EINVAL;
     if (p.dr_m - p.dr_k > MSMAX)
         return set_error("dr_m - dr_k must be <= %d", MSMAX), MG_EINVAL;
+    if (!(p.partial_tol >= 0.0 && p.partial_tol < 1.0))
+        return set_error("partial_tol must be in [0, 1)"), MG_EINVAL;
+    if (p.partial_tol > 0.0 && (!(p.coarse_tol_partial > 0.0 && p.coarse_tol_partial < 1.0) || p.partial_max_iters < 1))
+        return set_error("partial mode: coarse_tol_partial must be in (0, 1), partial_max_iters positive"),
+               MG_EINVAL;
+    if (p.partial_tol > 0.0 && p.coarse_solver != MG_COARSE_DR_PROJ)
+        return set_error("the partial intermediate solve is built for the deflated coarse solve"), MG_EINVAL;
     return MG_OK;
 }
 
@@ -166,6 +173,17 @@ mg_status alloc_workspaces(Handle& H, cudaStream_t s, bool owner) {
     H.cpart_ctas = sm_count();
     MG_TRY(halloc_t(H, &H.cpart, (size_t)2 * H.cpart_ctas * PSTR));
     MG_TRY(halloc_t(H, &H.cstats, 1));
+    if (p.partial_tol > 0.0) {
+        const long n1 = H.L64[1].n;
+        MG_TRY(halloc_t(H, &H.p64.V, (size_t)(p.fgmres_m + 1) * n1));
+        MG_TRY(halloc_t(H, &H.p64.Z, (size_t)p.fgmres_m * n1));
+        MG_TRY(halloc_t(H, &H.p64.r, (size_t)n1));
+        MG_TRY(halloc_t(H, &H.p64.ks, 1));
+        MG_TRY(halloc_t(H, &H.p32.V, (size_t)(p.fgmres_m + 1) * n1));
+        MG_TRY(halloc_t(H, &H.p32.Z, (size_t)p.fgmres_m * n1));
+        MG_TRY(halloc_t(H, &H.p32.r, (size_t)n1));
+        MG_TRY(halloc_t(H, &H.p32.ks, 1));
+    }
     if (p.method == MG_METHOD_FINE_DEFLATION) {
         MG_TRY(halloc_t(H, &H.fdV, (size_t)(p.dr_m + 1) * n0));
         MG_TRY(halloc_t(H, &H.fdV2, (size_t)(p.dr_m + 1) * n0));
@@ -466,6 +484,9 @@ mg_status mg_default_params(mg_params* p) {
     p->seed = 12345ULL;
     p->method = MG_METHOD_MG;
     p->parallel = 1;
+    p->partial_tol = 0.0;
+    p->coarse_tol_partial = 1e-2;
+    p->partial_max_iters = 200;
     return MG_OK;
 }
 

@@ -70,6 +70,15 @@ struct CoarseWS {
     KState* ks = nullptr;
 };
 
+// Intermediate-grid FGMRES of the partial solve (mg_params.partial_tol > 0), one precision.
+template <typename T>
+struct PartialWS {
+    C2<T>* V = nullptr;   // (fgmres_m + 1) x n1
+    C2<T>* Z = nullptr;   // fgmres_m x n1
+    C2<T>* r = nullptr;
+    KState* ks = nullptr;
+};
+
 struct Scalars {  // device scalars of the host-driven loops
     double nb2;       // ||b||^2 of the current solve
     double r2;        // ||r||^2
@@ -131,6 +140,10 @@ struct Handle {
     KState* fdks = nullptr;
     KState* fdpls = nullptr;
     int fine_k = 0;
+    // partial intermediate solve
+    PartialWS<double> p64;
+    PartialWS<float> p32;
+    int cur_outer = 0;        // outer FGMRES step being preconditioned (picks the coarse tolerance)
     int defl_k = 0;           // 0: no deflation space yet
     Stats st;
     ApplyTimer timers[3];
@@ -142,11 +155,14 @@ struct Handle {
 
     template <typename T> Level<T>* levels();
     template <typename T> CoarseWS<T>& coarse();
+    template <typename T> PartialWS<T>& partial();
 };
 template <> inline Level<double>* Handle::levels<double>() { return L64; }
 template <> inline Level<float>* Handle::levels<float>() { return L32; }
 template <> inline CoarseWS<double>& Handle::coarse<double>() { return c64; }
 template <> inline CoarseWS<float>& Handle::coarse<float>() { return c32; }
+template <> inline PartialWS<double>& Handle::partial<double>() { return p64; }
+template <> inline PartialWS<float>& Handle::partial<float>() { return p32; }
 
 // allocation owned by the handle
 mg_status halloc(Handle& H, void** p, size_t bytes);

@@ -217,12 +217,21 @@ mg_status dr_solve_on(Handle& H, Level<double>& L, double2* V0, double2* V20, do
     }
 }
 
-// The first coarsest-grid solve: GMRES-DR to coarse_tol_first, which also
-// builds the coarse deflation space of the handle.
+// Coarse tolerances (Section 2).  V-cycle: GMRES-DR to coarse_tol_first, every
+// projected solve to coarse_tol_rest.  Partial intermediate solve: coarse solves
+// inside a right-hand side's first outer iteration go to coarse_tol_rest
+// (GMRES-DR first), every later one to coarse_tol_partial.
+double coarse_tol_dr(const Handle& H) { return H.p.partial_tol > 0.0 ? H.p.coarse_tol_rest : H.p.coarse_tol_first; }
+double coarse_tol_proj(const Handle& H) {
+    return (H.p.partial_tol > 0.0 && H.cur_outer > 0) ? H.p.coarse_tol_partial : H.p.coarse_tol_rest;
+}
+
+// The first coarsest-grid solve: GMRES-DR, which also builds the coarse
+// deflation space of the handle.
 mg_status dr_solve(Handle& H, const double2* f, double2* x, cudaStream_t s) {
     long long iters = 0;
     MG_TRY(dr_solve_on(H, H.L64[2], H.c64.V, H.c64.V2, H.c64.W, H.c64.ks, H.pls, H.defl_k, f, x,
-                       H.p.coarse_tol_first, iters, s));
+                       coarse_tol_dr(H), iters, s));
     H.st.coarse_iters += iters;
     H.st.mvps[2] += iters;
     H.st.dr_solves += 1;
@@ -290,7 +299,7 @@ mg_status proj_solve(Handle& H, const C2<T>* f, C2<T>* x, cudaStream_t s) {
     a.pls = H.pls;
     a.k = H.defl_k;
     a.ms = std::max(H.p.dr_m - H.defl_k, 1);
-    a.tol = H.p.coarse_tol_rest;
+    a.tol = coarse_tol_proj(H);
     a.max_cycles = H.p.proj_max_cycles;
     a.part = H.cpart;
     a.part_ctas = H.cpart_ctas;
@@ -340,7 +349,12 @@ mg_status coarse_solve(Handle& H, const C2<T>* f, C2<T>* x, cudaStream_t s) {
 }
 
 template <typename T>
-mg_status vcycle(Handle& H, int l, const C2<T>* f, C2<T>* x, cudaStream_t s) {
+mg_status vcycle(Handle& H, int l, const C2<T>* f, C2<T>* x, cudaStream_t s);
+
+// One cycle on grid l (l = 0, 1): x = S(f); x += P (grid l+1 with P^+ r);
+// r = f - A x; x += S(r).
+template <typename T>
+mg_status cycle(Handle& H, int l, const C2<T>* f, C2<T>* x, cudaStream_t s) {
     Level<T>* Ls = H.levels<T>();
     Level<T>& L = Ls[l];
     Level<T>& C = Ls[l + 1];
@@ -353,6 +367,58 @@ mg_status vcycle(Handle& H, int l, const C2<T>* f, C2<T>* x, cudaStream_t s) {
     H.st.mvps[l] += 1;
     smoother<T>(H, l, L, L.r, x, true, nullptr, s);
     return MG_OK;
+}
+
+// Partial intermediate solve (Section 2 variant): FGMRES(fgmres_m) on grid 1
+// from x = 0, preconditioned by the two-grid cycle there, until the true
+// residual satisfies ||f - A x|| <= partial_tol ||f|| (a cycle ends early on
+// the least-squares estimate), or partial_max_iters steps.
+template <typename T>
+mg_status partial_solve(Handle& H, const C2<T>* f, C2<T>* x, cudaStream_t s) {
+    Level<T>& L = H.levels<T>()[1];
+    PartialWS<T>& P = H.partial<T>();
+    const long n = L.n;
+    const int m = H.p.fgmres_m;
+    KState* ks = P.ks;
+    double* nf2 = MG_DEVF(H.sc, double, tmp) + 6;  // ||f||^2
+    double* r2 = MG_DEVF(H.sc, double, tmp) + 7;   // ||r||^2
+    launch_norm2<T>(nf2, f, n, H.red, Gate{}, s);
+    MG_CUDA_TRY(cudaMemsetAsync(x, 0, n * sizeof(C2<T>), s));
+    MG_CUDA_TRY(cudaMemcpyAsync(P.r, f, n * sizeof(C2<T>), cudaMemcpyDeviceToDevice, s));
+    const double tol = H.p.partial_tol;
+    int it = 0;
+    while (true) {
+        launch_norm2<T>(r2, P.r, n, H.red, Gate{}, s);
+        ks_start(ks, r2, tol, nf2, s);
+        launch_scale<T>(P.V, P.r, MG_DEVF(ks, double, scale), n, Gate{MG_DEVF(ks, int, scale_gate), 0}, s);
+        for (int jh = 0; jh < m && it < H.p.partial_max_iters; ++jh) {
+            const C2<T>* v = P.V + (long)jh * n;
+            C2<T>* z = P.Z + (long)jh * n;
+            MG_TRY(cycle<T>(H, 1, v, z, s));
+            arnoldi_step<T>(H, [&](C2<T>* w, Gate g) { L.apply(w, z, nullptr, false, g, s); }, P.V, n, ks, jh, s);
+            H.st.mvps[1] += 1;
+            ++it;
+            KHost kh;
+            MG_TRY(read_ks(H, ks, kh, s));
+            if (kh.step_gate != jh + 1) break;
+        }
+        ks_finish(ks, s);
+        launch_axpy_multi<T>(x, P.Z, n, 0, MG_DEVF(ks, int, j), MG_DEVF(ks, double2, d), 1.0, false, n, nullptr,
+                             H.red, Gate{}, s);
+        L.apply(P.r, x, f, false, Gate{}, s);  // true residual f - A x
+        H.st.mvps[1] += 1;
+        launch_norm2<T>(r2, P.r, n, H.red, Gate{}, s);
+        Scalars hs{};
+        MG_TRY(read_scalars(H, hs, s));
+        if (hs.tmp[7] <= tol * tol * hs.tmp[6] || it >= H.p.partial_max_iters) break;
+    }
+    return MG_OK;
+}
+
+template <typename T>
+mg_status vcycle(Handle& H, int l, const C2<T>* f, C2<T>* x, cudaStream_t s) {
+    if (l == 1 && H.p.partial_tol > 0.0) return partial_solve<T>(H, f, x, s);
+    return cycle<T>(H, l, f, x, s);
 }
 
 }  // namespace
@@ -386,6 +452,7 @@ mg_status fgmres_solve(Handle& H, const double2* b, double2* x, double tol, cuda
         for (int jh = 0; jh < m && outer < H.p.max_outer; ++jh) {
             double2* v = H.fV + (long)jh * n;
             double2* z = H.fZ + (long)jh * n;
+            H.cur_outer = outer;
             if (mixed) {
                 launch_convert<double, float>(H.v32, v, n, Gate{}, s);
                 MG_TRY(vcycle<float>(H, 0, H.v32, H.z32, s));
