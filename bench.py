@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-arms", action="store_true", help="skip the CGNE and fine GMRES-DR comparison arms")
     ap.add_argument("--no-serving", action="store_true", help="skip the served-stream sample")
     ap.add_argument("--no-partial", action="store_true", help="skip the partial-intermediate-solve variant")
+    ap.add_argument("--no-batching", action="store_true", help="skip the 64-right-hand-side batching sample")
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-rate", type=float, default=0.8,
                     help="Poisson arrival rate, requests/s (0.8: about 0.9x the measured saturated rate of this mix)")
@@ -485,6 +486,33 @@ def run_native(args):
         for h in hsp:
             h.close()
 
+    # ---------- batching: 64 right-hand sides of one configuration (configs[2] shape) ----------
+    batching = None
+    if not args.no_batching:
+        batching = {"rhs": 64, "config": 0, "precision": "mixed"}
+        B64 = torch.stack([torch.from_numpy(synth.rhs(L, 0, 50000 + i)[0]) for i in range(64)]).to(dev)
+        for mode, over in (("contexts", dict(parallel=7)), ("pairs", dict(parallel=7, pair_rhs=1))):
+            h = mg.mg_setup(torch.from_numpy(Us[0]).to(dev), L, L, m0s[0],
+                            params=mg.default_params(precision=mg.MG_MIXED, **over),
+                            starts0=torch.from_numpy(synth.nullvec_starts(L, 0, 0, 12, n0)).to(dev),
+                            starts1=torch.from_numpy(synth.nullvec_starts(L, 0, 1, 12, (L // 4) ** 2 * 24)).to(dev))
+            X64 = torch.zeros_like(B64)
+            mg.mg_solve(h, B64[0], X64[0], 1, TOL)  # builds the deflation space
+            mg.mg_solve(h, B64[1:15], X64[1:15], 14, TOL)  # contexts created, warm
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, it64, rr64, _ = mg.mg_solve(h, B64, X64, 64, TOL)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            assert max(rr64) <= TOL
+            ms_b = max_over_ranks(e0.elapsed_time(e1))
+            batching[mode] = {"solves_per_s": 64 / (ms_b / 1e3), "ms": ms_b, "outer_iters_mean": float(np.mean(it64))}
+            h.close()
+        batching["what"] = ("64 right-hand sides of one 256^2 configuration in one mg_solve: 7 concurrent solve "
+                            "contexts, one right-hand side each, against 7 workers with two right-hand sides each "
+                            "in lockstep, their coarsest solves sharing one cluster kernel")
+
     # ---------------- comparison arms of the 256^2 study (Section 2) ----------------
     arms = None
     if not args.no_arms:
@@ -538,6 +566,7 @@ def run_native(args):
         "outer_iters_mean": float(np.mean(iters)), "setup_s": setup_s,
         "fp64": fp64,
         "partial_solve": partial,
+        "batching_64rhs": batching,
         "arms_256": arms,
         "serving": serving,
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": nconf * n0 * 16,

@@ -88,6 +88,12 @@ typedef struct {
     double coarse_tol_partial; /* coarse tolerance after the first outer iteration in the
                                   partial mode: 1e-2 */
     int partial_max_iters; /* FGMRES iteration limit of one partial intermediate solve (200) */
+    int pair_rhs;          /* 1: with parallel > 1, each concurrent worker solves two right-hand
+                              sides in lockstep on two contexts, and their coarsest solves run as
+                              one cluster kernel that streams the coarse operator once for both
+                              (mixed precision, V-cycle, deflated coarse solve, device buffers;
+                              the results equal those of separate solves).  0 (default): one
+                              right-hand side per worker */
 } mg_params;
 
 /* solver of mg_solve (Section 2 compares both) */

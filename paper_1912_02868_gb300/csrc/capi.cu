@@ -66,6 +66,8 @@ void free_handle(Handle& H) {
     H.contexts.clear();
     if (H.own_stream) cudaStreamDestroy(H.own_stream);
     H.own_stream = nullptr;
+    if (H.work_stream) cudaStreamDestroy(H.work_stream);
+    H.work_stream = nullptr;
     for (auto& t : H.timers) {
         for (cudaEvent_t e : t.ev) cudaEventDestroy(e);
         t.ev.clear();
@@ -194,6 +196,55 @@ mg_status alloc_workspaces(Handle& H, cudaStream_t s, bool owner) {
         }
     }
     return MG_OK;
+}
+
+// Right-hand sides in lockstep pairs on two contexts A, B (pair_rhs): pairs
+// p = p0, p0 + step, ... < npairs of the list first, first + 1, ... < nrhs, on
+// stream s (device buffers).  Counters accumulate in A.st and B.st.  (Both
+// right-hand sides of a pair run on one stream: splitting their V-cycles over
+// two streams joined at the paired coarse kernel measured slower.)
+mg_status solve_rhs_pairs(Handle& A, Handle& Bh, const double2* B, double2* X, int first, int nrhs, int p0, int step,
+                          double tol, cudaStream_t s, int* iters, double* relres) {
+    const long n0 = A.L64[0].n;
+    MG_CUDA_TRY(cudaMemsetAsync(A.cstats, 0, sizeof(CoopStats), s));
+    MG_CUDA_TRY(cudaMemsetAsync(Bh.cstats, 0, sizeof(CoopStats), s));
+    mg_status result = MG_OK;
+    const int npairs = (nrhs - first + 1) / 2;
+    for (int p = p0; p < npairs; p += step) {
+        const int i0 = first + 2 * p, i1 = i0 + 1;
+        if (i1 >= nrhs) {  // an odd last one alone
+            int it = 0;
+            double rr = 0.0;
+            bool conv = false;
+            MG_TRY(fgmres_solve(A, B + (long)i0 * n0, X + (long)i0 * n0, tol, s, &it, &rr, &conv));
+            if (iters) iters[i0] = it;
+            if (relres) relres[i0] = rr;
+            if (!conv) result = MG_ENOTCONV;
+            continue;
+        }
+        Handle* HH[2] = {&A, &Bh};
+        const double2* const bb[2] = {B + (long)i0 * n0, B + (long)i1 * n0};
+        double2* const xx[2] = {X + (long)i0 * n0, X + (long)i1 * n0};
+        int it[2] = {0, 0};
+        double rr[2] = {0.0, 0.0};
+        bool conv[2] = {false, false};
+        MG_TRY(fgmres_solve_pair(HH, bb, xx, tol, s, it, rr, conv));
+        for (int q = 0; q < 2; ++q) {
+            const int i = q ? i1 : i0;
+            if (iters) iters[i] = it[q];
+            if (relres) relres[i] = rr[q];
+            if (!conv[q]) result = MG_ENOTCONV;
+        }
+    }
+    for (Handle* Hp : {&A, &Bh}) {
+        CoopStats cs{};
+        MG_CUDA_TRY(cudaMemcpyAsync(Hp->pinned, Hp->cstats, sizeof(CoopStats), cudaMemcpyDeviceToHost, s));
+        MG_CUDA_TRY(cudaStreamSynchronize(s));
+        std::memcpy(&cs, Hp->pinned, sizeof cs);
+        Hp->st.coarse_iters += cs.iters;
+        Hp->st.mvps[2] += cs.iters;
+    }
+    return result;
 }
 
 // Solve right-hand sides i = i0, i0 + step, ... < i1 on handle (or context) H and
@@ -487,6 +538,7 @@ mg_status mg_default_params(mg_params* p) {
     p->partial_tol = 0.0;
     p->coarse_tol_partial = 1e-2;
     p->partial_max_iters = 200;
+    p->pair_rhs = 0;
     return MG_OK;
 }
 
@@ -564,7 +616,12 @@ mg_status mg_solve(mg_handle h, const void* b, void* x, int nrhs, double tol, vo
             par = std::min(par, nrhs - 1);
         }
         if (first < nrhs) {
-            while ((int)H.contexts.size() < par - 1) {
+            // pair_rhs: every worker drives two contexts in lockstep
+            const bool pairs = H.p.pair_rhs && H.p.precision == MG_MIXED && H.p.method == MG_METHOD_MG &&
+                               H.p.coarse_solver == MG_COARSE_DR_PROJ && H.p.partial_tol == 0.0 && bdev && xdev;
+            if (pairs) par = std::max(1, std::min(par, (nrhs - first + 1) / 2));
+            const int nctx = pairs ? 2 * par - 1 : par - 1;
+            while ((int)H.contexts.size() < nctx) {
                 mg_handle_s* c = nullptr;
                 MG_TRY(make_context(H, &c));
                 H.contexts.push_back(c);
@@ -573,11 +630,16 @@ mg_status mg_solve(mg_handle h, const void* b, void* x, int nrhs, double tol, vo
                 c->h.defl_k = H.defl_k;
                 c->h.fine_k = H.fine_k;
             }
-            // inputs written on the caller's stream must be visible to the context streams
+            // this handle's share runs on a non-blocking stream of its own, like the
+            // contexts' (not on the caller's stream, which may be the legacy default
+            // stream); inputs written on the caller's stream must be visible to all
+            if (!H.work_stream) MG_CUDA_TRY(cudaStreamCreateWithFlags(&H.work_stream, cudaStreamNonBlocking));
+            const cudaStream_t ws = H.work_stream;
             cudaEvent_t ev;
             MG_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
             MG_CUDA_TRY(cudaEventRecord(ev, s));
-            for (int w = 0; w < par - 1; ++w) MG_CUDA_TRY(cudaStreamWaitEvent(H.contexts[w]->h.own_stream, ev, 0));
+            MG_CUDA_TRY(cudaStreamWaitEvent(ws, ev, 0));
+            for (int w = 0; w < nctx; ++w) MG_CUDA_TRY(cudaStreamWaitEvent(H.contexts[w]->h.own_stream, ev, 0));
             std::vector<mg_status> st_w(par, MG_OK);
             std::vector<std::string> err_w(par);
             std::vector<std::thread> th;
@@ -586,19 +648,41 @@ mg_status mg_solve(mg_handle h, const void* b, void* x, int nrhs, double tol, vo
             for (int w = 1; w < par; ++w) {
                 th.emplace_back([&, w]() {
                     cudaSetDevice(dev);
-                    Handle& C = H.contexts[w - 1]->h;
-                    C.st = Stats{};
-                    st_w[w] = solve_rhs(C, B, X, bdev, xdev, first + w, nrhs, par, tol, C.own_stream, iters, relres);
+                    if (pairs) {
+                        Handle& C = H.contexts[2 * w - 1]->h;
+                        Handle& D = H.contexts[2 * w]->h;
+                        C.st = Stats{};
+                        D.st = Stats{};
+                        st_w[w] = solve_rhs_pairs(C, D, B, X, first, nrhs, w, par, tol, C.own_stream, iters, relres);
+                    } else {
+                        Handle& C = H.contexts[w - 1]->h;
+                        C.st = Stats{};
+                        st_w[w] =
+                            solve_rhs(C, B, X, bdev, xdev, first + w, nrhs, par, tol, C.own_stream, iters, relres);
+                    }
                     if (st_w[w] != MG_OK && st_w[w] != MG_ENOTCONV) err_w[w] = mg_last_error();
                 });
             }
             const Stats keep = H.st;  // the first right-hand side, if it ran alone
             H.st = Stats{};
-            st_w[0] = solve_rhs(H, B, X, bdev, xdev, first, nrhs, par, tol, s, iters, relres);
+            if (pairs) {
+                Handle& D = H.contexts[0]->h;
+                D.st = Stats{};
+                st_w[0] = solve_rhs_pairs(H, D, B, X, first, nrhs, 0, par, tol, ws, iters, relres);
+            } else {
+                st_w[0] = solve_rhs(H, B, X, bdev, xdev, first, nrhs, par, tol, ws, iters, relres);
+            }
             for (auto& t : th) t.join();
+            // later work on the caller's stream follows every worker's
+            cudaEventRecord(ev, ws);
+            cudaStreamWaitEvent(s, ev, 0);
+            for (int w = 0; w < nctx; ++w) {
+                cudaEventRecord(ev, H.contexts[w]->h.own_stream);
+                cudaStreamWaitEvent(s, ev, 0);
+            }
             cudaEventDestroy(ev);
             Stats sum = keep;
-            for (int w = 0; w < par; ++w) {
+            for (int w = 0; w <= nctx; ++w) {
                 const Stats& sw = (w == 0) ? H.st : H.contexts[w - 1]->h.st;
                 for (int l = 0; l < 3; ++l) sum.mvps[l] += sw.mvps[l];
                 sum.outer += sw.outer;

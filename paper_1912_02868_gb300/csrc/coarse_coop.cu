@@ -211,6 +211,32 @@ __device__ __forceinline__ C2<T> accum_rows(C2<T> acc, const C2<T>* X, long ldx,
     return acc;
 }
 
+// accum_rows for two right-hand sides at once (their loads interleaved; per
+// right-hand side the order of accum_rows)
+template <typename T, bool SUB>
+__device__ __forceinline__ void accum_rows2(C2<T>& acc0, C2<T>& acc1, const C2<T>* X0, const C2<T>* X1, long ldx,
+                                            int e, const C2<T>* coef0, const C2<T>* coef1, int cnt) {
+    int i = 0;
+    for (; i + 8 <= cnt; i += 8) {
+        C2<T> v[8], w[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            v[u] = X0[(long)(i + u) * ldx + e];
+            w[u] = X1[(long)(i + u) * ldx + e];
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            acc0 = SUB ? csub(acc0, cmul(v[u], coef0[i + u])) : cfma(v[u], coef0[i + u], acc0);
+            acc1 = SUB ? csub(acc1, cmul(w[u], coef1[i + u])) : cfma(w[u], coef1[i + u], acc1);
+        }
+    }
+    for (; i < cnt; ++i) {
+        const C2<T> v = X0[(long)i * ldx + e], w = X1[(long)i * ldx + e];
+        acc0 = SUB ? csub(acc0, cmul(v, coef0[i])) : cfma(v, coef0[i], acc0);
+        acc1 = SUB ? csub(acc1, cmul(w, coef1[i])) : cfma(w, coef1[i], acc1);
+    }
+}
+
 // Sum the pushed partials of all CTAs of the cluster in rank order (every CTA
 // gets the same result): red[i] = sum_r inbox[r][i], i < n.  Called after the
 // cluster barrier that follows the pushes.
@@ -571,6 +597,429 @@ __global__ void __maxnreg__(128) k_coarse_proj(CoopArgs<T> a) {
     cluster.sync();  // no CTA leaves while others may still read its shared memory
 }
 
+// ---------------------------------------------------------------------------
+// Two right-hand sides of one coarsest operator in lockstep (FP32, push mode).
+// Both solves run the same GMRES-Proj algorithm as k_coarse_proj, step for
+// step and with the same arithmetic per right-hand side (so each result equals
+// the single kernel's); they share the operator stream of the apply (each
+// block entry is loaded once and used for both vectors) and the cluster
+// barriers.  A solve that has stopped its cycle, or converged, idles through
+// the other's steps.
+
+template <typename T>
+struct PairSmem {
+    C2<T> inbox[2][2][MAX_CLUSTER][PSTR];  // [phase][rhs]: partial sums pushed by every CTA
+    C2<T> red[2][PSTR];
+    C2<T> h1[2][MSMAX + 1];
+    C2<T> xs[2][MAX_SPC][5][NDOF];
+    int pusht[MAX_SPC][5];
+    Small<T> st[2];
+    T scal[2][8];
+    int ctl[2][8];
+};
+
+// push_gram for the two right-hand sides at once: warp task i forms product i
+// (basis vector i, or the norm when i == nd) of both right-hand sides, their
+// loads and shuffles interleaved; act[b] == 0 skips rhs b.  Per right-hand side
+// the summation order is push_gram's.
+template <typename T>
+__device__ void push_gram2(const C2<T>* const X[2], long ldx, int nd, const C2<T>* const y[2], int nrows, bool norm,
+                           C2<T>* const inbox[2], const int act[2], int nr, int me, int nw) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int per = nd + (norm ? 1 : 0);
+    const bool on0 = act[0] != 0, on1 = act[1] != 0;
+    if (!on0 && !on1) return;
+    // an idle right-hand side reads the active one's vectors (never stored)
+    const int b0 = on0 ? 0 : 1, b1 = on1 ? 1 : 0;
+    const C2<T>* y0 = y[b0];
+    const C2<T>* y1 = y[b1];
+    for (int i = warp; i < per; i += nw) {
+        C2<T> p4[4], q4[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) p4[u] = q4[u] = mk<T>(0, 0);
+        const C2<T>* x0 = (i < nd) ? X[b0] + (long)i * ldx : y0;
+        const C2<T>* x1 = (i < nd) ? X[b1] + (long)i * ldx : y1;
+        int e = lane;
+        for (; e + 96 < nrows; e += 128) {
+            C2<T> xa[4], ya[4], xb[4], yb[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                xa[u] = x0[e + 32 * u];
+                ya[u] = y0[e + 32 * u];
+                xb[u] = x1[e + 32 * u];
+                yb[u] = y1[e + 32 * u];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                p4[u] = cfmac(xa[u], ya[u], p4[u]);
+                q4[u] = cfmac(xb[u], yb[u], q4[u]);
+            }
+        }
+        for (; e < nrows; e += 32) {
+            p4[0] = cfmac(x0[e], y0[e], p4[0]);
+            q4[0] = cfmac(x1[e], y1[e], q4[0]);
+        }
+        C2<T> p = cadd(cadd(p4[0], p4[1]), cadd(p4[2], p4[3]));
+        C2<T> q = cadd(cadd(q4[0], q4[1]), cadd(q4[2], q4[3]));
+        if (i >= nd) p.y = q.y = 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            p.x += __shfl_xor_sync(0xffffffffu, p.x, o);
+            p.y += __shfl_xor_sync(0xffffffffu, p.y, o);
+            q.x += __shfl_xor_sync(0xffffffffu, q.x, o);
+            q.y += __shfl_xor_sync(0xffffffffu, q.y, o);
+        }
+        if (lane < nr) {
+            if (on0) st_rank<T>(inbox[0] + me * PSTR + i, lane, me, p);
+            if (on1) st_rank<T>(inbox[1] + me * PSTR + i, lane, me, q);
+        }
+    }
+}
+
+// reduce_inbox for the two right-hand sides (warp task i sums entry i of both,
+// same tree as the single kernel), then a block barrier
+template <typename T>
+__device__ void reduce_inbox2(C2<T>* const inbox[2], int nr, int n, C2<T>* const red[2], const int act[2], int nw) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool on0 = act[0] != 0, on1 = act[1] != 0;
+    if (on0 || on1)
+        for (int i = warp; i < n; i += nw) {
+            C2<T> p = mk<T>(0, 0), q = mk<T>(0, 0);
+            if (lane < nr) {
+                if (on0) p = inbox[0][lane * PSTR + i];
+                if (on1) q = inbox[1][lane * PSTR + i];
+            }
+#pragma unroll
+            for (int o = MAX_CLUSTER / 2; o > 0; o >>= 1) {
+                p.x += __shfl_xor_sync(0xffffffffu, p.x, o);
+                p.y += __shfl_xor_sync(0xffffffffu, p.y, o);
+                q.x += __shfl_xor_sync(0xffffffffu, q.x, o);
+                q.y += __shfl_xor_sync(0xffffffffu, q.y, o);
+            }
+            if (lane == 0) {
+                if (on0) red[0][i] = p;
+                if (on1) red[1][i] = q;
+            }
+        }
+    __syncthreads();
+}
+
+template <typename T>
+__device__ __forceinline__ void push_row2(PairSmem<T>& S, int me, int b, int e, C2<T> v) {
+    const int ls = e / NDOF, kk = e - ls * NDOF;
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        const int code = S.pusht[ls][q];
+        st_rank<T>(&S.xs[b][(code >> 3) & 0x1fff][code & 7][kk], code >> 16, me, v);
+    }
+}
+
+template <typename T>
+__global__ void __maxnreg__(128) k_coarse_proj_pair(CoopArgs<T> a0, CoopArgs<T> a1) {
+    using Z = C2<T>;
+    cg::cluster_group cluster = cg::this_cluster();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PairSmem<T>& S = *reinterpret_cast<PairSmem<T>*>(smem_raw);
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    const int rank = (int)cluster.block_rank(), ncta = (int)cluster.num_blocks();
+    const long nsite = (long)a0.Nx * a0.Nt;
+    const long n = nsite * NDOF;
+    const long s0 = (long)rank * a0.spc;
+    const long s1 = min(nsite, s0 + a0.spc);
+    const int my_sites = (int)max(0L, s1 - s0);
+    const long r0 = s0 * NDOF;
+    const int nrows = my_sites * NDOF;
+    const int k = a0.k, ms = a0.ms;
+    const int LD = MSMAX + 1;
+    const int rows_cap = a0.spc * NDOF;
+    const long ldv = rows_cap;
+    Z* Vb[2];
+    Vb[0] = reinterpret_cast<Z*>(smem_raw + sizeof(PairSmem<T>));
+    Vb[1] = Vb[0] + (long)(ms + 1) * rows_cap;
+    const Z* Wl = a0.W + r0;
+    const long ldw = n;
+    Z* xl[2] = {a0.x + r0, a1.x + r0};
+    Z* rl[2] = {a0.r + r0, a1.r + r0};
+    const Z* fl[2] = {a0.f + r0, a1.f + r0};
+    const double tol_rel[2] = {a0.tol, a1.tol};
+    for (int e = tid; e < my_sites * 5; e += nt) {  // push table, as in k_coarse_proj
+        const int ls = e / 5, q = e - ls * 5;
+        const int from[5] = {0, 2, 1, 4, 3};
+        const long w = nbr_site(s0 + ls, from[q], a0.Nx, a0.Nt);
+        const int owner = (int)(w / a0.spc);
+        S.pusht[ls][q] = (owner << 16) | ((int)(w - (long)owner * a0.spc) << 3) | q;
+    }
+    // projection matrices M, N (shared deflation space), as in k_coarse_proj
+    Z* Mp = Vb[1] + (long)(ms + 1) * rows_cap;
+    Z* Np = Mp + k * (k + 1);
+    if (tid < 32) {
+        const KState* P = a0.pls;
+        for (int l = tid; l <= k; l += 32) {
+            Z g[KLD], dd[KMAX];
+            for (int i = 0; i <= k; ++i) g[i] = mk<T>(i == l ? T(1) : T(0), 0);
+            for (int t = 0; t < P->nrot; ++t)
+                rot_<T>((T)P->rc[t], from_d2<T>(P->rs[t]), g[P->ra[t]], g[P->rb[t]]);
+            for (int i = k - 1; i >= 0; --i) {
+                Z acc = g[i];
+                for (int m = i + 1; m < k; ++m) acc = csub(acc, cmul(from_d2<T>(P->R[i + KLD * m]), dd[m]));
+                dd[i] = cdiv_<T>(acc, from_d2<T>(P->R[i + KLD * i]));
+            }
+            for (int i = 0; i < k; ++i) Mp[i + k * l] = dd[i];
+            for (int i = 0; i <= k; ++i) {
+                Z acc = mk<T>(0, 0);
+                for (int m = 0; m < k; ++m) acc = cfma(from_d2<T>(P->H[i + KLD * m]), dd[m], acc);
+                Np[i + (k + 1) * l] = acc;
+            }
+        }
+    }
+    for (int e = tid; e < 2 * nrows; e += nt) {  // x = 0, r = f
+        const int b = e / nrows, rr = e - b * nrows;
+        xl[b][rr] = mk<T>(0, 0);
+        rl[b][rr] = fl[b][rr];
+    }
+    __syncthreads();
+    int act[2] = {1, 1}, conv[2] = {0, 0}, iters[2] = {0, 0};
+    const int all2[2] = {1, 1};
+    C2<T>* const in0[2] = {&S.inbox[0][0][0][0], &S.inbox[0][1][0][0]};
+    C2<T>* const in1[2] = {&S.inbox[1][0][0][0], &S.inbox[1][1][0][0]};
+    C2<T>* const redp[2] = {S.red[0], S.red[1]};
+    C2<T>* const h1p[2] = {S.h1[0], S.h1[1]};
+    const Z* const rlc[2] = {rl[0], rl[1]};
+    push_gram2<T>(rlc, 0, 0, rlc, nrows, true, in0, all2, ncta, rank, nw);
+    cluster.sync();
+    reduce_inbox2<T>(in0, ncta, 1, redp, all2, nw);
+    double tol_abs[2];
+    for (int b = 0; b < 2; ++b) tol_abs[b] = tol_rel[b] * sqrt(fmax((double)S.red[b][0].x, 0.0));
+    int cycles = 0;
+    while (act[0] || act[1]) {
+        // ---- projection onto the shared deflation space, per right-hand side ----
+        const Z* const Wb[2] = {Wl, Wl};
+        push_gram2<T>(Wb, ldw, k + 1, rlc, nrows, false, in1, act, ncta, rank, nw);
+        cluster.sync();
+        reduce_inbox2<T>(in1, ncta, k + 1, redp, act, nw);
+        for (int t = tid; t < 2 * (k + 1); t += nt) {
+            const int b = t / (k + 1), i = t - b * (k + 1);
+            if (!act[b]) continue;
+            Z pdv = mk<T>(0, 0), puv = mk<T>(0, 0);
+            for (int l = 0; l <= k; ++l) {
+                const Z gl = S.red[b][l];
+                if (i < k) pdv = cfma(Mp[i + k * l], gl, pdv);
+                puv = cfma(Np[i + (k + 1) * l], gl, puv);
+            }
+            if (i < k) S.st[b].pd[i] = pdv;
+            S.st[b].pu[i] = puv;
+        }
+        __syncthreads();
+        for (int e = tid; e < 2 * nrows; e += nt) {
+            const int b = e / nrows, rr = e - b * nrows;
+            if (!act[b]) continue;
+            xl[b][rr] = accum_rows<T, false>(xl[b][rr], Wl, ldw, rr, S.st[b].pd, k);
+            rl[b][rr] = accum_rows<T, true>(rl[b][rr], Wl, ldw, rr, S.st[b].pu, k + 1);
+        }
+        __syncthreads();
+        push_gram2<T>(rlc, 0, 0, rlc, nrows, true, in0, act, ncta, rank, nw);
+        cluster.sync();
+        reduce_inbox2<T>(in0, ncta, 1, redp, act, nw);
+        double beta[2] = {0.0, 0.0};
+        for (int b = 0; b < 2; ++b) {
+            if (!act[b]) continue;
+            beta[b] = sqrt(fmax((double)S.red[b][0].x, 0.0));
+            if (beta[b] <= tol_abs[b] || beta[b] == 0.0) {
+                conv[b] = 1;
+                act[b] = 0;
+            }
+        }
+        if (!act[0] && !act[1]) break;
+        // ---- one GMRES(ms) cycle from r for each active right-hand side ----
+        for (int e = tid; e < 2 * LD * MSMAX; e += nt) {
+            const int b = e / (LD * MSMAX), q = e - b * (LD * MSMAX);
+            S.st[b].H[q] = mk<T>(0, 0);
+            S.st[b].Rm[q] = mk<T>(0, 0);
+        }
+        if (tid == 0)
+            for (int b = 0; b < 2; ++b) {
+                if (!act[b]) continue;
+                for (int i = 0; i <= ms; ++i) {
+                    S.st[b].c[i] = mk<T>(i == 0 ? (T)beta[b] : T(0), 0);
+                    S.st[b].g[i] = S.st[b].c[i];
+                }
+                S.scal[b][0] = (T)(1.0 / beta[b]);
+            }
+        __syncthreads();
+        for (int e = tid; e < 2 * nrows; e += nt) {
+            const int b = e / nrows, rr = e - b * nrows;
+            if (!act[b]) continue;
+            const Z v = cscale(rl[b][rr], S.scal[b][0]);
+            Vb[b][rr] = v;
+            push_row2<T>(S, rank, b, rr, v);
+        }
+        cluster.sync();  // v_0 complete in every CTA
+        int cact[2] = {act[0], act[1]}, jj[2] = {ms, ms};
+        for (int j = 0; j < ms && (cact[0] || cact[1]); ++j) {
+            Z* wl[2] = {Vb[0] + (long)(j + 1) * ldv, Vb[1] + (long)(j + 1) * ldv};
+            // w_b = A v_b: each block entry loaded once for both vectors
+            for (int e = tid; e < nrows; e += nt) {
+                const int ls = e / NDOF, kk = e - ls * NDOF;
+                const Z* Ab = a0.A + (s0 + ls) * (5L * NDOF * NDOF) + kk;
+                Z acc0 = mk<T>(0, 0), acc1 = mk<T>(0, 0);
+#pragma unroll
+                for (int d = 0; d < 5; ++d) {
+#pragma unroll
+                    for (int l = 0; l < NDOF; ++l) {
+                        const Z av = __ldg(Ab + (d * NDOF + l) * NDOF);
+                        acc0 = cfma(av, S.xs[0][ls][d][l], acc0);
+                        acc1 = cfma(av, S.xs[1][ls][d][l], acc1);
+                    }
+                }
+                if (cact[0]) wl[0][e] = acc0;
+                if (cact[1]) wl[1][e] = acc1;
+            }
+            __syncthreads();
+            const Z* const Vc[2] = {Vb[0], Vb[1]};
+            const Z* const wc[2] = {wl[0], wl[1]};
+            push_gram2<T>(Vc, ldv, j + 1, wc, nrows, false, in1, cact, ncta, rank, nw);
+            cluster.sync();
+            reduce_inbox2<T>(in1, ncta, j + 1, h1p, cact, nw);
+            if (cact[0] && cact[1]) {
+                for (int rr = tid; rr < nrows; rr += nt) {
+                    Z w0 = wl[0][rr], w1 = wl[1][rr];
+                    accum_rows2<T, true>(w0, w1, Vb[0], Vb[1], ldv, rr, S.h1[0], S.h1[1], j + 1);
+                    wl[0][rr] = w0;
+                    wl[1][rr] = w1;
+                }
+            } else {
+                const int b = cact[0] ? 0 : 1;
+                for (int rr = tid; rr < nrows; rr += nt)
+                    wl[b][rr] = accum_rows<T, true>(wl[b][rr], Vb[b], ldv, rr, S.h1[b], j + 1);
+            }
+            __syncthreads();
+            push_gram2<T>(Vc, ldv, j + 1, wc, nrows, true, in0, cact, ncta, rank, nw);
+            cluster.sync();
+            reduce_inbox2<T>(in0, ncta, j + 2, redp, cact, nw);
+            T hn[2];
+            {  // warp butterfly per right-hand side, as in k_coarse_proj (both at once)
+                T h2[2] = {0, 0};
+                for (int i = lane; i <= j; i += 32)
+#pragma unroll
+                    for (int b = 0; b < 2; ++b) h2[b] += S.red[b][i].x * S.red[b][i].x + S.red[b][i].y * S.red[b][i].y;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                    for (int b = 0; b < 2; ++b) h2[b] += __shfl_xor_sync(0xffffffffu, h2[b], o);
+#pragma unroll
+                for (int b = 0; b < 2; ++b) hn[b] = sqrt(fmax((T)S.red[b][j + 1].x - h2[b], T(0)));
+            }
+            const T sc[2] = {hn[0] > T(0) ? T(1) / hn[0] : T(0), hn[1] > T(0) ? T(1) / hn[1] : T(0)};
+            if (cact[0] && cact[1]) {
+                for (int rr = tid; rr < nrows; rr += nt) {
+                    Z w0 = wl[0][rr], w1 = wl[1][rr];
+                    accum_rows2<T, true>(w0, w1, Vb[0], Vb[1], ldv, rr, S.red[0], S.red[1], j + 1);
+                    w0 = cscale(w0, sc[0]);
+                    w1 = cscale(w1, sc[1]);
+                    wl[0][rr] = w0;
+                    wl[1][rr] = w1;
+                    push_row2<T>(S, rank, 0, rr, w0);
+                    push_row2<T>(S, rank, 1, rr, w1);
+                }
+            } else {
+                const int b = cact[0] ? 0 : 1;
+                for (int rr = tid; rr < nrows; rr += nt) {
+                    const Z v = cscale(accum_rows<T, true>(wl[b][rr], Vb[b], ldv, rr, S.red[b], j + 1), sc[b]);
+                    wl[b][rr] = v;
+                    push_row2<T>(S, rank, b, rr, v);
+                }
+            }
+            __syncwarp();
+            cluster_arrive();
+            // warp b updates the least squares of right-hand side b
+            if (warp < 2 && cact[warp]) {
+                const int b = warp;
+                Small<T>& st = S.st[b];
+                for (int i = lane; i <= j; i += 32) st.H[i + LD * j] = cadd(S.h1[b][i], S.red[b][i]);
+                if (lane == 0) st.H[(j + 1) + LD * j] = mk<T>(hn[b], 0);
+                __syncwarp();
+                if (lane == 0) {
+                    const Z* __restrict__ Hc = st.H + LD * j;
+                    Z* __restrict__ Rc = st.Rm + LD * j;
+                    const T* __restrict__ rcs = st.rc;
+                    const Z* __restrict__ rss = st.rs;
+                    Z p = Hc[0];
+#pragma unroll 8
+                    for (int t = 0; t < j; ++t) {
+                        Z q = Hc[t + 1];
+                        rot_<T>(rcs[t], rss[t], p, q);
+                        Rc[t] = p;
+                        p = q;
+                    }
+                    T cc;
+                    Z ss, rr2;
+                    givens_real_<T>(p, hn[b], cc, ss, rr2);
+                    Rc[j] = rr2;
+                    st.rc[j] = cc;
+                    st.rs[j] = ss;
+                    rot_<T>(cc, ss, st.g[j], st.g[j + 1]);
+                    const Z gn = st.g[j + 1];
+                    S.ctl[b][0] = ((double)(gn.x * gn.x + gn.y * gn.y) <= tol_abs[b] * tol_abs[b]) ? 1 : 0;
+                    S.ctl[b][1] = (hn[b] == T(0)) ? 1 : 0;
+                }
+                __syncwarp();
+            }
+            cluster_wait();
+            __syncthreads();
+            for (int b = 0; b < 2; ++b) {
+                if (!cact[b]) continue;
+                ++iters[b];
+                conv[b] = S.ctl[b][0];
+                if (S.ctl[b][0] | S.ctl[b][1]) {
+                    cact[b] = 0;
+                    jj[b] = j + 1;
+                }
+            }
+        }
+        // ---- finish the cycle of each active right-hand side ----
+        if (lane == 0 && warp < 2 && act[warp]) {  // back substitution: warp b's lane 0
+            const int b = warp, jc = jj[b];
+            Small<T>& st = S.st[b];
+            for (int i = jc - 1; i >= 0; --i) {
+                Z acc = st.g[i];
+                for (int l = i + 1; l < jc; ++l) acc = csub(acc, cmul(st.Rm[i + LD * l], st.d[l]));
+                const Z piv = st.Rm[i + LD * i];
+                st.d[i] = (piv.x == T(0) && piv.y == T(0)) ? mk<T>(0, 0) : cdiv_<T>(acc, piv);
+            }
+        }
+        __syncthreads();
+        for (int t = tid; t < 2 * (MSMAX + 1); t += nt) {
+            const int b = t / (MSMAX + 1), i = t - b * (MSMAX + 1);
+            if (!act[b] || i > jj[b]) continue;
+            Z acc = S.st[b].c[i];
+            for (int l = 0; l < jj[b]; ++l) acc = csub(acc, cmul(S.st[b].H[i + LD * l], S.st[b].d[l]));
+            S.st[b].rho[i] = acc;
+        }
+        __syncthreads();
+        for (int e = tid; e < 2 * nrows; e += nt) {
+            const int b = e / nrows, rr = e - b * nrows;
+            if (!act[b]) continue;
+            xl[b][rr] = accum_rows<T, false>(xl[b][rr], Vb[b], ldv, rr, S.st[b].d, jj[b]);
+            rl[b][rr] = accum_rows<T, false>(mk<T>(0, 0), Vb[b], ldv, rr, S.st[b].rho, jj[b] + 1);
+        }
+        ++cycles;
+        __syncthreads();
+        for (int b = 0; b < 2; ++b)
+            if (act[b] && (conv[b] || cycles >= a0.max_cycles)) act[b] = 0;
+    }
+    if (rank == 0 && tid == 0) {
+        a0.out->iters += iters[0];
+        a0.out->cycles += cycles;
+        a0.out->solves += 1;
+        a0.out->unconverged += conv[0] ? 0 : 1;
+        a1.out->iters += iters[1];
+        a1.out->cycles += cycles;
+        a1.out->solves += 1;
+        a1.out->unconverged += conv[1] ? 0 : 1;
+    }
+    cluster.sync();  // no CTA leaves while others may still write its shared memory
+}
+
 struct Geometry {
     int cluster = 1, spc = 1, threads = 32, vs = 0, lsw = 0;
     size_t smem = 0;
@@ -667,5 +1116,69 @@ mg_status launch_coarse_proj(const CoopArgs<T>& args_in, cudaStream_t s) {
 
 template mg_status launch_coarse_proj<double>(const CoopArgs<double>&, cudaStream_t);
 template mg_status launch_coarse_proj<float>(const CoopArgs<float>&, cudaStream_t);
+
+mg_status launch_coarse_proj_pair(const CoopArgs<float>& a0in, const CoopArgs<float>& a1in, cudaStream_t s,
+                                  bool* launched) {
+    *launched = false;
+    CoopArgs<float> a0 = a0in, a1 = a1in;
+    if (a0.A != a1.A || a0.W != a1.W || a0.pls != a1.pls || a0.k != a1.k || a0.ms != a1.ms || a0.Nx != a1.Nx ||
+        a0.Nt != a1.Nt || a0.max_cycles != a1.max_cycles) {
+        set_error("coarse pair solve: the two solves must share the operator and the deflation space");
+        return MG_EINVAL;
+    }
+    if (a0.ms < 1 || a0.ms > MSMAX || a0.k < 1 || a0.k + 1 > PSTR || a0.ms + 2 > PSTR) {
+        set_error("coarse pair solve: unsupported (m - k, k) = (%d, %d)", a0.ms, a0.k);
+        return MG_EINVAL;
+    }
+    static bool configured[16] = {};
+    int dev = 0;
+    MG_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 16) dev = 0;
+    if (!configured[dev]) {
+        MG_CUDA_TRY(cudaFuncSetAttribute(k_coarse_proj_pair<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)SMEM_LIMIT));
+        MG_CUDA_TRY(
+            cudaFuncSetAttribute(k_coarse_proj_pair<float>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        configured[dev] = true;
+    }
+    // push mode only: both basis slices in shared memory, one staging chunk;
+    // otherwise the caller runs the two solves one after the other
+    const long nsite = (long)a0.Nx * a0.Nt;
+    for (int cl = 16; cl >= 1; cl >>= 1) {
+        const long spc = (nsite + cl - 1) / cl;
+        if (spc > MAX_SPC) return MG_OK;
+        const int ctas = (int)((nsite + spc - 1) / spc);
+        const int rows = (int)spc * NDOF;
+        const int threads = std::min(std::max(((rows + 31) / 32) * 32, 64), MAX_THREADS);
+        const size_t smem = sizeof(PairSmem<float>) + 2 * slice_bytes<float>(a0.ms, rows) + proj_bytes<float>(a0.k);
+        if (smem > SMEM_LIMIT) return MG_OK;
+        cudaLaunchConfig_t cfg{};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = ctas;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(ctas);
+        cfg.blockDim = dim3(threads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, k_coarse_proj_pair<float>, &cfg) != cudaSuccess) {
+            (void)cudaGetLastError();
+            continue;
+        }
+        if (nclusters < 1) continue;
+        a0.spc = a1.spc = (int)spc;
+        a0.vs = a1.vs = 1;
+        a0.lsw = a1.lsw = 0;
+        MG_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_coarse_proj_pair<float>, a0, a1));
+        count_launch();
+        *launched = true;
+        return MG_OK;
+    }
+    return MG_OK;
+}
 
 }  // namespace mg

@@ -150,6 +150,7 @@ struct Handle {
     // concurrent solve contexts sharing this hierarchy (mg_solve with nrhs > 1)
     bool is_context = false;             // a context: shares hierarchy and deflation, owns workspaces
     cudaStream_t own_stream = nullptr;   // a context's stream
+    cudaStream_t work_stream = nullptr;  // this handle's stream for its share of a parallel solve
     std::vector<mg_handle_s*> contexts;
     size_t bytes = 0;                    // device bytes this handle allocated
 
@@ -173,6 +174,10 @@ template <typename P> mg_status halloc_t(Handle& H, P** p, size_t count) {
 // solve entry points (solver.cu)
 mg_status fgmres_solve(Handle& H, const double2* b, double2* x, double tol, cudaStream_t s, int* iters,
                        double* relres, bool* converged);
+// Two right-hand sides on two contexts of one hierarchy, in lockstep with paired
+// coarsest solves (mixed precision, deflation space built); solver.cu.
+mg_status fgmres_solve_pair(Handle* HH[2], const double2* const b[2], double2* const x[2], double tol,
+                            cudaStream_t s, int it_out[2], double rr_out[2], bool conv_out[2]);
 mg_status build_hierarchy(Handle& H, const double2* gauge_dev, const double2* starts0, const double2* starts1,
                           const double2* nullvecs0, const double2* nullvecs1, cudaStream_t s);
 mg_status fine_deflated_solve(Handle& H, const double2* b, double2* x, double tol, cudaStream_t s, int* iters,

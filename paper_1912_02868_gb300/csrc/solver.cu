@@ -284,7 +284,7 @@ mg_status proj_solve_host(Handle& H, Level<double>& L, double2* V, const double2
 // solve is one cooperative kernel (coarse_coop.cu); its iteration counts are
 // accumulated on the device and read once per mg_solve.
 template <typename T>
-mg_status proj_solve(Handle& H, const C2<T>* f, C2<T>* x, cudaStream_t s) {
+CoopArgs<T> proj_args(Handle& H, const C2<T>* f, C2<T>* x) {
     Level<T>& L = H.levels<T>()[2];
     CoarseWS<T>& W = H.coarse<T>();
     CoopArgs<T> a{};
@@ -304,6 +304,13 @@ mg_status proj_solve(Handle& H, const C2<T>* f, C2<T>* x, cudaStream_t s) {
     a.part = H.cpart;
     a.part_ctas = H.cpart_ctas;
     a.out = H.cstats;
+    return a;
+}
+
+template <typename T>
+mg_status proj_solve(Handle& H, const C2<T>* f, C2<T>* x, cudaStream_t s) {
+    Level<T>& L = H.levels<T>()[2];
+    const CoopArgs<T> a = proj_args<T>(H, f, x);
     // grid-2 timing covers the whole projected solve (one kernel)
     ApplyTimer* t = L.timer;
     cudaEvent_t e1 = nullptr;
@@ -421,6 +428,32 @@ mg_status vcycle(Handle& H, int l, const C2<T>* f, C2<T>* x, cudaStream_t s) {
     return cycle<T>(H, l, f, x, s);
 }
 
+// The V-cycle of grid 0 split at the coarsest solve, for the lockstep pair:
+// everything before it (smoothing on grids 0 and 1, both restrictions, leaving
+// the coarse right-hand side in grid 2's f) and everything after it.  Together
+// with the coarse solve in between they are the same operations as cycle(0).
+template <typename T>
+void vcycle_pre(Handle& H, const C2<T>* f, C2<T>* x, cudaStream_t s) {
+    Level<T>* Ls = H.levels<T>();
+    smoother<T>(H, 0, Ls[0], f, x, false, Ls[0].r, s);
+    launch_restrict<T>(Ls[1].f, Ls[0].r, Ls[0].Q, Ls[0].Nx, Ls[0].Nt, Ls[0].h, Gate{}, s);
+    smoother<T>(H, 1, Ls[1], Ls[1].f, Ls[1].x, false, Ls[1].r, s);
+    launch_restrict<T>(Ls[2].f, Ls[1].r, Ls[1].Q, Ls[1].Nx, Ls[1].Nt, Ls[1].h, Gate{}, s);
+}
+
+template <typename T>
+void vcycle_post(Handle& H, const C2<T>* f, C2<T>* x, cudaStream_t s) {
+    Level<T>* Ls = H.levels<T>();
+    launch_prolong<T>(Ls[1].x, Ls[2].x, Ls[1].Q, Ls[1].Nx, Ls[1].Nt, Ls[1].h, true, Gate{}, s);
+    Ls[1].apply(Ls[1].r, Ls[1].x, Ls[1].f, false, Gate{}, s);
+    H.st.mvps[1] += 1;
+    smoother<T>(H, 1, Ls[1], Ls[1].r, Ls[1].x, true, nullptr, s);
+    launch_prolong<T>(x, Ls[1].x, Ls[0].Q, Ls[0].Nx, Ls[0].Nt, Ls[0].h, true, Gate{}, s);
+    Ls[0].apply(Ls[0].r, x, f, false, Gate{}, s);
+    H.st.mvps[0] += 1;
+    smoother<T>(H, 0, Ls[0], Ls[0].r, x, true, nullptr, s);
+}
+
 }  // namespace
 
 mg_status fgmres_solve(Handle& H, const double2* b, double2* x, double tol, cudaStream_t s, int* iters,
@@ -487,6 +520,110 @@ mg_status fgmres_solve(Handle& H, const double2* b, double2* x, double tol, cuda
     }
     *iters = outer;
     H.st.outer += outer;
+    return MG_OK;
+}
+
+// Two right-hand sides on two solve contexts of one hierarchy (mixed
+// precision, deflation space built), driven in lockstep on one stream: every
+// outer step advances each unfinished solve by one preconditioned Arnoldi step,
+// with the two coarsest solves of that step run by one cluster kernel
+// (launch_coarse_proj_pair).  Each solve follows exactly the operations of
+// fgmres_solve on its own context, so its result is the same.
+mg_status fgmres_solve_pair(Handle* HH[2], const double2* const b[2], double2* const x[2], double tol,
+                            cudaStream_t s, int it_out[2], double rr_out[2], bool conv_out[2]) {
+    const long n = HH[0]->L64[0].n;
+    const int m = HH[0]->p.fgmres_m;
+    bool active[2];
+    int jh[2] = {0, 0}, outer[2] = {0, 0};
+    double nb[2];
+    auto r2p = [&](int r) { return MG_DEVF(HH[r]->sc, double, r2); };
+    auto fnb2p = [&](int r) { return MG_DEVF(HH[r]->sc, double, tmp) + 4; };
+    for (int r = 0; r < 2; ++r) launch_norm2<double>(fnb2p(r), b[r], n, HH[r]->red, Gate{}, s);
+    for (int r = 0; r < 2; ++r) {
+        Handle& H = *HH[r];
+        Scalars hs{};
+        MG_TRY(read_scalars(H, hs, s));
+        nb[r] = std::sqrt(hs.tmp[4]);
+        MG_CUDA_TRY(cudaMemsetAsync(x[r], 0, n * sizeof(double2), s));
+        it_out[r] = 0;
+        active[r] = nb[r] != 0.0;
+        if (!active[r]) {
+            rr_out[r] = 0.0;
+            conv_out[r] = true;
+            continue;
+        }
+        MG_CUDA_TRY(cudaMemcpyAsync(H.fr, b[r], n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+    }
+    auto cycle_start = [&](int r) {
+        Handle& H = *HH[r];
+        launch_norm2<double>(r2p(r), H.fr, n, H.red, Gate{}, s);
+        ks_start(H.fks, r2p(r), tol, fnb2p(r), s);
+        launch_scale<double>(H.fV, H.fr, MG_DEVF(H.fks, double, scale), n, Gate{MG_DEVF(H.fks, int, scale_gate), 0}, s);
+        jh[r] = 0;
+    };
+    for (int r = 0; r < 2; ++r)
+        if (active[r]) cycle_start(r);
+    while (active[0] || active[1]) {
+        for (int r = 0; r < 2; ++r) {
+            if (!active[r]) continue;
+            Handle& H = *HH[r];
+                launch_convert<double, float>(H.v32, H.fV + (long)jh[r] * n, n, Gate{}, s);
+            H.cur_outer = outer[r];
+            vcycle_pre<float>(H, H.v32, H.z32, s);
+        }
+        bool paired = false;
+        if (active[0] && active[1] && HH[0]->defl_k > 0 && HH[1]->defl_k > 0) {
+            const CoopArgs<float> a0 = proj_args<float>(*HH[0], HH[0]->L32[2].f, HH[0]->L32[2].x);
+            const CoopArgs<float> a1 = proj_args<float>(*HH[1], HH[1]->L32[2].f, HH[1]->L32[2].x);
+            MG_TRY(launch_coarse_proj_pair(a0, a1, s, &paired));
+            if (paired) {
+                HH[0]->st.coarse_solves += 1;
+                HH[1]->st.coarse_solves += 1;
+            }
+        }
+        for (int r = 0; r < 2 && !paired; ++r)
+            if (active[r]) MG_TRY(coarse_solve<float>(*HH[r], HH[r]->L32[2].f, HH[r]->L32[2].x, s));
+        for (int r = 0; r < 2; ++r) {
+            if (!active[r]) continue;
+            Handle& H = *HH[r];
+                Level<double>& L0 = H.L64[0];
+            vcycle_post<float>(H, H.v32, H.z32, s);
+            double2* z = H.fZ + (long)jh[r] * n;
+            launch_convert<float, double>(z, H.z32, n, Gate{}, s);
+            arnoldi_step<double>(H, [&](double2* w, Gate g) { L0.apply(w, z, nullptr, false, g, s); }, H.fV, n,
+                                 H.fks, jh[r], s);
+            H.st.mvps[0] += 1;
+            ++outer[r];
+        }
+        for (int r = 0; r < 2; ++r) {
+            if (!active[r]) continue;
+            Handle& H = *HH[r];
+                KHost kh;
+            MG_TRY(read_ks(H, H.fks, kh, s));
+            const bool cycle_end = kh.step_gate != jh[r] + 1 || jh[r] + 1 == m || outer[r] >= H.p.max_outer;
+            if (!cycle_end) {
+                ++jh[r];
+                continue;
+            }
+            ks_finish(H.fks, s);
+            launch_axpy_multi<double>(x[r], H.fZ, n, 0, MG_DEVF(H.fks, int, j), MG_DEVF(H.fks, double2, d), 1.0, false,
+                                      n, nullptr, H.red, Gate{}, s);
+            H.L64[0].apply(H.fr, x[r], b[r], false, Gate{}, s);  // true residual b - D x (FP64)
+            H.st.mvps[0] += 1;
+            launch_norm2<double>(r2p(r), H.fr, n, H.red, Gate{}, s);
+            Scalars hs{};
+            MG_TRY(read_scalars(H, hs, s));
+            rr_out[r] = std::sqrt(hs.r2) / nb[r];
+            if (rr_out[r] <= tol || outer[r] >= H.p.max_outer) {
+                conv_out[r] = rr_out[r] <= tol;
+                active[r] = false;
+                it_out[r] = outer[r];
+                H.st.outer += outer[r];
+            } else {
+                cycle_start(r);
+            }
+        }
+    }
     return MG_OK;
 }
 
