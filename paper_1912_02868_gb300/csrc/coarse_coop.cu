@@ -35,7 +35,9 @@
 // mixed-precision V-cycle, FP64 on the plain path).
 #include <cooperative_groups.h>
 
+#include <mutex>
 #include <type_traits>
+#include <vector>
 
 #include "coarse_coop.cuh"
 
@@ -1026,11 +1028,8 @@ struct Geometry {
 };
 
 template <typename T>
-mg_status geometry(long nsite, int ms, int k, Geometry& g) {
+mg_status geometry_uncached(long nsite, int ms, int k, int dev, Geometry& g) {
     static bool configured[2][16] = {};
-    int dev = 0;
-    MG_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 16) dev = 0;
     const int pi = std::is_same<T, float>::value ? 0 : 1;
     if (!configured[pi][dev]) {
         MG_CUDA_TRY(cudaFuncSetAttribute(k_coarse_proj<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1081,6 +1080,31 @@ mg_status geometry(long nsite, int ms, int k, Geometry& g) {
     }
     set_error("coarse solve: no resident cluster shape for %ld coarse sites", nsite);
     return MG_EINVAL;
+}
+
+// geometry_uncached per (precision, device, coarse sites, ms, k), computed once
+// (its occupancy queries cost host time before every coarse solve otherwise)
+template <typename T>
+mg_status geometry(long nsite, int ms, int k, Geometry& g) {
+    struct Entry {
+        long nsite;
+        int ms, k, dev;
+        Geometry g;
+    };
+    static std::mutex mu;
+    static std::vector<Entry> cache;
+    int dev = 0;
+    MG_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 16) dev = 0;
+    std::lock_guard<std::mutex> lock(mu);
+    for (const Entry& e : cache)
+        if (e.nsite == nsite && e.ms == ms && e.k == k && e.dev == dev) {
+            g = e.g;
+            return MG_OK;
+        }
+    MG_TRY(geometry_uncached<T>(nsite, ms, k, dev, g));
+    cache.push_back(Entry{nsite, ms, k, dev, g});
+    return MG_OK;
 }
 
 }  // namespace
