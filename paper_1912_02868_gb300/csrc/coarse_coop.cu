@@ -106,6 +106,42 @@ __device__ __forceinline__ C2<R> cdiv_(C2<R> a, C2<R> b) {
     return mk<R>((a.x * r + a.y) / den, (a.y * r - a.x) / den);
 }
 
+// acc - a * b with every rounding step fixed: both cluster kernels get the same
+// operations, whatever contraction the compiler would pick for a * b - c * d
+template <typename R>
+__device__ __forceinline__ C2<R> cfms_(C2<R> a, C2<R> b, C2<R> acc) {
+    acc.x = fma(-a.x, b.x, acc.x);
+    acc.x = fma(a.y, b.y, acc.x);
+    acc.y = fma(-a.x, b.y, acc.y);
+    acc.y = fma(-a.y, b.x, acc.y);
+    return acc;
+}
+
+// d = R^{-1} g for the jc x jc upper-triangular R (column-major, leading
+// dimension MSMAX + 1, jc <= MSMAX < 32) by one warp, column by column. The
+// lanes first form the reciprocals of their pivots at once (a zero pivot gives
+// zero, so d_i = 0 there); then lane i keeps g_i minus the columns already
+// eliminated, and in turn i its d_i = (that) / R_ii is broadcast to the lanes
+// above.  Only a product, a shuffle and a subtraction stay on the serial chain.
+template <typename R>
+__device__ __forceinline__ void back_subst_warp(const C2<R>* Rm, const C2<R>* g, C2<R>* d, int jc, int lane) {
+    constexpr int LDR = MSMAX + 1;
+    C2<R> inv = mk<R>(0, 0), acc = mk<R>(0, 0);
+    if (lane < jc) {
+        const C2<R> piv = Rm[lane + LDR * lane];
+        if (piv.x != R(0) || piv.y != R(0)) inv = cdiv_<R>(mk<R>(1, 0), piv);
+        acc = g[lane];
+    }
+    for (int i = jc - 1; i >= 0; --i) {
+        const C2<R> rli = (lane < i) ? Rm[lane + LDR * i] : mk<R>(0, 0);
+        C2<R> di = mk<R>(fma(-acc.y, inv.y, acc.x * inv.x), fma(acc.y, inv.x, acc.x * inv.y));
+        di.x = __shfl_sync(0xffffffffu, di.x, i);
+        di.y = __shfl_sync(0xffffffffu, di.y, i);
+        if (lane == i) d[i] = di;
+        if (lane < i) acc = cfms_<R>(rli, di, acc);
+    }
+}
+
 template <typename R>
 __device__ __forceinline__ R rsqrt_(R x) {
     if constexpr (std::is_same<R, float>::value)
@@ -204,11 +240,11 @@ __device__ __forceinline__ C2<T> accum_rows(C2<T> acc, const C2<T>* X, long ldx,
 #pragma unroll
         for (int u = 0; u < 8; ++u) v[u] = X[(long)(i + u) * ldx + e];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) acc = SUB ? csub(acc, cmul(v[u], coef[i + u])) : cfma(v[u], coef[i + u], acc);
+        for (int u = 0; u < 8; ++u) acc = SUB ? cfms_<T>(v[u], coef[i + u], acc) : cfma(v[u], coef[i + u], acc);
     }
     for (; i < cnt; ++i) {
         const C2<T> v = X[(long)i * ldx + e];
-        acc = SUB ? csub(acc, cmul(v, coef[i])) : cfma(v, coef[i], acc);
+        acc = SUB ? cfms_<T>(v, coef[i], acc) : cfma(v, coef[i], acc);
     }
     return acc;
 }
@@ -228,14 +264,14 @@ __device__ __forceinline__ void accum_rows2(C2<T>& acc0, C2<T>& acc1, const C2<T
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-            acc0 = SUB ? csub(acc0, cmul(v[u], coef0[i + u])) : cfma(v[u], coef0[i + u], acc0);
-            acc1 = SUB ? csub(acc1, cmul(w[u], coef1[i + u])) : cfma(w[u], coef1[i + u], acc1);
+            acc0 = SUB ? cfms_<T>(v[u], coef0[i + u], acc0) : cfma(v[u], coef0[i + u], acc0);
+            acc1 = SUB ? cfms_<T>(w[u], coef1[i + u], acc1) : cfma(w[u], coef1[i + u], acc1);
         }
     }
     for (; i < cnt; ++i) {
         const C2<T> v = X0[(long)i * ldx + e], w = X1[(long)i * ldx + e];
-        acc0 = SUB ? csub(acc0, cmul(v, coef0[i])) : cfma(v, coef0[i], acc0);
-        acc1 = SUB ? csub(acc1, cmul(w, coef1[i])) : cfma(w, coef1[i], acc1);
+        acc0 = SUB ? cfms_<T>(v, coef0[i], acc0) : cfma(v, coef0[i], acc0);
+        acc1 = SUB ? cfms_<T>(w, coef1[i], acc1) : cfma(w, coef1[i], acc1);
     }
 }
 
@@ -364,7 +400,7 @@ __global__ void __maxnreg__(128) k_coarse_proj(CoopArgs<T> a) {
                 rot_<T>((T)P->rc[t], from_d2<T>(P->rs[t]), g[P->ra[t]], g[P->rb[t]]);
             for (int i = k - 1; i >= 0; --i) {
                 Z acc = g[i];
-                for (int m = i + 1; m < k; ++m) acc = csub(acc, cmul(from_d2<T>(P->R[i + KLD * m]), dd[m]));
+                for (int m = i + 1; m < k; ++m) acc = cfms_<T>(from_d2<T>(P->R[i + KLD * m]), dd[m], acc);
                 dd[i] = cdiv_<T>(acc, from_d2<T>(P->R[i + KLD * i]));
             }
             for (int i = 0; i < k; ++i) Mp[i + k * l] = dd[i];
@@ -451,10 +487,19 @@ __global__ void __maxnreg__(128) k_coarse_proj(CoopArgs<T> a) {
         push_gram<T>(cluster, rl, 0, 0, rl, nrows, true, &S.inbox[0][0][0], nwr);
         cluster.sync();
         reduce_inbox<T>(&S.inbox[0][0][0], ncta, 1, S.red, nwr);
-        const double beta = sqrt(fmax((double)S.red[0].x, 0.0));
-        if (beta <= tol_abs || beta == 0.0) {
-            conv = 1;
-            break;
+        // beta = ||r|| (FP64 square root and division: thread 0 alone, as the
+        // FP64 units are few), the stop test, and the start of the cycle
+        if (tid == 0) {
+            const double beta = sqrt(fmax((double)S.red[0].x, 0.0));
+            const int done = (beta <= tol_abs || beta == 0.0) ? 1 : 0;
+            S.ctl[2] = done;
+            if (!done) {
+                for (int i = 0; i <= ms; ++i) {
+                    st.c[i] = mk<T>(i == 0 ? (T)beta : T(0), 0);
+                    st.g[i] = st.c[i];
+                }
+                S.scal[0] = (T)(1.0 / beta);
+            }
         }
         // ---- one GMRES(ms) cycle from r ----
         // (shared memory is not zero-initialised: H must be zero below its subdiagonal)
@@ -462,14 +507,11 @@ __global__ void __maxnreg__(128) k_coarse_proj(CoopArgs<T> a) {
             st.H[e] = mk<T>(0, 0);
             st.Rm[e] = mk<T>(0, 0);
         }
-        if (tid == 0) {
-            for (int i = 0; i <= ms; ++i) {
-                st.c[i] = mk<T>(i == 0 ? (T)beta : T(0), 0);
-                st.g[i] = st.c[i];
-            }
-            S.scal[0] = (T)(1.0 / beta);
-        }
         __syncthreads();
+        if (S.ctl[2]) {
+            conv = 1;
+            break;
+        }
         {
             const T sc = S.scal[0];
             for (int e = tid; e < nrows; e += nt) {
@@ -567,18 +609,11 @@ __global__ void __maxnreg__(128) k_coarse_proj(CoopArgs<T> a) {
         }
         // ---- finish the cycle: d = R^{-1} g, rho = c - H d, x += V d, r = V rho ----
         const int jj = j;
-        if (tid == 0) {
-            for (int i = jj - 1; i >= 0; --i) {
-                Z acc = st.g[i];
-                for (int l = i + 1; l < jj; ++l) acc = csub(acc, cmul(st.Rm[i + LD * l], st.d[l]));
-                const Z piv = st.Rm[i + LD * i];
-                st.d[i] = (piv.x == T(0) && piv.y == T(0)) ? mk<T>(0, 0) : cdiv_<T>(acc, piv);
-            }
-        }
+        if (tid < 32) back_subst_warp<T>(st.Rm, st.g, st.d, jj, tid);
         __syncthreads();
         for (int i = tid; i <= jj; i += nt) {
             Z acc = st.c[i];
-            for (int l = 0; l < jj; ++l) acc = csub(acc, cmul(st.H[i + LD * l], st.d[l]));
+            for (int l = 0; l < jj; ++l) acc = cfms_<T>(st.H[i + LD * l], st.d[l], acc);
             st.rho[i] = acc;
         }
         __syncthreads();
@@ -763,7 +798,7 @@ __global__ void __maxnreg__(128) k_coarse_proj_pair(CoopArgs<T> a0, CoopArgs<T> 
                 rot_<T>((T)P->rc[t], from_d2<T>(P->rs[t]), g[P->ra[t]], g[P->rb[t]]);
             for (int i = k - 1; i >= 0; --i) {
                 Z acc = g[i];
-                for (int m = i + 1; m < k; ++m) acc = csub(acc, cmul(from_d2<T>(P->R[i + KLD * m]), dd[m]));
+                for (int m = i + 1; m < k; ++m) acc = cfms_<T>(from_d2<T>(P->R[i + KLD * m]), dd[m], acc);
                 dd[i] = cdiv_<T>(acc, from_d2<T>(P->R[i + KLD * i]));
             }
             for (int i = 0; i < k; ++i) Mp[i + k * l] = dd[i];
@@ -822,32 +857,34 @@ __global__ void __maxnreg__(128) k_coarse_proj_pair(CoopArgs<T> a0, CoopArgs<T> 
         push_gram2<T>(rlc, 0, 0, rlc, nrows, true, in0, act, ncta, rank, nw);
         cluster.sync();
         reduce_inbox2<T>(in0, ncta, 1, redp, act, nw);
-        double beta[2] = {0.0, 0.0};
-        for (int b = 0; b < 2; ++b) {
-            if (!act[b]) continue;
-            beta[b] = sqrt(fmax((double)S.red[b][0].x, 0.0));
-            if (beta[b] <= tol_abs[b] || beta[b] == 0.0) {
-                conv[b] = 1;
-                act[b] = 0;
+        // beta_b = ||r_b||, the stop tests and the starts of the cycles, by thread 0
+        // (FP64 square root and division), as in k_coarse_proj
+        if (tid == 0)
+            for (int b = 0; b < 2; ++b) {
+                S.ctl[b][2] = 1;
+                if (!act[b]) continue;
+                const double beta = sqrt(fmax((double)S.red[b][0].x, 0.0));
+                if (beta <= tol_abs[b] || beta == 0.0) continue;
+                S.ctl[b][2] = 0;
+                for (int i = 0; i <= ms; ++i) {
+                    S.st[b].c[i] = mk<T>(i == 0 ? (T)beta : T(0), 0);
+                    S.st[b].g[i] = S.st[b].c[i];
+                }
+                S.scal[b][0] = (T)(1.0 / beta);
             }
-        }
-        if (!act[0] && !act[1]) break;
         // ---- one GMRES(ms) cycle from r for each active right-hand side ----
         for (int e = tid; e < 2 * LD * MSMAX; e += nt) {
             const int b = e / (LD * MSMAX), q = e - b * (LD * MSMAX);
             S.st[b].H[q] = mk<T>(0, 0);
             S.st[b].Rm[q] = mk<T>(0, 0);
         }
-        if (tid == 0)
-            for (int b = 0; b < 2; ++b) {
-                if (!act[b]) continue;
-                for (int i = 0; i <= ms; ++i) {
-                    S.st[b].c[i] = mk<T>(i == 0 ? (T)beta[b] : T(0), 0);
-                    S.st[b].g[i] = S.st[b].c[i];
-                }
-                S.scal[b][0] = (T)(1.0 / beta[b]);
-            }
         __syncthreads();
+        for (int b = 0; b < 2; ++b)
+            if (act[b] && S.ctl[b][2]) {
+                conv[b] = 1;
+                act[b] = 0;
+            }
+        if (!act[0] && !act[1]) break;
         for (int e = tid; e < 2 * nrows; e += nt) {
             const int b = e / nrows, rr = e - b * nrows;
             if (!act[b]) continue;
@@ -979,22 +1016,14 @@ __global__ void __maxnreg__(128) k_coarse_proj_pair(CoopArgs<T> a0, CoopArgs<T> 
             }
         }
         // ---- finish the cycle of each active right-hand side ----
-        if (lane == 0 && warp < 2 && act[warp]) {  // back substitution: warp b's lane 0
-            const int b = warp, jc = jj[b];
-            Small<T>& st = S.st[b];
-            for (int i = jc - 1; i >= 0; --i) {
-                Z acc = st.g[i];
-                for (int l = i + 1; l < jc; ++l) acc = csub(acc, cmul(st.Rm[i + LD * l], st.d[l]));
-                const Z piv = st.Rm[i + LD * i];
-                st.d[i] = (piv.x == T(0) && piv.y == T(0)) ? mk<T>(0, 0) : cdiv_<T>(acc, piv);
-            }
-        }
+        if (warp < 2 && act[warp])  // back substitution of right-hand side b by warp b
+            back_subst_warp<T>(S.st[warp].Rm, S.st[warp].g, S.st[warp].d, jj[warp], lane);
         __syncthreads();
         for (int t = tid; t < 2 * (MSMAX + 1); t += nt) {
             const int b = t / (MSMAX + 1), i = t - b * (MSMAX + 1);
             if (!act[b] || i > jj[b]) continue;
             Z acc = S.st[b].c[i];
-            for (int l = 0; l < jj[b]; ++l) acc = csub(acc, cmul(S.st[b].H[i + LD * l], S.st[b].d[l]));
+            for (int l = 0; l < jj[b]; ++l) acc = cfms_<T>(S.st[b].H[i + LD * l], S.st[b].d[l], acc);
             S.st[b].rho[i] = acc;
         }
         __syncthreads();
