@@ -44,7 +44,7 @@ typedef enum {
     MG_ECUDA = -3,      /* a CUDA runtime call failed */
     MG_ENOTCONV = -4,   /* a solve reached its iteration limit */
     MG_EBUDGET = -5,    /* reserved for memory-budget admission */
-    MG_ETIMEOUT = -6    /* reserved for bounded device waits */
+    MG_ETIMEOUT = -6    /* a bounded device wait gave up (the coarse kernel's dataflow exchange) */
 } mg_status;
 
 /* coarsest-grid solver (Section 2) */

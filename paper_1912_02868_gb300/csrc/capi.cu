@@ -243,6 +243,7 @@ mg_status solve_rhs_pairs(Handle& A, Handle& Bh, const double2* B, double2* X, i
         std::memcpy(&cs, Hp->pinned, sizeof cs);
         Hp->st.coarse_iters += cs.iters;
         Hp->st.mvps[2] += cs.iters;
+        if (cs.timeouts) return set_error("coarse solve: a bounded wait of the dataflow exchange gave up"), MG_ETIMEOUT;
     }
     return result;
 }
@@ -288,6 +289,7 @@ mg_status solve_rhs(Handle& H, const double2* B, double2* X, bool bdev, bool xde
     std::memcpy(&cs, H.pinned, sizeof cs);
     H.st.coarse_iters += cs.iters;
     H.st.mvps[2] += cs.iters;
+    if (cs.timeouts) return set_error("coarse solve: a bounded wait of the dataflow exchange gave up"), MG_ETIMEOUT;
     return result;
 }
 

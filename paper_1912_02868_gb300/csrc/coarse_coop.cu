@@ -53,6 +53,7 @@ constexpr int MAX_SPC = 16;       // sites per apply chunk (staged neighbour row
 constexpr int MAX_NB_SITES = 64;  // sites per CTA in the neighbour table
 constexpr int MAX_CLUSTER = 16;    // CTAs of one cluster (non-portable size)
 constexpr size_t SMEM_LIMIT = 227 * 1024;
+constexpr long FLOW_SPIN = 1L << 20;  // try_wait rounds before a dataflow wait gives up
 
 template <typename R>
 struct Small {  // per-CTA copy of the small least-squares state, precision R
@@ -79,6 +80,8 @@ struct ClusterSmem {
     Small<T> st;
     T scal[8];
     int ctl[8];
+    unsigned long long mb[3];  // dataflow mode: arrivals of inbox[0], inbox[1] and xs
+    int fault;                 // dataflow mode: a wait gave up
 };
 
 // dynamic shared memory: ClusterSmem, then (optionally) the basis slice
@@ -301,6 +304,50 @@ __device__ void reduce_inbox(const C2<T>* inbox, int nr, int n, C2<T>* red, int 
 __device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory"); }
 __device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory"); }
 
+// Dataflow exchange (push mode): instead of a cluster barrier after each push,
+// every value goes out by st.async, which counts its bytes on an mbarrier in the
+// receiving CTA; a CTA goes on once its barrier has seen all the bytes of the
+// phase (armed by its thread 0 with the expected count).
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ unsigned cluster_addr(unsigned local, int rank) {
+    unsigned r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(r) : "r"(local), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arm(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+// bounded wait for the completion of the phase with this parity (acquiring the
+// cluster's st.async writes); false when it gave up
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+    const unsigned addr = smem_addr(bar);
+    for (long it = 0; it < FLOW_SPIN; ++it) {
+        unsigned ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+__device__ __forceinline__ void st_async(unsigned dst, float2 v, unsigned bar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];\n" ::"r"(dst),
+                 "f"(v.x), "f"(v.y), "r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void st_async(unsigned dst, double2 v, unsigned bar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f64 [%0], {%1, %2}, [%3];\n" ::"r"(dst),
+                 "d"(v.x), "d"(v.y), "r"(bar)
+                 : "memory");
+}
+
 __device__ __forceinline__ long nbr_site(long s, int d, int Nx, int Nt) {
     const int xx = (int)(s % Nx), tt = (int)(s / Nx);
     if (d == 1) return (xx + 1 == Nx) ? s - xx : s + 1;
@@ -319,6 +366,54 @@ __device__ __forceinline__ void push_row(ClusterSmem<T>& S, int me, int e, C2<T>
     for (int q = 0; q < 5; ++q) {
         const int code = S.pusht[ls][q];
         st_rank<T>(&S.xs[(code >> 3) & 0x1fff][code & 7][kk], code >> 16, me, v);
+    }
+}
+
+// push_gram and push_row in dataflow mode: the same values to the same places,
+// by st.async counted on the receiver's barrier bar (inbox or staging slots).
+template <typename T>
+__device__ void push_gram_flow(const C2<T>* X, long ldx, int nd, const C2<T>* y, int nrows, bool norm, C2<T>* inbox,
+                               unsigned long long* bar, int nr, int me, int nw) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (warp >= nw) return;
+    const int ntot = nd + (norm ? 1 : 0);
+    const unsigned bar_r = lane < nr ? cluster_addr(smem_addr(bar), lane) : 0u;
+    for (int i = warp; i < ntot; i += nw) {
+        C2<T> acc4[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc4[u] = mk<T>(0, 0);
+        const C2<T>* xi = (i < nd) ? X + (long)i * ldx : y;
+        int e = lane;
+        for (; e + 96 < nrows; e += 128) {
+            C2<T> xv[4], yv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                xv[u] = xi[e + 32 * u];
+                yv[u] = y[e + 32 * u];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc4[u] = cfmac(xv[u], yv[u], acc4[u]);
+        }
+        for (; e < nrows; e += 32) acc4[0] = cfmac(xi[e], y[e], acc4[0]);
+        C2<T> acc = cadd(cadd(acc4[0], acc4[1]), cadd(acc4[2], acc4[3]));
+        if (i >= nd) acc.y = 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+        }
+        if (lane < nr) st_async(cluster_addr(smem_addr(inbox + me * PSTR + i), lane), acc, bar_r);
+    }
+}
+template <typename T>
+__device__ __forceinline__ void push_row_flow(ClusterSmem<T>& S, int e, C2<T> v) {
+    const int ls = e / NDOF, kk = e - ls * NDOF;
+    const unsigned bar = smem_addr(&S.mb[2]);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        const int code = S.pusht[ls][q], owner = code >> 16;
+        st_async(cluster_addr(smem_addr(&S.xs[(code >> 3) & 0x1fff][code & 7][kk]), owner), v,
+                 cluster_addr(bar, owner));
     }
 }
 
@@ -373,6 +468,23 @@ __global__ void __maxnreg__(128) k_coarse_proj(CoopArgs<T> a) {
     // through global memory.  Slot q of own site u: the site w whose xs[w][d]
     // holds v(u), i.e. u = nbr(w, d).
     const bool push = a.vs && a.spc <= MAX_SPC;
+    // dataflow mode (push mode with a.flow): the reductions of each Arnoldi step
+    // and the staging of v_{j+1} go by st.async into barriers counted in bytes,
+    // with no cluster barrier in the step.  Buffer reuse stays safe without one:
+    // a CTA can send into a phase's inbox (or staging slots) only after it has
+    // received this CTA's contribution to a later exchange, which this CTA makes
+    // after it has read the buffer.
+    const bool flow = push && a.flow;
+    unsigned fph[3] = {0u, 0u, 0u};  // parity of the next phase of each barrier (row warps)
+    auto flow_wait = [&](int b) {
+        if (!S.fault && !mbar_wait(&S.mb[b], fph[b])) S.fault = 1;
+        fph[b] ^= 1u;
+    };
+    if (flow && tid == 0) {
+        for (int b = 0; b < 3; ++b) mbar_init(&S.mb[b], 1);
+        S.fault = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
     if (push)
         for (int e = tid; e < my_sites * 5; e += nt) {
             const int ls = e / 5, q = e - ls * 5;
@@ -530,6 +642,7 @@ __global__ void __maxnreg__(128) k_coarse_proj(CoopArgs<T> a) {
             Z* wl = Vl + (long)(j + 1) * ldv;
             // w = A v_j on the CTA's rows (column-major 24x24 blocks), MAX_SPC sites at a
             // time: stage the five neighbour rows of each site (other CTAs' rows: through L2)
+            if (flow && j > 0 && !ls_warp) flow_wait(2);  // v_j staged from every neighbour
             for (int c0 = 0; c0 < my_sites; c0 += MAX_SPC) {
                 const int cs = min(MAX_SPC, my_sites - c0);
                 if (!push) {
@@ -558,13 +671,25 @@ __global__ void __maxnreg__(128) k_coarse_proj(CoopArgs<T> a) {
                 conv = S.ctl[0];
                 if (S.ctl[0] | S.ctl[1]) break;  // step j is discarded: j columns
             }
-            push_gram<T>(cluster, Vl, ldv, j + 1, wl, nrows, false, &S.inbox[1][0][0], nwr);
-            cluster.sync();
+            if (flow) {
+                if (tid == 0) mbar_arm(&S.mb[1], (unsigned)(ncta * (j + 1) * sizeof(Z)));
+                push_gram_flow<T>(Vl, ldv, j + 1, wl, nrows, false, &S.inbox[1][0][0], &S.mb[1], ncta, rank, nwr);
+                if (!ls_warp) flow_wait(1);
+            } else {
+                push_gram<T>(cluster, Vl, ldv, j + 1, wl, nrows, false, &S.inbox[1][0][0], nwr);
+                cluster.sync();
+            }
             reduce_inbox<T>(&S.inbox[1][0][0], ncta, j + 1, S.h1, nwr);
             for (int e = tid; e < nrows; e += nt) wl[e] = accum_rows<T, true>(wl[e], Vl, ldv, e, S.h1, j + 1);
             __syncthreads();
-            push_gram<T>(cluster, Vl, ldv, j + 1, wl, nrows, true, &S.inbox[0][0][0], nwr);
-            cluster.sync();
+            if (flow) {
+                if (tid == 0) mbar_arm(&S.mb[0], (unsigned)(ncta * (j + 2) * sizeof(Z)));
+                push_gram_flow<T>(Vl, ldv, j + 1, wl, nrows, true, &S.inbox[0][0][0], &S.mb[0], ncta, rank, nwr);
+                if (!ls_warp) flow_wait(0);
+            } else {
+                push_gram<T>(cluster, Vl, ldv, j + 1, wl, nrows, true, &S.inbox[0][0][0], nwr);
+                cluster.sync();
+            }
             reduce_inbox<T>(&S.inbox[0][0][0], ncta, j + 2, S.red, nwr);
             // h_{j+1,j} = ||w - V h2|| = sqrt(n2 - |h2|^2) (V orthonormal), computed
             // identically by every thread; then v_{j+1} = (w - V h2) / h_{j+1,j}
@@ -576,14 +701,24 @@ __global__ void __maxnreg__(128) k_coarse_proj(CoopArgs<T> a) {
             {
                 const T sc = hn > T(0) ? T(1) / hn : T(0);
                 Z* wg = a.V + (long)(j + 1) * n + r0;
+                if (flow && tid == 0) mbar_arm(&S.mb[2], (unsigned)(my_sites * 5 * NDOF * sizeof(Z)));
                 for (int e = tid; e < nrows; e += nt) {
                     const Z v = cscale(accum_rows<T, true>(wl[e], Vl, ldv, e, S.red, j + 1), sc);
                     wl[e] = v;
-                    if (push)
+                    if (flow)
+                        push_row_flow<T>(S, e, v);
+                    else if (push)
                         push_row<T>(S, rank, e, v);
                     else if (a.vs)
                         wg[e] = v;
                 }
+            }
+            if (flow) {
+                // no barrier: the next apply waits for its staging slots instead; the
+                // least-squares warp updates step j meanwhile
+                if (ls_warp) ls_update(tid & 31, j, hn);
+                ++iters;
+                continue;
             }
             __syncwarp();
             cluster_arrive();  // v_{j+1} complete in this CTA
@@ -604,6 +739,7 @@ __global__ void __maxnreg__(128) k_coarse_proj(CoopArgs<T> a) {
             }
         }
         if (a.lsw && j == ms) {  // the last step's update, when no stop came before
+            if (flow && !ls_warp) flow_wait(2);  // the staging of v_ms, which no apply reads
             __syncthreads();
             conv = S.ctl[0];
         }
@@ -625,6 +761,8 @@ __global__ void __maxnreg__(128) k_coarse_proj(CoopArgs<T> a) {
         __syncthreads();
         if (conv || cycles >= a.max_cycles) break;
     }
+    __syncthreads();
+    if (flow && tid == 0 && S.fault) atomicAdd(reinterpret_cast<unsigned long long*>(&a.out->timeouts), 1ULL);
     if (rank == 0 && tid == 0) {
         a.out->iters += iters;
         a.out->cycles += cycles;
@@ -1150,6 +1288,7 @@ mg_status launch_coarse_proj(const CoopArgs<T>& args_in, cudaStream_t s) {
     a.spc = g.spc;
     a.vs = g.vs;
     a.lsw = g.lsw;
+    a.flow = g.lsw;  // push mode
     cudaLaunchConfig_t cfg{};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -1226,6 +1365,7 @@ mg_status launch_coarse_proj_pair(const CoopArgs<float>& a0in, const CoopArgs<fl
         a0.spc = a1.spc = (int)spc;
         a0.vs = a1.vs = 1;
         a0.lsw = a1.lsw = 0;
+        a0.flow = a1.flow = 0;
         MG_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_coarse_proj_pair<float>, a0, a1));
         count_launch();
         *launched = true;

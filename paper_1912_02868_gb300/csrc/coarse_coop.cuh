@@ -10,6 +10,7 @@ constexpr int PSTR = 64;   // stride of one CTA's partial sums
 // device-side counters of the projected coarse solves
 struct CoopStats {
     long long iters, cycles, solves, unconverged;
+    long long timeouts;  // CTAs in which a bounded wait of the dataflow exchange gave up
 };
 
 template <typename T>
@@ -31,6 +32,8 @@ struct CoopArgs {
     int spc;           // sites per CTA (set by the launcher)
     int vs;            // 1: own basis rows kept in shared memory (set by the launcher)
     int lsw;           // 1: one extra warp runs the least-squares updates (set by the launcher)
+    int flow;          // 1: push mode exchanges each step's values by st.async into byte-counted
+                       // barriers instead of cluster barriers (set by the launcher)
 };
 
 template <typename T>
