@@ -791,6 +791,8 @@ struct PairSmem {
     Small<T> st[2];
     T scal[2][8];
     int ctl[2][8];
+    unsigned long long mb[3];  // dataflow mode, as in ClusterSmem
+    int fault;
 };
 
 // push_gram for the two right-hand sides at once: warp task i forms product i
@@ -799,7 +801,8 @@ struct PairSmem {
 // the summation order is push_gram's.
 template <typename T>
 __device__ void push_gram2(const C2<T>* const X[2], long ldx, int nd, const C2<T>* const y[2], int nrows, bool norm,
-                           C2<T>* const inbox[2], const int act[2], int nr, int me, int nw) {
+                           C2<T>* const inbox[2], const int act[2], int nr, int me, int nw,
+                           unsigned long long* bar = nullptr) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int per = nd + (norm ? 1 : 0);
     const bool on0 = act[0] != 0, on1 = act[1] != 0;
@@ -845,8 +848,14 @@ __device__ void push_gram2(const C2<T>* const X[2], long ldx, int nd, const C2<T
             q.y += __shfl_xor_sync(0xffffffffu, q.y, o);
         }
         if (lane < nr) {
-            if (on0) st_rank<T>(inbox[0] + me * PSTR + i, lane, me, p);
-            if (on1) st_rank<T>(inbox[1] + me * PSTR + i, lane, me, q);
+            if (bar) {  // dataflow mode: st.async counted on the receiver's barrier
+                const unsigned br = cluster_addr(smem_addr(bar), lane);
+                if (on0) st_async(cluster_addr(smem_addr(inbox[0] + me * PSTR + i), lane), p, br);
+                if (on1) st_async(cluster_addr(smem_addr(inbox[1] + me * PSTR + i), lane), q, br);
+            } else {
+                if (on0) st_rank<T>(inbox[0] + me * PSTR + i, lane, me, p);
+                if (on1) st_rank<T>(inbox[1] + me * PSTR + i, lane, me, q);
+            }
         }
     }
 }
@@ -880,12 +889,16 @@ __device__ void reduce_inbox2(C2<T>* const inbox[2], int nr, int n, C2<T>* const
 }
 
 template <typename T>
-__device__ __forceinline__ void push_row2(PairSmem<T>& S, int me, int b, int e, C2<T> v) {
+__device__ __forceinline__ void push_row2(PairSmem<T>& S, int me, int b, int e, C2<T> v, bool flow = false) {
     const int ls = e / NDOF, kk = e - ls * NDOF;
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
-        const int code = S.pusht[ls][q];
-        st_rank<T>(&S.xs[b][(code >> 3) & 0x1fff][code & 7][kk], code >> 16, me, v);
+        const int code = S.pusht[ls][q], owner = code >> 16;
+        C2<T>* dst = &S.xs[b][(code >> 3) & 0x1fff][code & 7][kk];
+        if (flow)
+            st_async(cluster_addr(smem_addr(dst), owner), v, cluster_addr(smem_addr(&S.mb[2]), owner));
+        else
+            st_rank<T>(dst, owner, me, v);
     }
 }
 
@@ -923,6 +936,19 @@ __global__ void __maxnreg__(128) k_coarse_proj_pair(CoopArgs<T> a0, CoopArgs<T> 
         const long w = nbr_site(s0 + ls, from[q], a0.Nx, a0.Nt);
         const int owner = (int)(w / a0.spc);
         S.pusht[ls][q] = (owner << 16) | ((int)(w - (long)owner * a0.spc) << 3) | q;
+    }
+    // dataflow mode for the exchanges of each Arnoldi step, as in k_coarse_proj
+    // (one barrier a phase for both right-hand sides: bytes of the active ones)
+    const bool flow = a0.flow != 0;
+    unsigned fph[3] = {0u, 0u, 0u};
+    auto flow_wait = [&](int b) {
+        if (!S.fault && !mbar_wait(&S.mb[b], fph[b])) S.fault = 1;
+        fph[b] ^= 1u;
+    };
+    if (flow && tid == 0) {
+        for (int b = 0; b < 3; ++b) mbar_init(&S.mb[b], 1);
+        S.fault = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     // projection matrices M, N (shared deflation space), as in k_coarse_proj
     Z* Mp = Vb[1] + (long)(ms + 1) * rows_cap;
@@ -1034,6 +1060,8 @@ __global__ void __maxnreg__(128) k_coarse_proj_pair(CoopArgs<T> a0, CoopArgs<T> 
         int cact[2] = {act[0], act[1]}, jj[2] = {ms, ms};
         for (int j = 0; j < ms && (cact[0] || cact[1]); ++j) {
             Z* wl[2] = {Vb[0] + (long)(j + 1) * ldv, Vb[1] + (long)(j + 1) * ldv};
+            const int nact = cact[0] + cact[1];
+            if (flow && j > 0) flow_wait(2);  // v_j of both staged from every neighbour
             // w_b = A v_b: each block entry loaded once for both vectors
             for (int e = tid; e < nrows; e += nt) {
                 const int ls = e / NDOF, kk = e - ls * NDOF;
@@ -1054,8 +1082,14 @@ __global__ void __maxnreg__(128) k_coarse_proj_pair(CoopArgs<T> a0, CoopArgs<T> 
             __syncthreads();
             const Z* const Vc[2] = {Vb[0], Vb[1]};
             const Z* const wc[2] = {wl[0], wl[1]};
-            push_gram2<T>(Vc, ldv, j + 1, wc, nrows, false, in1, cact, ncta, rank, nw);
-            cluster.sync();
+            if (flow) {
+                if (tid == 0) mbar_arm(&S.mb[1], (unsigned)(nact * ncta * (j + 1) * sizeof(Z)));
+                push_gram2<T>(Vc, ldv, j + 1, wc, nrows, false, in1, cact, ncta, rank, nw, &S.mb[1]);
+                flow_wait(1);
+            } else {
+                push_gram2<T>(Vc, ldv, j + 1, wc, nrows, false, in1, cact, ncta, rank, nw);
+                cluster.sync();
+            }
             reduce_inbox2<T>(in1, ncta, j + 1, h1p, cact, nw);
             if (cact[0] && cact[1]) {
                 for (int rr = tid; rr < nrows; rr += nt) {
@@ -1070,8 +1104,14 @@ __global__ void __maxnreg__(128) k_coarse_proj_pair(CoopArgs<T> a0, CoopArgs<T> 
                     wl[b][rr] = accum_rows<T, true>(wl[b][rr], Vb[b], ldv, rr, S.h1[b], j + 1);
             }
             __syncthreads();
-            push_gram2<T>(Vc, ldv, j + 1, wc, nrows, true, in0, cact, ncta, rank, nw);
-            cluster.sync();
+            if (flow) {
+                if (tid == 0) mbar_arm(&S.mb[0], (unsigned)(nact * ncta * (j + 2) * sizeof(Z)));
+                push_gram2<T>(Vc, ldv, j + 1, wc, nrows, true, in0, cact, ncta, rank, nw, &S.mb[0]);
+                flow_wait(0);
+            } else {
+                push_gram2<T>(Vc, ldv, j + 1, wc, nrows, true, in0, cact, ncta, rank, nw);
+                cluster.sync();
+            }
             reduce_inbox2<T>(in0, ncta, j + 2, redp, cact, nw);
             T hn[2];
             {  // warp butterfly per right-hand side, as in k_coarse_proj (both at once)
@@ -1087,6 +1127,7 @@ __global__ void __maxnreg__(128) k_coarse_proj_pair(CoopArgs<T> a0, CoopArgs<T> 
                 for (int b = 0; b < 2; ++b) hn[b] = sqrt(fmax((T)S.red[b][j + 1].x - h2[b], T(0)));
             }
             const T sc[2] = {hn[0] > T(0) ? T(1) / hn[0] : T(0), hn[1] > T(0) ? T(1) / hn[1] : T(0)};
+            if (flow && tid == 0) mbar_arm(&S.mb[2], (unsigned)(nact * my_sites * 5 * NDOF * sizeof(Z)));
             if (cact[0] && cact[1]) {
                 for (int rr = tid; rr < nrows; rr += nt) {
                     Z w0 = wl[0][rr], w1 = wl[1][rr];
@@ -1095,19 +1136,19 @@ __global__ void __maxnreg__(128) k_coarse_proj_pair(CoopArgs<T> a0, CoopArgs<T> 
                     w1 = cscale(w1, sc[1]);
                     wl[0][rr] = w0;
                     wl[1][rr] = w1;
-                    push_row2<T>(S, rank, 0, rr, w0);
-                    push_row2<T>(S, rank, 1, rr, w1);
+                    push_row2<T>(S, rank, 0, rr, w0, flow);
+                    push_row2<T>(S, rank, 1, rr, w1, flow);
                 }
             } else {
                 const int b = cact[0] ? 0 : 1;
                 for (int rr = tid; rr < nrows; rr += nt) {
                     const Z v = cscale(accum_rows<T, true>(wl[b][rr], Vb[b], ldv, rr, S.red[b], j + 1), sc[b]);
                     wl[b][rr] = v;
-                    push_row2<T>(S, rank, b, rr, v);
+                    push_row2<T>(S, rank, b, rr, v, flow);
                 }
             }
             __syncwarp();
-            cluster_arrive();
+            if (!flow) cluster_arrive();  // dataflow mode: the next apply waits for its slots instead
             // warp b updates the least squares of right-hand side b
             if (warp < 2 && cact[warp]) {
                 const int b = warp;
@@ -1141,7 +1182,7 @@ __global__ void __maxnreg__(128) k_coarse_proj_pair(CoopArgs<T> a0, CoopArgs<T> 
                 }
                 __syncwarp();
             }
-            cluster_wait();
+            if (!flow) cluster_wait();
             __syncthreads();
             for (int b = 0; b < 2; ++b) {
                 if (!cact[b]) continue;
@@ -1153,6 +1194,7 @@ __global__ void __maxnreg__(128) k_coarse_proj_pair(CoopArgs<T> a0, CoopArgs<T> 
                 }
             }
         }
+        if (flow) flow_wait(2);  // the staging of the last step, which no apply reads
         // ---- finish the cycle of each active right-hand side ----
         if (warp < 2 && act[warp])  // back substitution of right-hand side b by warp b
             back_subst_warp<T>(S.st[warp].Rm, S.st[warp].g, S.st[warp].d, jj[warp], lane);
@@ -1176,6 +1218,8 @@ __global__ void __maxnreg__(128) k_coarse_proj_pair(CoopArgs<T> a0, CoopArgs<T> 
         for (int b = 0; b < 2; ++b)
             if (act[b] && (conv[b] || cycles >= a0.max_cycles)) act[b] = 0;
     }
+    __syncthreads();
+    if (flow && tid == 0 && S.fault) atomicAdd(reinterpret_cast<unsigned long long*>(&a0.out->timeouts), 1ULL);
     if (rank == 0 && tid == 0) {
         a0.out->iters += iters[0];
         a0.out->cycles += cycles;
@@ -1365,7 +1409,7 @@ mg_status launch_coarse_proj_pair(const CoopArgs<float>& a0in, const CoopArgs<fl
         a0.spc = a1.spc = (int)spc;
         a0.vs = a1.vs = 1;
         a0.lsw = a1.lsw = 0;
-        a0.flow = a1.flow = 0;
+        a0.flow = a1.flow = 1;
         MG_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_coarse_proj_pair<float>, a0, a1));
         count_launch();
         *launched = true;
