@@ -439,8 +439,9 @@ def run_native(args):
                 "bytes_per_launch": c_bytes, "steps_per_launch": steps_per_launch,
                 "us_per_step": 1e6 * c_avg / max(steps_per_launch, 1), "avg_launch_us": c_avg * 1e6,
                 "launches": c_n, "share_of_timed_gpu_time": None, "peak_source": peak_kind,
-                "note": "latency-bound: each Krylov step is three cluster barriers and DSMEM reductions; the "
-                        "stencil operand (5.9 MB) is L2-resident, so HBM is not the binding limit"}
+                "note": "latency-bound: each Krylov step is two DSMEM reductions and a neighbour exchange, "
+                        "counted on mbarriers; the stencil operand (5.9 MB) is L2-resident, so HBM is not the "
+                        "binding limit"}
     # the bandwidth-bound kernel of the V-cycle: the intermediate-grid 24x24 block stencil (FP32)
     s1 = (L // 4) ** 2
     bytes_per_launch = (5 * 576 + 2 * 24) * 8 * s1  # blocks + input + output, complex64
