@@ -94,6 +94,12 @@ typedef struct {
                               (mixed precision, V-cycle, deflated coarse solve, device buffers;
                               the results equal those of separate solves).  0 (default): one
                               right-hand side per worker */
+    int vcycle_graph;      /* 1 (default): in mixed precision, once the deflation space exists, the
+                              V-cycle (grid-0 and grid-1 smoothing and transfers, the coarse
+                              GMRES-Proj kernel) is captured into a CUDA graph and replayed: one
+                              launch a V-cycle, the same kernels and arguments.  Not with the
+                              partial intermediate solve or with apply timing on.  0: launched
+                              kernel by kernel */
 } mg_params;
 
 /* solver of mg_solve (Section 2 compares both) */

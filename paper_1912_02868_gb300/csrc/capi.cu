@@ -68,6 +68,10 @@ void free_handle(Handle& H) {
     H.own_stream = nullptr;
     if (H.work_stream) cudaStreamDestroy(H.work_stream);
     H.work_stream = nullptr;
+    if (H.vg.exec) cudaGraphExecDestroy(H.vg.exec);
+    H.vg = VGraph{};
+    if (H.cap_stream) cudaStreamDestroy(H.cap_stream);
+    H.cap_stream = nullptr;
     for (auto& t : H.timers) {
         for (cudaEvent_t e : t.ev) cudaEventDestroy(e);
         t.ev.clear();
@@ -116,6 +120,8 @@ mg_status check_params(const mg_params& p) {
                MG_EINVAL;
     if (p.partial_tol > 0.0 && p.coarse_solver != MG_COARSE_DR_PROJ)
         return set_error("the partial intermediate solve is built for the deflated coarse solve"), MG_EINVAL;
+    if (p.pair_rhs != 0 && p.pair_rhs != 1) return set_error("pair_rhs must be 0 or 1"), MG_EINVAL;
+    if (p.vcycle_graph != 0 && p.vcycle_graph != 1) return set_error("vcycle_graph must be 0 or 1"), MG_EINVAL;
     return MG_OK;
 }
 
@@ -541,6 +547,7 @@ mg_status mg_default_params(mg_params* p) {
     p->coarse_tol_partial = 1e-2;
     p->partial_max_iters = 200;
     p->pair_rhs = 0;
+    p->vcycle_graph = 1;
     return MG_OK;
 }
 

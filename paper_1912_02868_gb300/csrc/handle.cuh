@@ -96,6 +96,17 @@ struct Stats {
     int dr_solves = 0;
 };
 
+// The captured mixed V-cycle of a handle (mg_params.vcycle_graph): the graph,
+// the deflation size it was captured with, its kernel count and the counters
+// one replay adds.
+struct VGraph {
+    cudaGraphExec_t exec = nullptr;
+    int k = 0;
+    unsigned long long kernels = 0;
+    Stats per_replay;
+    int eligible_runs = 0;  // eligible V-cycles run before capture (the first warms the launch set-up)
+};
+
 struct Handle {
     int Lx = 0, Lt = 0;
     double m0 = 0.0;
@@ -151,6 +162,8 @@ struct Handle {
     bool is_context = false;             // a context: shares hierarchy and deflation, owns workspaces
     cudaStream_t own_stream = nullptr;   // a context's stream
     cudaStream_t work_stream = nullptr;  // this handle's stream for its share of a parallel solve
+    cudaStream_t cap_stream = nullptr;   // stream the V-cycle graph is captured on
+    VGraph vg;
     std::vector<mg_handle_s*> contexts;
     size_t bytes = 0;                    // device bytes this handle allocated
 

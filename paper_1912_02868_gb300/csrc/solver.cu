@@ -13,6 +13,8 @@
 #include <cstring>
 #include <type_traits>
 
+#include <vector>
+
 #include "handle.cuh"
 
 namespace mg {
@@ -428,6 +430,72 @@ mg_status vcycle(Handle& H, int l, const C2<T>* f, C2<T>* x, cudaStream_t s) {
     return cycle<T>(H, l, f, x, s);
 }
 
+// The mixed V-cycle H.v32 -> H.z32 as a CUDA graph (mg_params.vcycle_graph).
+// Eligible once the deflation space exists, in the plain V-cycle mode with the
+// deflated coarse solve and no apply timing: the kernels and their arguments
+// are then the same in every V-cycle (fixed buffers of the handle; the coarse
+// tolerance does not depend on the outer step).  The first eligible V-cycle
+// runs launch by launch, which also sets up the coarse kernel's launch shape
+// outside any capture; the second is captured on the handle's capture stream
+// (nothing runs during capture), instantiated, and from then on every V-cycle
+// is one graph launch on the caller's stream.  A new deflation size re-captures.
+mg_status vcycle_mixed(Handle& H, cudaStream_t s) {
+    bool timing = false;
+    for (const ApplyTimer& t : H.timers) timing = timing || t.on;
+    const bool eligible = H.p.vcycle_graph && H.defl_k > 0 && H.p.partial_tol == 0.0 &&
+                          H.p.coarse_solver == MG_COARSE_DR_PROJ && !timing;
+    if (!eligible) return vcycle<float>(H, 0, H.v32, H.z32, s);
+    VGraph& G = H.vg;
+    if (G.exec && G.k != H.defl_k) {
+        cudaGraphExecDestroy(G.exec);
+        G = VGraph{};
+    }
+    if (!G.exec && G.eligible_runs++ == 0) return vcycle<float>(H, 0, H.v32, H.z32, s);
+    if (!G.exec) {
+        if (!H.cap_stream) MG_CUDA_TRY(cudaStreamCreateWithFlags(&H.cap_stream, cudaStreamNonBlocking));
+        const Stats before = H.st;
+        MG_CUDA_TRY(cudaStreamBeginCapture(H.cap_stream, cudaStreamCaptureModeThreadLocal));
+        const mg_status st = vcycle<float>(H, 0, H.v32, H.z32, H.cap_stream);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(H.cap_stream, &g);
+        const Stats during = H.st;
+        H.st = before;  // nothing ran: the counters advance per replay below
+        size_t nn = 0;
+        std::vector<cudaGraphNode_t> nodes;
+        unsigned long long kernels = 0;
+        if (st == MG_OK && ce == cudaSuccess && g && cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess) {
+            nodes.resize(nn);
+            if (nn && cudaGraphGetNodes(g, nodes.data(), &nn) == cudaSuccess)
+                for (cudaGraphNode_t nd : nodes) {
+                    cudaGraphNodeType ty;
+                    if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++kernels;
+                }
+        }
+        g_launches.fetch_sub(kernels, std::memory_order_relaxed);  // counted at capture, not launched
+        cudaGraphExec_t ex = nullptr;
+        const cudaError_t ie = (st == MG_OK && ce == cudaSuccess) ? cudaGraphInstantiate(&ex, g, 0) : ce;
+        if (g) cudaGraphDestroy(g);
+        if (st != MG_OK) return st;
+        if (ie != cudaSuccess) {
+            (void)cudaGetLastError();
+            set_error("V-cycle graph capture failed: %s", cudaGetErrorString(ie));
+            return MG_ECUDA;
+        }
+        G.exec = ex;
+        G.k = H.defl_k;
+        G.kernels = kernels;
+        for (int l = 0; l < 3; ++l) G.per_replay.mvps[l] = during.mvps[l] - before.mvps[l];
+        G.per_replay.coarse_solves = during.coarse_solves - before.coarse_solves;
+        G.per_replay.coarse_iters = during.coarse_iters - before.coarse_iters;
+    }
+    MG_CUDA_TRY(cudaGraphLaunch(G.exec, s));
+    count_launch(G.kernels);
+    for (int l = 0; l < 3; ++l) H.st.mvps[l] += G.per_replay.mvps[l];
+    H.st.coarse_solves += G.per_replay.coarse_solves;
+    H.st.coarse_iters += G.per_replay.coarse_iters;
+    return MG_OK;
+}
+
 // The V-cycle of grid 0 split at the coarsest solve, for the lockstep pair:
 // everything before it (smoothing on grids 0 and 1, both restrictions, leaving
 // the coarse right-hand side in grid 2's f) and everything after it.  Together
@@ -488,7 +556,7 @@ mg_status fgmres_solve(Handle& H, const double2* b, double2* x, double tol, cuda
             H.cur_outer = outer;
             if (mixed) {
                 launch_convert<double, float>(H.v32, v, n, Gate{}, s);
-                MG_TRY(vcycle<float>(H, 0, H.v32, H.z32, s));
+                MG_TRY(vcycle_mixed(H, s));
                 launch_convert<float, double>(z, H.z32, n, Gate{}, s);
             } else {
                 MG_TRY(vcycle<double>(H, 0, v, z, s));
