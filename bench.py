@@ -563,7 +563,7 @@ def run_native(args):
         "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": "256^2 x 10 configs x 1 RHS per step, deflated MG-FGMRES(8), GMRES-DR(30,10)/"
-                               "GMRES-Proj(30,10), tol 1e-8 true FP64 residual; mixed: FP32 V-cycle, FP64 outer",
+                               "GMRES-Proj(30,10), tol 1e-8 true FP64 residual; mixed: FP32 V-cycle (coarsest operator streamed as an FP16 copy), FP64 outer",
                    "lattice": L, "configs": nconf, "beta": 6.0, "tol": TOL, "precision": "mixed",
                    "l2": "working set > L2: 10 resident hierarchies (~3.8 GB) cycled every step",
                    "parallelism": f"replicas x{world}", "m0_fingerprints_match": fp_ok},

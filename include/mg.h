@@ -100,6 +100,10 @@ typedef struct {
                               launch a V-cycle, the same kernels and arguments.  Not with the
                               partial intermediate solve or with apply timing on.  0: launched
                               kernel by kernel */
+    int coarse_half;       /* 1 (default): in mixed precision, the coarsest operator streamed by the
+                              GMRES-Proj cluster kernels each Arnoldi step is an FP16 copy (each
+                              part rounded once from FP64), multiplied in FP32; the deflation build
+                              (GMRES-DR) keeps the FP64 operator.  0: the FP32 copy */
 } mg_params;
 
 /* solver of mg_solve (Section 2 compares both) */

@@ -6,6 +6,7 @@
 // vectors: FP32) - FP64 arithmetic is a small fraction of the FP32 rate on
 // this GPU, and a reduction sits on the critical path of every Krylov step.
 // Results are always returned as FP64.
+#include <cuda_fp16.h>
 #include "ops.cuh"
 
 namespace mg {
@@ -313,6 +314,21 @@ INST(double)
 INST(float)
 #undef INST
 template void launch_convert<double, float>(C2<float>*, const C2<double>*, long, Gate, cudaStream_t);
+
+// Complex FP64 -> packed FP16 pair (real part in the low half, imaginary in the
+// high half), each part rounded to nearest once from FP64
+__global__ void k_pack_half(unsigned* y, const double2* x, long n) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const double2 v = x[i];
+        const unsigned re = __half_as_ushort(__double2half(v.x));
+        const unsigned im = __half_as_ushort(__double2half(v.y));
+        y[i] = (im << 16) | re;
+    }
+}
+void launch_pack_half(unsigned* y, const double2* x, long n, cudaStream_t s) {
+    k_pack_half<<<ew_blocks(n), 256, 0, s>>>(y, x, n);
+    count_launch();
+}
 template void launch_convert<float, double>(C2<double>*, const C2<float>*, long, Gate, cudaStream_t);
 template void launch_convert<double, double>(C2<double>*, const C2<double>*, long, Gate, cudaStream_t);
 template void launch_convert<float, float>(C2<float>*, const C2<float>*, long, Gate, cudaStream_t);

@@ -122,6 +122,7 @@ mg_status check_params(const mg_params& p) {
         return set_error("the partial intermediate solve is built for the deflated coarse solve"), MG_EINVAL;
     if (p.pair_rhs != 0 && p.pair_rhs != 1) return set_error("pair_rhs must be 0 or 1"), MG_EINVAL;
     if (p.vcycle_graph != 0 && p.vcycle_graph != 1) return set_error("vcycle_graph must be 0 or 1"), MG_EINVAL;
+    if (p.coarse_half != 0 && p.coarse_half != 1) return set_error("coarse_half must be 0 or 1"), MG_EINVAL;
     return MG_OK;
 }
 
@@ -323,6 +324,7 @@ mg_status make_context(Handle& P, mg_handle_s** out) {
         C.A64[l] = P.A64[l];
         C.A32[l] = P.A32[l];
     }
+    C.A16c = P.A16c;
     for (int l = 0; l < 2; ++l) {
         C.Q64[l] = P.Q64[l];
         C.Q32[l] = P.Q32[l];
@@ -443,6 +445,7 @@ mg_status setup_common(const void* gauge, int Lx, int Lt, double m0, int nvec, i
         TRYF(halloc_t(H, &H.A64[l], (size_t)nx[l] * nt[l] * 5 * 576));
         TRYF(halloc_t(H, &H.A32[l], (size_t)nx[l] * nt[l] * 5 * 576));
     }
+    if (p.precision == MG_MIXED && p.coarse_half) TRYF(halloc_t(H, &H.A16c, (size_t)nx[2] * nt[2] * 5 * 576));
     for (int l = 0; l < 2; ++l) {
         const size_t q = (size_t)nx[l + 1] * nt[l + 1] * 24 * 16 * (dof[l] / 2);
         TRYF(halloc_t(H, &H.Q64[l], q));
@@ -548,6 +551,7 @@ mg_status mg_default_params(mg_params* p) {
     p->partial_max_iters = 200;
     p->pair_rhs = 0;
     p->vcycle_graph = 1;
+    p->coarse_half = 1;
     return MG_OK;
 }
 

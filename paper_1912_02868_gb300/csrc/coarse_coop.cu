@@ -34,6 +34,7 @@
 // The small least squares runs in the precision of the vectors (FP32 in the
 // mixed-precision V-cycle, FP64 on the plain path).
 #include <cooperative_groups.h>
+#include <cuda_fp16.h>
 
 #include <mutex>
 #include <type_traits>
@@ -173,6 +174,14 @@ __device__ __forceinline__ void rot_(R c, C2<R> s, C2<R>& up, C2<R>& uq) {
     const C2<R> p = up, q = uq;
     up = cadd(cscale(p, c), cmul(s, q));
     uq = csub(cscale(q, c), cmul(conj_(s), p));
+}
+
+// One complex entry of the FP16 operator copy (real part in the low half)
+template <typename T>
+__device__ __forceinline__ C2<T> half_entry(const unsigned* p) {
+    const unsigned u = __ldg(p);
+    const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&u));
+    return mk<T>((T)f.x, (T)f.y);
 }
 
 // Store v at the address dst has in the shared memory of CTA `rank` of the
@@ -653,17 +662,32 @@ __global__ void __maxnreg__(128) k_coarse_proj(CoopArgs<T> a) {
                     }
                     __syncthreads();
                 }
-                for (int e = tid; e < cs * NDOF; e += nt) {
-                    const int ls = e / NDOF, kk = e - ls * NDOF;
-                    const Z* Ab = a.A + (s0 + c0 + ls) * (5L * NDOF * NDOF) + kk;
-                    Z acc = mk<T>(0, 0);
+                if (a.Ah) {  // FP16 operator copy: half the bytes of the stream, FP32 arithmetic
+                    for (int e = tid; e < cs * NDOF; e += nt) {
+                        const int ls = e / NDOF, kk = e - ls * NDOF;
+                        const unsigned* Ab = a.Ah + (s0 + c0 + ls) * (5L * NDOF * NDOF) + kk;
+                        Z acc = mk<T>(0, 0);
 #pragma unroll
-                    for (int d = 0; d < 5; ++d) {
+                        for (int d = 0; d < 5; ++d) {
 #pragma unroll
-                        for (int l = 0; l < NDOF; ++l)
-                            acc = cfma(__ldg(Ab + (d * NDOF + l) * NDOF), S.xs[ls][d][l], acc);
+                            for (int l = 0; l < NDOF; ++l)
+                                acc = cfma(half_entry<T>(Ab + (d * NDOF + l) * NDOF), S.xs[ls][d][l], acc);
+                        }
+                        wl[(long)c0 * NDOF + e] = acc;
                     }
-                    wl[(long)c0 * NDOF + e] = acc;
+                } else {
+                    for (int e = tid; e < cs * NDOF; e += nt) {
+                        const int ls = e / NDOF, kk = e - ls * NDOF;
+                        const Z* Ab = a.A + (s0 + c0 + ls) * (5L * NDOF * NDOF) + kk;
+                        Z acc = mk<T>(0, 0);
+#pragma unroll
+                        for (int d = 0; d < 5; ++d) {
+#pragma unroll
+                            for (int l = 0; l < NDOF; ++l)
+                                acc = cfma(__ldg(Ab + (d * NDOF + l) * NDOF), S.xs[ls][d][l], acc);
+                        }
+                        wl[(long)c0 * NDOF + e] = acc;
+                    }
                 }
                 __syncthreads();
             }
@@ -1065,15 +1089,28 @@ __global__ void __maxnreg__(128) k_coarse_proj_pair(CoopArgs<T> a0, CoopArgs<T> 
             // w_b = A v_b: each block entry loaded once for both vectors
             for (int e = tid; e < nrows; e += nt) {
                 const int ls = e / NDOF, kk = e - ls * NDOF;
-                const Z* Ab = a0.A + (s0 + ls) * (5L * NDOF * NDOF) + kk;
                 Z acc0 = mk<T>(0, 0), acc1 = mk<T>(0, 0);
+                if (a0.Ah) {  // FP16 operator copy, as in k_coarse_proj
+                    const unsigned* Ab = a0.Ah + (s0 + ls) * (5L * NDOF * NDOF) + kk;
 #pragma unroll
-                for (int d = 0; d < 5; ++d) {
+                    for (int d = 0; d < 5; ++d) {
 #pragma unroll
-                    for (int l = 0; l < NDOF; ++l) {
-                        const Z av = __ldg(Ab + (d * NDOF + l) * NDOF);
-                        acc0 = cfma(av, S.xs[0][ls][d][l], acc0);
-                        acc1 = cfma(av, S.xs[1][ls][d][l], acc1);
+                        for (int l = 0; l < NDOF; ++l) {
+                            const Z av = half_entry<T>(Ab + (d * NDOF + l) * NDOF);
+                            acc0 = cfma(av, S.xs[0][ls][d][l], acc0);
+                            acc1 = cfma(av, S.xs[1][ls][d][l], acc1);
+                        }
+                    }
+                } else {
+                    const Z* Ab = a0.A + (s0 + ls) * (5L * NDOF * NDOF) + kk;
+#pragma unroll
+                    for (int d = 0; d < 5; ++d) {
+#pragma unroll
+                        for (int l = 0; l < NDOF; ++l) {
+                            const Z av = __ldg(Ab + (d * NDOF + l) * NDOF);
+                            acc0 = cfma(av, S.xs[0][ls][d][l], acc0);
+                            acc1 = cfma(av, S.xs[1][ls][d][l], acc1);
+                        }
                     }
                 }
                 if (cact[0]) wl[0][e] = acc0;
@@ -1357,7 +1394,7 @@ mg_status launch_coarse_proj_pair(const CoopArgs<float>& a0in, const CoopArgs<fl
                                   bool* launched) {
     *launched = false;
     CoopArgs<float> a0 = a0in, a1 = a1in;
-    if (a0.A != a1.A || a0.W != a1.W || a0.pls != a1.pls || a0.k != a1.k || a0.ms != a1.ms || a0.Nx != a1.Nx ||
+    if (a0.A != a1.A || a0.Ah != a1.Ah || a0.W != a1.W || a0.pls != a1.pls || a0.k != a1.k || a0.ms != a1.ms || a0.Nx != a1.Nx ||
         a0.Nt != a1.Nt || a0.max_cycles != a1.max_cycles) {
         set_error("coarse pair solve: the two solves must share the operator and the deflation space");
         return MG_EINVAL;

@@ -16,6 +16,8 @@ struct CoopStats {
 template <typename T>
 struct CoopArgs {
     const C2<T>* A;    // coarse stencil, column-major 24x24 blocks
+    const unsigned* Ah;  // or null: the same stencil in FP16 (real part in the low half), read
+                         // instead of A by the push-mode apply (FP32 arithmetic)
     int Nx, Nt;        // coarse grid
     const C2<T>* f;    // right-hand side
     C2<T>* x;          // solution (output, initial guess zero)

@@ -123,6 +123,7 @@ struct Handle {
     double2* Q64[2] = {nullptr, nullptr};
     float2* U32 = nullptr;
     float2* A32[3] = {nullptr, nullptr, nullptr};
+    unsigned* A16c = nullptr;  // FP16 copy of the coarsest operator for the cluster kernels (coarse_half)
     float2* Q32[2] = {nullptr, nullptr};
     // fine FGMRES (FP64)
     double2* fV = nullptr;  // (m+1) x n0

@@ -67,6 +67,8 @@ template <typename Ta, typename Tb>
 void launch_convert(C2<Tb>* y, const C2<Ta>* x, long n, Gate g, cudaStream_t s);
 // y = x + a * y  with a = (*num / *den) (CG search direction update), or when
 // den == nullptr, a = *num.
+// FP16 copy of a complex FP64 array: y[i] = half(re) | half(im) << 16
+void launch_pack_half(unsigned* y, const double2* x, long n, cudaStream_t s);
 template <typename T>
 void launch_xpay(C2<T>* y, const C2<T>* x, const double* num, const double* den, long n, Gate g, cudaStream_t s);
 // CG step: e += alpha p, r -= alpha q, alpha = *rr / *pq (real); *rr_new = ||r||^2

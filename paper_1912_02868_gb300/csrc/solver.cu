@@ -306,6 +306,7 @@ CoopArgs<T> proj_args(Handle& H, const C2<T>* f, C2<T>* x) {
     a.part = H.cpart;
     a.part_ctas = H.cpart_ctas;
     a.out = H.cstats;
+    a.Ah = std::is_same<T, float>::value ? H.A16c : nullptr;
     return a;
 }
 
@@ -816,6 +817,7 @@ mg_status build_hierarchy(Handle& H, const double2* gauge_dev, const double2* st
     launch_convert<double, float>(H.U32, H.U64, 2L * L[0].Nx * L[0].Nt, Gate{}, s);
     for (int l = 1; l < 3; ++l)
         launch_convert<double, float>(H.A32[l], H.A64[l], (long)L[l].Nx * L[l].Nt * 5 * 576, Gate{}, s);
+    if (H.A16c) launch_pack_half(H.A16c, H.A64[2], (long)L[2].Nx * L[2].Nt * 5 * 576, s);
     for (int l = 0; l < 2; ++l)
         launch_convert<double, float>(H.Q32[l], H.Q64[l], (long)L[l + 1].Nx * L[l + 1].Nt * 24 * 16 * L[l].h,
                                       Gate{}, s);
