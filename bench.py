@@ -420,11 +420,12 @@ def run_native(args):
 
     # Roofline of the dominant kernel: the coarsest-grid GMRES-Proj solve (one cluster
     # kernel per coarse solve, ~90% of the solve time).  Algorithmic bytes of one of
-    # its Krylov steps: the 16^2 x 5 x 24 x 24 complex64 stencil read once, v_j read
-    # and v_{j+1} written once; steps per launch from the solve counters.
+    # its Krylov steps: the 16^2 x 5 x 24 x 24 stencil read once (its FP16 copy, 4 bytes
+    # an entry, as the mixed default streams it), v_j read and v_{j+1} written once
+    # (complex64); steps per launch from the solve counters.
     peaks, peak_kind = measured_peaks()
     s2 = (L // 16) ** 2
-    step_bytes = (5 * 576 + 2 * 24) * 8 * s2
+    step_bytes = (5 * 576 * 4 + 2 * 24 * 8) * s2
     c_ms, c_n = kt[2]
     steps_per_launch = kt["coarse_iters"] / max(kt["coarse_solves"] - kt["dr_solves"], 1)
     c_avg = c_ms / 1e3 / max(c_n, 1)
@@ -439,7 +440,8 @@ def run_native(args):
         return None
     roofline = {"bound": "hbm", "achieved": c_ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": c_ach / peaks["hbm_gbs"], "traffic": traffic_of("coarse_proj_f32_256.json"),
-                "kernel": "k_coarse_proj<float> (whole coarse GMRES-Proj solve, 16^2 x 24, cluster of 16 CTAs)",
+                "kernel": "k_coarse_proj<float> (whole coarse GMRES-Proj solve, 16^2 x 24, FP16 operator, "
+                          "cluster of 16 CTAs)",
                 "bytes_per_launch": c_bytes, "steps_per_launch": steps_per_launch,
                 "us_per_step": 1e6 * c_avg / max(steps_per_launch, 1), "avg_launch_us": c_avg * 1e6,
                 "launches": c_n, "share_of_timed_gpu_time": None, "peak_source": peak_kind,

@@ -55,6 +55,12 @@ constexpr int MAX_NB_SITES = 64;  // sites per CTA in the neighbour table
 constexpr int MAX_CLUSTER = 16;    // CTAs of one cluster (non-portable size)
 constexpr size_t SMEM_LIMIT = 227 * 1024;
 constexpr long FLOW_SPIN = 1L << 20;  // try_wait rounds before a dataflow wait gives up
+// FP16 operator (push mode): the blocks of directions 0..ASH_DIRS-1 of a CTA's
+// sites stay in its shared memory for the whole solve, the other directions
+// stream from L2 each step.  A site's part is padded by 24 words so that the two
+// sites one warp reads fall on different banks.
+constexpr int ASH_DIRS = 3;
+constexpr int ASH_SITE_WORDS = ASH_DIRS * 24 * 24 + 24;
 
 template <typename R>
 struct Small {  // per-CTA copy of the small least-squares state, precision R
@@ -178,10 +184,13 @@ __device__ __forceinline__ void rot_(R c, C2<R> s, C2<R>& up, C2<R>& uq) {
 
 // One complex entry of the FP16 operator copy (real part in the low half)
 template <typename T>
-__device__ __forceinline__ C2<T> half_entry(const unsigned* p) {
-    const unsigned u = __ldg(p);
+__device__ __forceinline__ C2<T> half_bits(unsigned u) {
     const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&u));
     return mk<T>((T)f.x, (T)f.y);
+}
+template <typename T>
+__device__ __forceinline__ C2<T> half_entry(const unsigned* p) {
+    return half_bits<T>(__ldg(p));
 }
 
 // Store v at the address dst has in the shared memory of CTA `rank` of the
@@ -533,6 +542,15 @@ __global__ void __maxnreg__(128) k_coarse_proj(CoopArgs<T> a) {
         }
     }
 
+    // a.ash: the FP16 blocks of the first ASH_DIRS directions of the own sites,
+    // copied once into shared memory after M and N
+    unsigned* Ash = reinterpret_cast<unsigned*>(Np + (k + 1) * (k + 1));
+    if (a.ash)
+        for (int e = tid; e < my_sites * ASH_DIRS * NDOF * NDOF; e += nt) {
+            const int ls = e / (ASH_DIRS * NDOF * NDOF), q = e - ls * (ASH_DIRS * NDOF * NDOF);
+            Ash[ls * ASH_SITE_WORDS + q] = a.Ah[(s0 + ls) * (5L * NDOF * NDOF) + q];
+        }
+
     Z* xl = a.x + r0;
     Z* rl = a.r + r0;
     // x = 0, r = f, ||f||^2
@@ -667,11 +685,24 @@ __global__ void __maxnreg__(128) k_coarse_proj(CoopArgs<T> a) {
                         const int ls = e / NDOF, kk = e - ls * NDOF;
                         const unsigned* Ab = a.Ah + (s0 + c0 + ls) * (5L * NDOF * NDOF) + kk;
                         Z acc = mk<T>(0, 0);
+                        if (a.ash) {  // push mode: c0 == 0
+                            const unsigned* As = Ash + ls * ASH_SITE_WORDS + kk;
 #pragma unroll
-                        for (int d = 0; d < 5; ++d) {
+                            for (int d = 0; d < 5; ++d) {
 #pragma unroll
-                            for (int l = 0; l < NDOF; ++l)
-                                acc = cfma(half_entry<T>(Ab + (d * NDOF + l) * NDOF), S.xs[ls][d][l], acc);
+                                for (int l = 0; l < NDOF; ++l) {
+                                    const Z av = d < ASH_DIRS ? half_bits<T>(As[(d * NDOF + l) * NDOF])
+                                                              : half_entry<T>(Ab + (d * NDOF + l) * NDOF);
+                                    acc = cfma(av, S.xs[ls][d][l], acc);
+                                }
+                            }
+                        } else {
+#pragma unroll
+                            for (int d = 0; d < 5; ++d) {
+#pragma unroll
+                                for (int l = 0; l < NDOF; ++l)
+                                    acc = cfma(half_entry<T>(Ab + (d * NDOF + l) * NDOF), S.xs[ls][d][l], acc);
+                            }
                         }
                         wl[(long)c0 * NDOF + e] = acc;
                     }
@@ -1271,8 +1302,8 @@ __global__ void __maxnreg__(128) k_coarse_proj_pair(CoopArgs<T> a0, CoopArgs<T> 
 }
 
 struct Geometry {
-    int cluster = 1, spc = 1, threads = 32, vs = 0, lsw = 0;
-    size_t smem = 0;
+    int cluster = 1, spc = 1, threads = 32, vs = 0, lsw = 0, ash = 0;
+    size_t smem = 0, smem_ash = 0;  // dynamic shared memory without / with the shared FP16 blocks
 };
 
 template <typename T>
@@ -1323,6 +1354,18 @@ mg_status geometry_uncached(long nsite, int ms, int k, int dev, Geometry& g) {
             g.vs = vs;
             g.lsw = lsw;
             g.smem = smem;
+            // FP32 push mode: room for the shared FP16 blocks (used when the handle
+            // streams the FP16 operator), if the number of resident clusters holds
+            const size_t ash_bytes = (size_t)spc * ASH_SITE_WORDS * sizeof(unsigned);
+            if (std::is_same<T, float>::value && lsw && smem + ash_bytes <= SMEM_LIMIT) {
+                cfg.dynamicSmemBytes = smem + ash_bytes;
+                int nc2 = 0;
+                if (cudaOccupancyMaxActiveClusters(&nc2, k_coarse_proj<T>, &cfg) == cudaSuccess && nc2 >= nclusters) {
+                    g.ash = 1;
+                    g.smem_ash = smem + ash_bytes;
+                }
+                (void)cudaGetLastError();
+            }
             return MG_OK;
         }
     }
@@ -1370,6 +1413,7 @@ mg_status launch_coarse_proj(const CoopArgs<T>& args_in, cudaStream_t s) {
     a.vs = g.vs;
     a.lsw = g.lsw;
     a.flow = g.lsw;  // push mode
+    a.ash = (g.ash && a.Ah) ? 1 : 0;
     cudaLaunchConfig_t cfg{};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -1378,7 +1422,7 @@ mg_status launch_coarse_proj(const CoopArgs<T>& args_in, cudaStream_t s) {
     attr[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3(g.cluster);
     cfg.blockDim = dim3(g.threads);
-    cfg.dynamicSmemBytes = g.smem;
+    cfg.dynamicSmemBytes = a.ash ? g.smem_ash : g.smem;
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
@@ -1446,6 +1490,7 @@ mg_status launch_coarse_proj_pair(const CoopArgs<float>& a0in, const CoopArgs<fl
         a0.spc = a1.spc = (int)spc;
         a0.vs = a1.vs = 1;
         a0.lsw = a1.lsw = 0;
+        a0.ash = a1.ash = 0;
         a0.flow = a1.flow = 1;
         MG_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_coarse_proj_pair<float>, a0, a1));
         count_launch();

@@ -34,6 +34,8 @@ struct CoopArgs {
     int spc;           // sites per CTA (set by the launcher)
     int vs;            // 1: own basis rows kept in shared memory (set by the launcher)
     int lsw;           // 1: one extra warp runs the least-squares updates (set by the launcher)
+    int ash;           // 1: the FP16 blocks of the first directions are kept in shared memory
+                       // (set by the launcher)
     int flow;          // 1: push mode exchanges each step's values by st.async into byte-counted
                        // barriers instead of cluster barriers (set by the launcher)
 };
