@@ -3,12 +3,11 @@
 //
 // The coarsest grid is small (256 sites x 24 dofs at 256^2) and its solve runs
 // ~10^3 Krylov steps per outer iteration, so a step is bound by latency, not
-// by bytes.  One cluster of up to 16 CTAs runs a whole solve: three hardware
-// cluster barriers per Arnoldi step (the last one split, with the least-squares
-// update between its arrive and wait), reductions through distributed shared
-// memory, and the small least-squares work done redundantly (and identically)
-// by every CTA, so no CTA ever waits for another one's scalar result.  Several
-// solves (one per stream) run side by side on different clusters.
+// by bytes.  One cluster of up to 16 CTAs runs a whole solve: reductions
+// through distributed shared memory, and the small least-squares work done
+// redundantly (and identically) by every CTA, so no CTA ever waits for another
+// one's scalar result.  Several solves (one per stream) run side by side on
+// different clusters.
 //
 // Work split: CTA b of the cluster owns sites [b*spc, (b+1)*spc) and their 24
 // dofs.  When it fits, the CTA keeps its rows of the Krylov basis in shared
@@ -21,15 +20,20 @@
 // tables are built once per launch.
 //
 // Per Arnoldi step j (CGS2, as in the rest of the library):
-//   w = A v_j; h1 = V^+ w: partials pushed to every CTA          [barrier]
-//   reduce h1; w -= V h1; h2 = V^+ w, n2 = ||w||^2: pushed        [barrier]
+//   w = A v_j; h1 = V^+ w: partials pushed to every CTA          [exchange]
+//   reduce h1; w -= V h1; h2 = V^+ w, n2 = ||w||^2: pushed        [exchange]
 //   reduce; h_{j+1,j} = sqrt(n2 - |h2|^2) (V orthonormal);
-//   v_{j+1} = (w - V h2) / h_{j+1,j}                              [arrive]
-//   warp 0: Givens update of the least squares, residual estimate [wait]
-// Reductions add the CTAs' partials in rank order with one fixed warp tree, so
-// every CTA holds bit-identical scalars and takes identical control decisions.
-// Partials are pushed into every CTA's shared memory (distributed shared-memory
-// stores) before the barrier, so each reduction after it reads local memory.
+//   v_{j+1} = (w - V h2) / h_{j+1,j}, pushed to the staging slots [exchange]
+//   Givens update of the least squares and the residual estimate
+// In push mode an exchange is dataflow: the values go by st.async into the
+// receivers' shared memory, counted in bytes on an mbarrier there, and an extra
+// least-squares warp runs the Givens update of step j during the apply of step
+// j + 1.  Otherwise an exchange is a hardware cluster barrier after plain
+// distributed shared-memory stores (the last one split, with warp 0's Givens
+// update between its arrive and wait).  Reductions add the CTAs' partials in
+// rank order with one fixed warp tree, so every CTA holds bit-identical scalars
+// and takes identical control decisions, and each reduction reads only local
+// shared memory.
 //
 // The small least squares runs in the precision of the vectors (FP32 in the
 // mixed-precision V-cycle, FP64 on the plain path).
@@ -297,8 +301,9 @@ __device__ __forceinline__ void accum_rows2(C2<T>& acc0, C2<T>& acc1, const C2<T
 }
 
 // Sum the pushed partials of all CTAs of the cluster in rank order (every CTA
-// gets the same result): red[i] = sum_r inbox[r][i], i < n.  Called after the
-// cluster barrier that follows the pushes.
+// gets the same result): red[i] = sum_r inbox[r][i], i < n.  Called once all
+// partials are in: after the cluster barrier, or the dataflow wait, that
+// follows the pushes.
 template <typename T>
 __device__ void reduce_inbox(const C2<T>* inbox, int nr, int n, C2<T>* red, int nw) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;

@@ -46,7 +46,7 @@ mg_status launch_coarse_proj(const CoopArgs<T>& a, cudaStream_t s);
 // The projected solves of two right-hand sides of one coarsest operator (same
 // A, deflation space and parameters; own f, x, r, V and counters) in one
 // cluster kernel, in lockstep: each block entry of A is loaded once for both
-// vectors and the two share the cluster barriers.  FP32 only.  *launched is
+// vectors and the two share each step's exchanges.  FP32 only.  *launched is
 // false (and nothing is enqueued) when the shape does not fit the kernel (both
 // basis slices in shared memory); the caller then launches the two one by one.
 mg_status launch_coarse_proj_pair(const CoopArgs<float>& a0, const CoopArgs<float>& a1, cudaStream_t s,
