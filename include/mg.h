@@ -104,6 +104,10 @@ typedef struct {
                               GMRES-Proj cluster kernels each Arnoldi step is an FP16 copy (each
                               part rounded once from FP64), multiplied in FP32; the deflation build
                               (GMRES-DR) keeps the FP64 operator.  0: the FP32 copy */
+    int coarse_dcgs2;      /* 1: the single-right-hand-side GMRES-Proj cluster kernel orthogonalises
+                              by delayed CGS2, one exchange per Arnoldi step instead of two (when
+                              its basis and staging sit in shared memory; the paired kernel keeps
+                              CGS2).  0 (default): CGS2 */
 } mg_params;
 
 /* solver of mg_solve (Section 2 compares both) */

@@ -33,6 +33,7 @@ class MGParams(ctypes.Structure):
         ("method", ctypes.c_int), ("parallel", ctypes.c_int), ("partial_tol", ctypes.c_double),
         ("coarse_tol_partial", ctypes.c_double), ("partial_max_iters", ctypes.c_int), ("pair_rhs", ctypes.c_int),
         ("vcycle_graph", ctypes.c_int), ("coarse_half", ctypes.c_int),
+        ("coarse_dcgs2", ctypes.c_int),
     ]
 
 

@@ -123,6 +123,7 @@ mg_status check_params(const mg_params& p) {
     if (p.pair_rhs != 0 && p.pair_rhs != 1) return set_error("pair_rhs must be 0 or 1"), MG_EINVAL;
     if (p.vcycle_graph != 0 && p.vcycle_graph != 1) return set_error("vcycle_graph must be 0 or 1"), MG_EINVAL;
     if (p.coarse_half != 0 && p.coarse_half != 1) return set_error("coarse_half must be 0 or 1"), MG_EINVAL;
+    if (p.coarse_dcgs2 != 0 && p.coarse_dcgs2 != 1) return set_error("coarse_dcgs2 must be 0 or 1"), MG_EINVAL;
     return MG_OK;
 }
 
@@ -552,6 +553,7 @@ mg_status mg_default_params(mg_params* p) {
     p->pair_rhs = 0;
     p->vcycle_graph = 1;
     p->coarse_half = 1;
+    p->coarse_dcgs2 = 0;
     return MG_OK;
 }
 

@@ -93,6 +93,8 @@ struct ClusterSmem {
     int ctl[8];
     unsigned long long mb[3];  // dataflow mode: arrivals of inbox[0], inbox[1] and xs
     int fault;                 // dataflow mode: a wait gave up
+    C2<T> zc[MSMAX + 1];       // delayed CGS2: coefficients of the u_{j+1} update
+    C2<T> hnext[MSMAX + 1];    // delayed CGS2: first projection of A q_j
 };
 
 // dynamic shared memory: ClusterSmem, then (optionally) the basis slice
@@ -360,6 +362,10 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
     }
     return false;
 }
+// barrier 1 over the first nthreads threads (the row warps)
+__device__ __forceinline__ void row_warps_sync(int nthreads) {
+    asm volatile("bar.sync 1, %0;\n" ::"r"(nthreads) : "memory");
+}
 __device__ __forceinline__ void st_async(unsigned dst, float2 v, unsigned bar) {
     asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];\n" ::"r"(dst),
                  "f"(v.x), "f"(v.y), "r"(bar)
@@ -607,6 +613,189 @@ __global__ void __maxnreg__(128) k_coarse_proj(CoopArgs<T> a) {
         }
         __syncwarp();
     };
+    // The same Givens update for a column jc of H that the row warps have already
+    // written in full (delayed CGS2), with subdiagonal hnv
+    auto ls_col = [&](int lane, int jc, T hnv) {
+        if (lane == 0) {
+            const Z* __restrict__ Hc = st.H + LD * jc;
+            Z* __restrict__ Rc = st.Rm + LD * jc;
+            const T* __restrict__ rcs = st.rc;
+            const Z* __restrict__ rss = st.rs;
+            Z p = Hc[0];
+#pragma unroll 8
+            for (int t = 0; t < jc; ++t) {
+                Z q = Hc[t + 1];
+                rot_<T>(rcs[t], rss[t], p, q);
+                Rc[t] = p;
+                p = q;
+            }
+            T cc;
+            Z ss, rr;
+            givens_real_<T>(p, hnv, cc, ss, rr);
+            Rc[jc] = rr;
+            st.rc[jc] = cc;
+            st.rs[jc] = ss;
+            rot_<T>(cc, ss, st.g[jc], st.g[jc + 1]);
+            const Z gn = st.g[jc + 1];
+            S.ctl[0] = ((double)(gn.x * gn.x + gn.y * gn.y) <= tol_abs * tol_abs) ? 1 : 0;
+            S.ctl[1] = (hnv == T(0)) ? 1 : 0;
+        }
+        __syncwarp();
+    };
+    // delayed CGS2 (a.dc, dataflow push mode only): one exchange per Arnoldi step
+    const bool dc = flow && a.lsw && a.dc;
+    // w = A v (push mode: v staged in xs) on the CTA's rows, then a CTA barrier
+    auto dc_apply = [&](Z* out) {
+        for (int e = tid; e < nrows; e += nt) {
+            const int ls = e / NDOF, kk = e - ls * NDOF;
+            Z acc = mk<T>(0, 0);
+            if (a.Ah) {
+                const unsigned* Ab = a.Ah + (s0 + ls) * (5L * NDOF * NDOF) + kk;
+                if (a.ash) {
+                    const unsigned* As = Ash + ls * ASH_SITE_WORDS + kk;
+#pragma unroll
+                    for (int d = 0; d < 5; ++d) {
+#pragma unroll
+                        for (int l = 0; l < NDOF; ++l) {
+                            const Z av = d < ASH_DIRS ? half_bits<T>(As[(d * NDOF + l) * NDOF])
+                                                      : half_entry<T>(Ab + (d * NDOF + l) * NDOF);
+                            acc = cfma(av, S.xs[ls][d][l], acc);
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int d = 0; d < 5; ++d) {
+#pragma unroll
+                        for (int l = 0; l < NDOF; ++l)
+                            acc = cfma(half_entry<T>(Ab + (d * NDOF + l) * NDOF), S.xs[ls][d][l], acc);
+                    }
+                }
+            } else {
+                const Z* Ab = a.A + (s0 + ls) * (5L * NDOF * NDOF) + kk;
+#pragma unroll
+                for (int d = 0; d < 5; ++d) {
+#pragma unroll
+                    for (int l = 0; l < NDOF; ++l) acc = cfma(__ldg(Ab + (d * NDOF + l) * NDOF), S.xs[ls][d][l], acc);
+                }
+            }
+            out[e] = acc;
+        }
+        __syncthreads();
+    };
+    // One GMRES(ms) cycle with delayed CGS2 from v_0 (row 0, staged): step j applies
+    // A to u_j, the once-orthogonalised next vector, and one exchange gives
+    // a = Q_{j-1}^+ u_j, |u_j|^2, Q_{j-1}^+ w and u_j^+ w.  That finishes q_j
+    // (the second pass of step j - 1) and column j - 1 of H; A q_j then follows
+    // from the Arnoldi relation, A q_j = (w - Q_j H a) / rho, and its first
+    // projection gives u_{j+1}.  The least-squares warp updates column j - 1
+    // during the rest of step j; its stop flags are read at step j + 1's apply
+    // barrier.  The inboxes alternate by step (buffer reuse stays safe as in the
+    // two-exchange step).  Returns the number of finished columns.
+    auto dcgs2_cycle = [&]() -> int {
+        const int lane = tid & 31;
+        Z* const ib[2] = {&S.inbox[0][0][0], &S.inbox[1][0][0]};
+        const unsigned zb = (unsigned)sizeof(Z);
+        const unsigned stage_bytes = (unsigned)(my_sites * 5 * NDOF) * zb;
+        // step 0: w = A q_0, h = q_0^+ w, u_1 = w - q_0 h
+        {
+            Z* const w = Vl + ldv;
+            dc_apply(w);
+            if (tid == 0) mbar_arm(&S.mb[0], (unsigned)ncta * zb);
+            push_gram_flow<T>(Vl, ldv, 1, w, nrows, false, ib[0], &S.mb[0], ncta, rank, nwr);
+            if (!ls_warp) flow_wait(0);
+            reduce_inbox<T>(ib[0], ncta, 1, S.h1, nwr);
+            if (tid == 0) mbar_arm(&S.mb[2], stage_bytes);
+            for (int e = tid; e < nrows; e += nt) {
+                const Z v = accum_rows<T, true>(w[e], Vl, ldv, e, S.h1, 1);
+                w[e] = v;
+                push_row_flow<T>(S, e, v);
+            }
+        }
+        for (int j = 1; j < ms; ++j) {
+            Z* const u = Vl + (long)j * ldv;
+            Z* const wl = Vl + (long)(j + 1) * ldv;
+            if (!ls_warp) flow_wait(2);  // u_j staged from every neighbour
+            dc_apply(wl);
+            if (j >= 2 && (S.ctl[0] | S.ctl[1])) {  // column j - 2 ended the cycle
+                conv = S.ctl[0];
+                return j - 1;
+            }
+            const int b = j & 1;
+            if (tid == 0) mbar_arm(&S.mb[b], (unsigned)(ncta * (2 * j + 2)) * zb);
+            push_gram_flow<T>(Vl, ldv, j, u, nrows, true, ib[b], &S.mb[b], ncta, rank, nwr);
+            push_gram_flow<T>(Vl, ldv, j + 1, wl, nrows, false, ib[b] + (j + 1), &S.mb[b], ncta, rank, nwr);
+            if (!ls_warp) flow_wait(b);
+            reduce_inbox<T>(ib[b], ncta, 2 * j + 2, S.red, nwr);  // a | |u|^2 | Q^+ w | u^+ w
+            T aa = 0;
+            Z ab = mk<T>(0, 0);
+            for (int i = lane; i < j; i += 32) {
+                aa += S.red[i].x * S.red[i].x + S.red[i].y * S.red[i].y;
+                ab = cfmac(S.red[i], S.red[j + 1 + i], ab);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                aa += __shfl_xor_sync(0xffffffffu, aa, o);
+                ab.x += __shfl_xor_sync(0xffffffffu, ab.x, o);
+                ab.y += __shfl_xor_sync(0xffffffffu, ab.y, o);
+            }
+            const T rho = sqrt(fmax((T)S.red[j].x - aa, T(0)));
+            const T irho = rho > T(0) ? T(1) / rho : T(0);
+            for (int e = tid; e < nrows; e += nt) u[e] = cscale(accum_rows<T, true>(u[e], Vl, ldv, e, S.red, j), irho);
+            if (tid < j) st.H[tid + LD * (j - 1)] = cadd(S.h1[tid], S.red[tid]);
+            if (tid == j) st.H[j + LD * (j - 1)] = mk<T>(rho, 0);
+            __syncthreads();  // q_j and column j - 1 complete
+            if (ls_warp) {
+                ls_col(lane, j - 1, rho);
+            } else {
+                if (tid <= j) {
+                    Z y = mk<T>(0, 0);
+                    for (int l = (tid > 0 ? tid - 1 : 0); l < j; ++l) y = cfma(st.H[tid + LD * l], S.red[l], y);
+                    const Z qw = tid < j ? S.red[j + 1 + tid] : cscale(csub(S.red[2 * j + 1], ab), irho);
+                    const Z h = cscale(csub(qw, y), irho);
+                    S.hnext[tid] = h;
+                    S.zc[tid] = cadd(y, cscale(h, rho));
+                }
+                row_warps_sync(nwr * 32);
+                if (tid <= j) S.h1[tid] = S.hnext[tid];
+                if (tid == 0) mbar_arm(&S.mb[2], stage_bytes);
+                for (int e = tid; e < nrows; e += nt) {
+                    const Z v = cscale(accum_rows<T, true>(wl[e], Vl, ldv, e, S.zc, j + 1), irho);
+                    wl[e] = v;
+                    push_row_flow<T>(S, e, v);
+                }
+            }
+            ++iters;
+        }
+        // u_ms is staged, and no apply reads it
+        if (!ls_warp) flow_wait(2);
+        __syncthreads();  // the update of column ms - 2 is complete
+        if (ms >= 2 && (S.ctl[0] | S.ctl[1])) {
+            conv = S.ctl[0];
+            return ms - 1;
+        }
+        // the last second pass: q_ms and column ms - 1
+        const int b = ms & 1;
+        Z* const u = Vl + (long)ms * ldv;
+        if (tid == 0) mbar_arm(&S.mb[b], (unsigned)(ncta * (ms + 1)) * zb);
+        push_gram_flow<T>(Vl, ldv, ms, u, nrows, true, ib[b], &S.mb[b], ncta, rank, nwr);
+        if (!ls_warp) flow_wait(b);
+        reduce_inbox<T>(ib[b], ncta, ms + 1, S.red, nwr);
+        T aa = 0;
+        for (int i = lane; i < ms; i += 32) aa += S.red[i].x * S.red[i].x + S.red[i].y * S.red[i].y;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) aa += __shfl_xor_sync(0xffffffffu, aa, o);
+        const T rho = sqrt(fmax((T)S.red[ms].x - aa, T(0)));
+        const T irho = rho > T(0) ? T(1) / rho : T(0);
+        for (int e = tid; e < nrows; e += nt) u[e] = cscale(accum_rows<T, true>(u[e], Vl, ldv, e, S.red, ms), irho);
+        if (tid < ms) st.H[tid + LD * (ms - 1)] = cadd(S.h1[tid], S.red[tid]);
+        if (tid == ms) st.H[ms + LD * (ms - 1)] = mk<T>(rho, 0);
+        __syncthreads();
+        if (ls_warp) ls_col(lane, ms - 1, rho);
+        __syncthreads();
+        ++iters;
+        conv = S.ctl[0];
+        return ms;
+    };
     while (true) {
         // ---- projection onto the deflation space: d = argmin ||W^+ r - H_k d|| ----
         push_gram<T>(cluster, Wl, ldw, k + 1, rl, nrows, false, &S.inbox[1][0][0], nwr);
@@ -643,6 +832,7 @@ __global__ void __maxnreg__(128) k_coarse_proj(CoopArgs<T> a) {
                     st.g[i] = st.c[i];
                 }
                 S.scal[0] = (T)(1.0 / beta);
+                S.ctl[0] = S.ctl[1] = 0;
             }
         }
         // ---- one GMRES(ms) cycle from r ----
@@ -669,6 +859,9 @@ __global__ void __maxnreg__(128) k_coarse_proj(CoopArgs<T> a) {
         }
         cluster.sync();  // v_0 complete in every CTA
         int j = 0, stop = 0;
+        if (dc) {
+            j = dcgs2_cycle();
+        } else {
         for (; j < ms && !stop; ++j) {
             const Z* vj = a.V + (long)j * n;
             Z* wl = Vl + (long)(j + 1) * ldv;
@@ -802,6 +995,7 @@ __global__ void __maxnreg__(128) k_coarse_proj(CoopArgs<T> a) {
             if (flow && !ls_warp) flow_wait(2);  // the staging of v_ms, which no apply reads
             __syncthreads();
             conv = S.ctl[0];
+        }
         }
         // ---- finish the cycle: d = R^{-1} g, rho = c - H d, x += V d, r = V rho ----
         const int jj = j;

@@ -36,6 +36,7 @@ struct CoopArgs {
     int lsw;           // 1: one extra warp runs the least-squares updates (set by the launcher)
     int ash;           // 1: the FP16 blocks of the first directions are kept in shared memory
                        // (set by the launcher)
+    int dc;            // 1: delayed CGS2, one exchange per Arnoldi step (dataflow push mode)
     int flow;          // 1: push mode exchanges each step's values by st.async into byte-counted
                        // barriers instead of cluster barriers (set by the launcher)
 };

@@ -307,6 +307,7 @@ CoopArgs<T> proj_args(Handle& H, const C2<T>* f, C2<T>* x) {
     a.part_ctas = H.cpart_ctas;
     a.out = H.cstats;
     a.Ah = std::is_same<T, float>::value ? H.A16c : nullptr;
+    a.dc = H.p.coarse_dcgs2;
     return a;
 }
 
