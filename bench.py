@@ -493,7 +493,7 @@ def run_native(args):
         for h in hsp:
             h.close()
 
-    # ---------- batching: 64 right-hand sides of one configuration (configs[2] shape) ----------
+    # ---------- batching: 64 right-hand sides of one 256^2 configuration ----------
     batching = None
     if not args.no_batching:
         batching = {"rhs": 64, "config": 0, "precision": "mixed"}

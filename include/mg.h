@@ -316,14 +316,14 @@ unsigned long long mg_kernel_launches(void);
  * application whose pool owns all of HBM, or a thread that must not let
  * cudaMalloc/cudaFree synchronise the device while other streams run).
  * Computes r = b - D(m0) x with the solver's FP64 residual kernel and
- *   norms[0] = ||b - D x||_2,  norms[1] = ||b||_2,
- * the quantities of the outer stopping test (Section 2).
+ *   norms[0] = ||b - D x||_2,  norms[1] = ||b||_2.
  *   gauge     device, complex128[L_t][L_x][2] (caller-owned, read only)
  *   b, x      device, complex128[L_t][L_x][2] (read only)
  *   r         device, complex128[L_t][L_x][2] (written; must not alias b or x)
  *   norms     host, double[2] (written; the call waits for `stream`)
- * No device memory is allocated: the reductions use a fixed 64 KB array in
- * the library's device image, which bounds the lattice to at most 2^20 sites
+ * All four device pointers must be memory of the current device (MG_EINVAL
+ * otherwise).  No device memory is allocated: the reductions use a fixed
+ * 32 800-byte array in the library's device image, which bounds the lattice to at most 2^20 sites
  * (1024 x 1024); larger lattices return MG_EINVAL.  The first call on each
  * device looks up that array's address, so it should come before any stream
  * capture begins on the device.  There is one such array per device: calls

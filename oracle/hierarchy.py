@@ -12,7 +12,7 @@ The paper builds each coarser grid as follows:
 5. Galerkin operator  A^ = P^+ A P;
 and then repeats 1-5 on A^ to build the coarsest operator.
 
-Readings where the paper is silent (each listed in the design doc):
+Readings where the paper is silent:
 * the near-null solver is CG on A A^+ (Hermitian positive definite), stopped on
   the recursive residual ||r|| <= tol ||A A^+ x||;
 * Gram-Schmidt is modified Gram-Schmidt in vector order, globally and locally;

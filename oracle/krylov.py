@@ -17,7 +17,7 @@ step is the plain definition  min_d ||c - H_j d||.
                      the deflation space alternating with GMRES(m-k) cycles
 * cgne             - CG on A A^+ y = b, x = A^+ y (the undeflated comparison)
 
-Readings (listed in the design doc): the GMRES-Proj cycle length is m - k; a
+Readings where the paper is silent: the GMRES-Proj cycle length is m - k; a
 GMRES-DR solve also ends after `stall` cycles without 0.1% progress or
 `max_cycles` cycles, and always exports the deflation space (V_{k+1}, H_k) of
 its last cycle (restarting that cycle once more when it ended early); the

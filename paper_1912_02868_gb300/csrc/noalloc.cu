@@ -38,7 +38,8 @@ constexpr int NA_MAX_DEVICES = 64;
 // [0, NA_MAX_BLOCKS): per-block (||r||^2, ||b||^2) partials, each written by
 // its block before it is read; [NA_MAX_BLOCKS]: the totals; the first word of
 // [NA_MAX_BLOCKS + 1]: the arrival counter of the blocks, which must be zero
-// when a launch starts (cleared by every call).  64 KB in all.
+// when a launch starts (cleared by every call).  (2048 + 2) x 16 bytes =
+// 32 800 bytes in all.
 static __device__ __align__(256) double2 na_scratch[NA_MAX_BLOCKS + 2];
 
 std::mutex na_mutex;
@@ -145,6 +146,8 @@ mg_status mg_wilson_residual_noalloc(const void* gauge, int L_x, int L_t, double
                   NA_MAX_SITES);
         return MG_EINVAL;
     }
+    int cur = 0;
+    MG_CUDA_TRY(cudaGetDevice(&cur));
     for (const void* p : {gauge, b, x, static_cast<const void*>(r)}) {
         cudaPointerAttributes a;
         if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -153,6 +156,9 @@ mg_status mg_wilson_residual_noalloc(const void* gauge, int L_x, int L_t, double
         }
         if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
             return set_error("gauge, b, x and r must be device pointers"), MG_EINVAL;
+        // the scratch address and the kernels belong to the current device
+        if (a.type == cudaMemoryTypeDevice && a.device != cur)
+            return set_error("gauge, b, x and r must be memory of the current device (%d)", cur), MG_EINVAL;
     }
     double2* scratch = nullptr;
     MG_TRY(scratch_of_current_device(&scratch));
