@@ -52,8 +52,13 @@ enum { MG_COARSE_DR_PROJ = 0, /* GMRES-DR(m,k) first, then GMRES-Proj(m,k) */
        MG_COARSE_CGNE = 1     /* CGNE to coarse_tol_rest at every outer iteration */ };
 
 /* arithmetic of the preconditioner; the outer FGMRES is always FP64 */
-enum { MG_FP64 = 0,    /* everything in FP64 */
-       MG_MIXED = 1    /* V-cycle in FP32; deflation space built in FP64 */ };
+enum { MG_FP64 = 0,        /* everything in FP64 */
+       MG_MIXED = 1,       /* V-cycle in FP32; deflation space built in FP64 */
+       MG_MIXED_BF16 = 2,  /* block solve: right-hand sides in lockstep blocks of rhs_block, V-cycle
+                              in FP32 with the intermediate and coarsest 24x24 block products on
+                              tensor cores (BF16 operator, FP32 vectors split into two BF16 parts,
+                              FP32 accumulation); deflation space built in FP64 */
+       MG_MIXED_FP16 = 3   /* the same with an FP16 operator */ };
 
 typedef struct {
     int levels;            /* grids in the hierarchy: 3 */
@@ -108,6 +113,12 @@ typedef struct {
                               by delayed CGS2, one exchange per Arnoldi step instead of two (when
                               its basis and staging sit in shared memory; the paired kernel keeps
                               CGS2).  0 (default): CGS2 */
+    int rhs_block;         /* MG_MIXED_BF16 / MG_MIXED_FP16: right-hand sides solved in lockstep per
+                              block, 1..64 (64).  Each has its own FGMRES(fgmres_m) in FP64 and
+                              converges on its own true residual; the V-cycle and the coarse
+                              GMRES-Proj solves of a block run batched (the first right-hand side
+                              of a handle builds the deflation space alone first).  The outer
+                              iteration limit max_outer is checked at restarts */
 } mg_params;
 
 /* solver of mg_solve (Section 2 compares both) */
@@ -193,8 +204,19 @@ const char* mg_last_error(void);
 /* ------------------------------------------------------------------------- */
 
 /* precision of the operator-level calls: the vectors are complex128 for
- * MG_F64 and complex64 for MG_F32 */
-enum { MG_F64 = 0, MG_F32 = 1 };
+ * MG_F64 and complex64 for MG_F32, MG_BF16 and MG_F16; MG_BF16 / MG_F16 are the
+ * tensor-core block products (BF16 / FP16 operator, FP32 vectors, FP32 accumulation) */
+enum { MG_F64 = 0, MG_F32 = 1, MG_BF16 = 2, MG_F16 = 3 };
+
+/*
+ * y_r = D^ x_r, r < nrhs, on grid `level` (1 or 2) with the tensor-core block
+ * stencil of the block solve (Section 2's Galerkin operator D^ = P^+ D P, 24x24
+ * complex blocks as real 48x48 products in mma.sync m16n8k16 tiles).
+ *   precision  MG_BF16 or MG_F16: the operator rounded once from FP64
+ *   nrhs       a multiple of 8 (eight right-hand sides share an MMA tile), <= 64
+ *   x, y       device, complex64[nrhs][n_level] (must not alias)
+ */
+mg_status mg_apply_block(mg_handle h, int level, int precision, int nrhs, const void* x, void* y, void* stream);
 
 /*
  * y = D x (dagger = 0) or y = D^+ x = sigma_3 D sigma_3 x (dagger = 1) on one
@@ -223,6 +245,62 @@ mg_status mg_prolong(mg_handle h, int level, int precision, const void* coarse, 
 mg_status mg_get_stencil(mg_handle h, int level, void* out);
 mg_status mg_get_prolongator(mg_handle h, int level, void* out);
 mg_status mg_get_deflation(mg_handle h, void* W, void* H, int* k_out);
+
+/*
+ * Replace the handle's coarse deflation space (Section 2: the space (V_{k+1}, H_k)
+ * that GMRES-DR leaves for the GMRES-Proj solves) with a given one:
+ *   W   host or device, complex128[k+1][n_2], orthonormal rows
+ *   H   host or device, complex128[k+1][k] (row-major), D^ W_k = W H
+ *   k   1 <= k <= dr_m
+ * Every later coarse solve of the handle (and of its solve contexts) is then a
+ * GMRES-Proj solve with this space.  Used to run the coarse solves of the
+ * library and of an independent implementation on the same space.
+ * Errors: MG_EINVAL (sizes, a solve context), MG_ECUDA.
+ */
+mg_status mg_set_deflation(mg_handle h, const void* W, const void* H, int k);
+
+/* flags of mg_coarse_solve */
+enum { MG_COARSE_PROBE_TIMEOUT = 1 };
+
+/* launch shape of the last mg_coarse_solve */
+typedef struct {
+    int ctas;            /* CTAs of the cluster */
+    int sites_per_cta;   /* coarse sites each CTA owns */
+    int dataflow;        /* 1: st.async / byte-counted mbarrier exchange in each Arnoldi step */
+    int dcgs2;           /* 1: delayed CGS2 ran (one exchange per step) */
+    int half_operator;   /* 1: the FP16 copy of the operator was streamed */
+    int shared_blocks;   /* 1: the FP16 blocks of three directions were held in shared memory */
+    int paired;          /* 1: the two-right-hand-side kernel */
+    long long cycles;    /* GMRES cycles of right-hand side 0 */
+    long long timeouts;  /* CTAs in which a bounded wait gave up */
+} mg_coarse_info;
+
+/*
+ * One projected solve of the coarsest system D^ x = b (Section 2: GMRES-Proj(m,k)
+ * with the handle's deflation space, from x = 0, until the least-squares
+ * residual estimate is <= tol ||b||), run by the same kernels, with the same
+ * launch shape, as the coarse solves inside the V-cycle.
+ *   precision  MG_F64: complex128 vectors and the FP64 operator; MG_F32:
+ *              complex64 vectors (the FP16 operator copy when coarse_half,
+ *              delayed CGS2 when coarse_dcgs2); MG_BF16 / MG_F16: the batched
+ *              GMRES-Proj of the block solve, complex64 vectors, tensor-core
+ *              applies (info reports ctas = 0)
+ *   nrhs       1, or 2 with MG_F32 (the two-right-hand-side kernel), or 1..64
+ *              with MG_BF16 / MG_F16
+ *   b, x       device, [nrhs][n_2] in that precision; x is output
+ *   flags      MG_COARSE_PROBE_TIMEOUT (tests): before the first cycle every CTA
+ *              waits, bounded by `spin`, on a barrier that nothing completes, so
+ *              the give-up path runs; the call then returns MG_ETIMEOUT and the
+ *              handle stays usable
+ *   spin       try_wait rounds before a bounded wait gives up (0: 2^20)
+ *   iters      host long long[nrhs] or NULL: Krylov steps per right-hand side
+ *   converged  host int[nrhs] or NULL
+ *   info       host or NULL: the launch shape
+ * Needs a deflation space (a first mg_solve, or mg_set_deflation).
+ * Errors: MG_EINVAL, MG_ECUDA, MG_ETIMEOUT (a bounded wait gave up).
+ */
+mg_status mg_coarse_solve(mg_handle h, int precision, int nrhs, const void* b, void* x, double tol, int flags,
+                          long long spin, void* stream, long long* iters, int* converged, mg_coarse_info* info);
 
 /* Grid sizes: sites per direction and dofs per site of `level`. */
 mg_status mg_level_shape(mg_handle h, int level, int* n_x, int* n_t, int* dof);
@@ -284,6 +362,12 @@ mg_status mg_server_submit(mg_server s, const mg_request* r, unsigned long long*
 /* Block until the request is done.  iters/relres: host [nrhs] or NULL;
  * latency_s: host or NULL, seconds from submission to completion. */
 mg_status mg_server_wait(mg_server s, unsigned long long ticket, int* iters, double* relres,
+                         double* latency_s);
+/* Non-blocking mg_server_wait: *done = 0 and MG_OK while the request is still
+ * running (the ticket stays valid); once it has finished, *done = 1, the
+ * outputs and the status are those of mg_server_wait, and the ticket is
+ * released. */
+mg_status mg_server_poll(mg_server s, unsigned long long ticket, int* done, int* iters, double* relres,
                          double* latency_s);
 mg_status mg_server_stats(mg_server s, mg_server_info* out);
 /* Stop the workers (queued items are dropped) and free every hierarchy. */

@@ -13,14 +13,16 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import (MG_COARSE_CGNE, MG_COARSE_DR_PROJ, MG_F32, MG_F64, MG_FP64, MG_MIXED, MG_OK,  # noqa: F401
+from ._lib import (MG_COARSE_CGNE, MG_COARSE_DR_PROJ, MG_F32, MG_F64, MG_BF16, MG_F16, MG_FP64, MG_MIXED,  # noqa: F401
+                   MG_MIXED_BF16, MG_MIXED_FP16, MG_OK,
                    MG_METHOD_MG, MG_METHOD_FINE_DEFLATION,
-                   MG_ENOTCONV, MGError, MGParams, MGSolveStats, load)
+                   MG_ENOTCONV, MG_ETIMEOUT, MG_COARSE_PROBE_TIMEOUT, MGError, MGParams, MGSolveStats, load)
 
 __all__ = ["build", "default_params", "mg_setup", "mg_setup_from_vectors", "mg_solve", "mg_destroy",
            "mg_reset_deflation", "mg_apply", "mg_restrict", "mg_prolong", "mg_get_stencil",
            "mg_get_prolongator", "mg_get_deflation", "mg_level_shape", "mg_wilson_apply", "mg_timing_enable",
-           "mg_timing_read", "mg_kernel_launches", "mg_wilson_residual_noalloc", "Handle"]
+           "mg_timing_read", "mg_kernel_launches", "mg_wilson_residual_noalloc", "mg_set_deflation",
+           "mg_coarse_solve", "mg_apply_block", "Handle"]
 
 
 def build(force: bool = False) -> str:
@@ -136,6 +138,12 @@ def mg_apply(h: Handle, level, x, y, dagger=False, precision=MG_F64, stream=None
                "mg_apply")
 
 
+def mg_apply_block(h: Handle, level, x, y, nrhs, precision=MG_BF16, stream=None):
+    """y[r] = D^ x[r] on grid 1 or 2 for nrhs (a multiple of 8) complex64 vectors, tensor cores."""
+    _lib.check(load().mg_apply_block(h.ptr, level, precision, nrhs, _ptr(x), _ptr(y), _stream(stream, x)),
+               "mg_apply_block")
+
+
 def mg_restrict(h: Handle, level, fine, coarse, precision=MG_F64, stream=None):
     _lib.check(load().mg_restrict(h.ptr, level, precision, _ptr(fine), _ptr(coarse), _stream(stream, fine)),
                "mg_restrict")
@@ -180,6 +188,25 @@ def mg_get_deflation(h: Handle):
     Hm = np.empty((k.value + 1, k.value), dtype=np.complex128)
     _lib.check(lib.mg_get_deflation(h.ptr, _ptr(W), _ptr(Hm), ctypes.byref(k)), "mg_get_deflation")
     return W, Hm
+
+
+def mg_set_deflation(h: Handle, W, Hm):
+    """Load a deflation space: W complex128[k+1][n2] rows, Hm complex128[k+1][k] (host or device)."""
+    k = int(Hm.shape[1])
+    _lib.check(load().mg_set_deflation(h.ptr, _ptr(W), _ptr(Hm), k), "mg_set_deflation")
+
+
+def mg_coarse_solve(h: Handle, b, x, tol, precision=MG_F64, nrhs=1, flags=0, spin=0, stream=None,
+                    allow=(MG_OK,)):
+    """One projected coarse solve (device b, x [nrhs][n2]).  Returns
+    (status, iters[nrhs], converged[nrhs], info dict)."""
+    iters = (ctypes.c_longlong * nrhs)()
+    conv = (ctypes.c_int * nrhs)()
+    info = _lib.MGCoarseInfo()
+    st = load().mg_coarse_solve(h.ptr, precision, nrhs, _ptr(b), _ptr(x), float(tol), int(flags), int(spin),
+                                _stream(stream, b, x), iters, conv, ctypes.byref(info))
+    _lib.check(st, "mg_coarse_solve", allow=allow)
+    return st, list(iters), [bool(c) for c in conv], {f: getattr(info, f) for f, _ in info._fields_}
 
 
 def mg_wilson_apply(gauge, Lx, Lt, m0, x, y, dagger=False, precision=MG_F64, stream=None):
@@ -238,6 +265,19 @@ class Server:
         st = load().mg_server_wait(self.ptr, int(ticket), it, rr, ctypes.byref(lat))
         self._keep.pop(ticket, None)
         _lib.check(st, "mg_server_wait", allow=(MG_OK, MG_ENOTCONV) if allow_notconv else (MG_OK,))
+        return st, list(it), list(rr), lat.value
+
+    def poll(self, ticket, nrhs, allow_notconv=False):
+        """None while the request runs; then (status, iters, relres, latency) as wait()."""
+        done = ctypes.c_int()
+        it = (ctypes.c_int * nrhs)()
+        rr = (ctypes.c_double * nrhs)()
+        lat = ctypes.c_double()
+        st = load().mg_server_poll(self.ptr, int(ticket), ctypes.byref(done), it, rr, ctypes.byref(lat))
+        if st == MG_OK and not done.value:
+            return None
+        self._keep.pop(ticket, None)
+        _lib.check(st, "mg_server_poll", allow=(MG_OK, MG_ENOTCONV) if allow_notconv else (MG_OK,))
         return st, list(it), list(rr), lat.value
 
     def stats(self) -> dict:

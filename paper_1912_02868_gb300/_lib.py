@@ -13,8 +13,8 @@ LIB_PATH = os.path.join(_HERE, "libmg.so")
 
 MG_OK, MG_EINVAL, MG_ENOMEM, MG_ECUDA, MG_ENOTCONV, MG_EBUDGET, MG_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 MG_COARSE_DR_PROJ, MG_COARSE_CGNE = 0, 1
-MG_FP64, MG_MIXED = 0, 1
-MG_F64, MG_F32 = 0, 1
+MG_FP64, MG_MIXED, MG_MIXED_BF16, MG_MIXED_FP16 = 0, 1, 2, 3
+MG_F64, MG_F32, MG_BF16, MG_F16 = 0, 1, 2, 3
 MG_METHOD_MG, MG_METHOD_FINE_DEFLATION = 0, 1
 
 STATUS_NAMES = {0: "MG_OK", -1: "MG_EINVAL", -2: "MG_ENOMEM", -3: "MG_ECUDA", -4: "MG_ENOTCONV",
@@ -33,7 +33,7 @@ class MGParams(ctypes.Structure):
         ("method", ctypes.c_int), ("parallel", ctypes.c_int), ("partial_tol", ctypes.c_double),
         ("coarse_tol_partial", ctypes.c_double), ("partial_max_iters", ctypes.c_int), ("pair_rhs", ctypes.c_int),
         ("vcycle_graph", ctypes.c_int), ("coarse_half", ctypes.c_int),
-        ("coarse_dcgs2", ctypes.c_int),
+        ("coarse_dcgs2", ctypes.c_int), ("rhs_block", ctypes.c_int),
     ]
 
 
@@ -59,6 +59,16 @@ class MGServerInfo(ctypes.Structure):
     ]
 
 
+class MGCoarseInfo(ctypes.Structure):
+    _fields_ = [
+        ("ctas", ctypes.c_int), ("sites_per_cta", ctypes.c_int), ("dataflow", ctypes.c_int), ("dcgs2", ctypes.c_int),
+        ("half_operator", ctypes.c_int), ("shared_blocks", ctypes.c_int), ("paired", ctypes.c_int),
+        ("cycles", ctypes.c_longlong), ("timeouts", ctypes.c_longlong),
+    ]
+
+
+MG_COARSE_PROBE_TIMEOUT = 1
+
 _lib = None
 
 # every symbol declared in include/mg.h
@@ -66,7 +76,8 @@ SYMBOLS = ("mg_default_params", "mg_setup", "mg_setup_from_vectors", "mg_solve",
            "mg_destroy", "mg_last_error", "mg_apply", "mg_restrict", "mg_prolong", "mg_get_stencil",
            "mg_get_prolongator", "mg_get_deflation", "mg_level_shape", "mg_wilson_apply",
            "mg_timing_enable", "mg_timing_read", "mg_kernel_launches", "mg_server_create", "mg_server_submit",
-           "mg_server_wait", "mg_server_stats", "mg_server_destroy", "mg_wilson_residual_noalloc")
+           "mg_server_wait", "mg_server_poll", "mg_server_stats", "mg_server_destroy", "mg_wilson_residual_noalloc",
+           "mg_set_deflation", "mg_coarse_solve", "mg_apply_block")
 
 
 def load(path: str | None = None) -> ctypes.CDLL:
@@ -101,7 +112,13 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "mg_server_create": (i, [ctypes.POINTER(MGParams), ctypes.c_ulonglong, i, ctypes.POINTER(vp)]),
         "mg_server_submit": (i, [vp, ctypes.POINTER(MGRequest), ctypes.POINTER(ctypes.c_ulonglong)]),
         "mg_server_wait": (i, [vp, ctypes.c_ulonglong, ctypes.POINTER(i), ctypes.POINTER(d), ctypes.POINTER(d)]),
+        "mg_server_poll": (i, [vp, ctypes.c_ulonglong, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(d),
+                               ctypes.POINTER(d)]),
         "mg_server_stats": (i, [vp, ctypes.POINTER(MGServerInfo)]),
+        "mg_set_deflation": (i, [vp, vp, vp, i]),
+        "mg_apply_block": (i, [vp, i, i, i, vp, vp, vp]),
+        "mg_coarse_solve": (i, [vp, i, i, vp, vp, d, i, ctypes.c_longlong, vp, ctypes.POINTER(ctypes.c_longlong),
+                                ctypes.POINTER(i), ctypes.POINTER(MGCoarseInfo)]),
         "mg_server_destroy": (i, [vp]),
         "mg_wilson_residual_noalloc": (i, [vp, i, i, d, vp, vp, vp, ctypes.POINTER(d), vp]),
     }

@@ -6,6 +6,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <memory>
 #include <thread>
 #include <vector>
 #include <algorithm>
@@ -68,6 +69,8 @@ void free_handle(Handle& H) {
     H.own_stream = nullptr;
     if (H.work_stream) cudaStreamDestroy(H.work_stream);
     H.work_stream = nullptr;
+    destroy_batch(H.bws);
+    H.bws = nullptr;
     if (H.vg.exec) cudaGraphExecDestroy(H.vg.exec);
     H.vg = VGraph{};
     if (H.cap_stream) cudaStreamDestroy(H.cap_stream);
@@ -107,8 +110,14 @@ mg_status check_params(const mg_params& p) {
         return set_error("tolerances must be in (0, 1)"), MG_EINVAL;
     if (p.coarse_solver != MG_COARSE_DR_PROJ && p.coarse_solver != MG_COARSE_CGNE)
         return set_error("unknown coarse_solver %d", p.coarse_solver), MG_EINVAL;
-    if (p.precision != MG_FP64 && p.precision != MG_MIXED)
+    if (p.precision != MG_FP64 && p.precision != MG_MIXED && p.precision != MG_MIXED_BF16 &&
+        p.precision != MG_MIXED_FP16)
         return set_error("unknown precision %d", p.precision), MG_EINVAL;
+    if (p.rhs_block < 1 || p.rhs_block > 64) return set_error("rhs_block must be in [1, 64]"), MG_EINVAL;
+    if ((p.precision == MG_MIXED_BF16 || p.precision == MG_MIXED_FP16) &&
+        (p.method != MG_METHOD_MG || p.coarse_solver != MG_COARSE_DR_PROJ || p.partial_tol > 0.0))
+        return set_error("the tensor-core block solve (precision %d) is built for the V-cycle with the deflated "
+                         "coarse solve", p.precision), MG_EINVAL;
     if (p.method != MG_METHOD_MG && p.method != MG_METHOD_FINE_DEFLATION)
         return set_error("unknown method %d", p.method), MG_EINVAL;
     if (p.dr_m - p.dr_k > MSMAX)
@@ -446,7 +455,7 @@ mg_status setup_common(const void* gauge, int Lx, int Lt, double m0, int nvec, i
         TRYF(halloc_t(H, &H.A64[l], (size_t)nx[l] * nt[l] * 5 * 576));
         TRYF(halloc_t(H, &H.A32[l], (size_t)nx[l] * nt[l] * 5 * 576));
     }
-    if (p.precision == MG_MIXED && p.coarse_half) TRYF(halloc_t(H, &H.A16c, (size_t)nx[2] * nt[2] * 5 * 576));
+    if (p.precision != MG_FP64 && p.coarse_half) TRYF(halloc_t(H, &H.A16c, (size_t)nx[2] * nt[2] * 5 * 576));
     for (int l = 0; l < 2; ++l) {
         const size_t q = (size_t)nx[l + 1] * nt[l + 1] * 24 * 16 * (dof[l] / 2);
         TRYF(halloc_t(H, &H.Q64[l], q));
@@ -554,6 +563,7 @@ mg_status mg_default_params(mg_params* p) {
     p->vcycle_graph = 1;
     p->coarse_half = 1;
     p->coarse_dcgs2 = 0;
+    p->rhs_block = 64;
     return MG_OK;
 }
 
@@ -619,7 +629,30 @@ mg_status mg_solve(mg_handle h, const void* b, void* x, int nrhs, double tol, vo
         if (r == MG_ENOTCONV) notconv = true;
         return r == MG_ENOTCONV ? MG_OK : r;
     };
-    if (par <= 1) {
+    // precision MG_MIXED_BF16 / MG_MIXED_FP16: lockstep blocks of rhs_block right-hand
+    // sides with tensor-core block products, after the first right-hand side of the
+    // handle has built the deflation space alone (FP32 path, FP64 GMRES-DR)
+    const bool block = (H.p.precision == MG_MIXED_BF16 || H.p.precision == MG_MIXED_FP16) && !H.is_context;
+    if (block) {
+        int first = 0;
+        if (!have_defl) {
+            MG_TRY(seq(0, std::min(nrhs, 1)));
+            first = 1;
+        }
+        for (int i0 = first; i0 < nrhs; i0 += H.p.rhs_block) {
+            const int nb = std::min(H.p.rhs_block, nrhs - i0);
+            std::vector<int> it(nb, 0);
+            std::vector<double> rr(nb, 0.0);
+            std::unique_ptr<bool[]> cv(new bool[nb]);
+            MG_TRY(fgmres_solve_block(H, B + (long)i0 * n0, X + (long)i0 * n0, nb, tol,
+                                      H.p.precision == MG_MIXED_FP16, s, it.data(), rr.data(), cv.get(), nullptr));
+            for (int r = 0; r < nb; ++r) {
+                if (iters) iters[i0 + r] = it[r];
+                if (relres) relres[i0 + r] = rr[r];
+                if (!cv[r]) notconv = true;
+            }
+        }
+    } else if (par <= 1) {
         MG_TRY(seq(0, nrhs));
     } else {
         // the first right-hand side builds the deflation space alone; the rest are

@@ -58,7 +58,7 @@ constexpr int MAX_SPC = 16;       // sites per apply chunk (staged neighbour row
 constexpr int MAX_NB_SITES = 64;  // sites per CTA in the neighbour table
 constexpr int MAX_CLUSTER = 16;    // CTAs of one cluster (non-portable size)
 constexpr size_t SMEM_LIMIT = 227 * 1024;
-constexpr long FLOW_SPIN = 1L << 20;  // try_wait rounds before a dataflow wait gives up
+constexpr long FLOW_SPIN = 1L << 20;  // default try_wait rounds before a dataflow wait gives up
 // FP16 operator (push mode): the blocks of directions 0..ASH_DIRS-1 of a CTA's
 // sites stay in its shared memory for the whole solve, the other directions
 // stream from L2 each step.  A site's part is padded by 24 words so that the two
@@ -91,8 +91,10 @@ struct ClusterSmem {
     Small<T> st;
     T scal[8];
     int ctl[8];
-    unsigned long long mb[3];  // dataflow mode: arrivals of inbox[0], inbox[1] and xs
+    unsigned long long mb[4];  // dataflow mode: arrivals of inbox[0], inbox[1] and xs; [3]: the
+                               // probe's barrier, which nothing completes
     int fault;                 // dataflow mode: a wait gave up
+    int fpub[2];               // fault as published at a cycle's first cluster barrier (by cycle parity)
     C2<T> zc[MSMAX + 1];       // delayed CGS2: coefficients of the u_{j+1} update
     C2<T> hnext[MSMAX + 1];    // delayed CGS2: first projection of A q_j
 };
@@ -348,9 +350,9 @@ __device__ __forceinline__ void mbar_arm(unsigned long long* bar, unsigned bytes
 }
 // bounded wait for the completion of the phase with this parity (acquiring the
 // cluster's st.async writes); false when it gave up
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, long spin) {
     const unsigned addr = smem_addr(bar);
-    for (long it = 0; it < FLOW_SPIN; ++it) {
+    for (long it = 0; it < spin; ++it) {
         unsigned ok;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
@@ -504,15 +506,27 @@ __global__ void __maxnreg__(128) k_coarse_proj(CoopArgs<T> a) {
     // received this CTA's contribution to a later exchange, which this CTA makes
     // after it has read the buffer.
     const bool flow = push && a.flow;
+    const long spin = a.spin > 0 ? a.spin : FLOW_SPIN;
     unsigned fph[3] = {0u, 0u, 0u};  // parity of the next phase of each barrier (row warps)
+    // A wait that gives up marks the CTA faulted.  From then on the CTA skips
+    // its waits and stops arming its barriers (a phase is never armed twice
+    // while incomplete; bytes that still arrive only lower the transaction
+    // count of a phase nobody waits for), and at the next cycle's first cluster
+    // barrier every CTA sees the fault and leaves the solve loop together.
     auto flow_wait = [&](int b) {
-        if (!S.fault && !mbar_wait(&S.mb[b], fph[b])) S.fault = 1;
+        if (!S.fault && !mbar_wait(&S.mb[b], fph[b], spin)) S.fault = 1;
         fph[b] ^= 1u;
     };
-    if (flow && tid == 0) {
-        for (int b = 0; b < 3; ++b) mbar_init(&S.mb[b], 1);
+    auto arm = [&](int b, unsigned bytes) {
+        if (tid == 0 && !S.fault) mbar_arm(&S.mb[b], bytes);
+    };
+    if (tid == 0) {
+        if (flow) {
+            for (int b = 0; b < 4; ++b) mbar_init(&S.mb[b], 1);
+            asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        }
         S.fault = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        S.fpub[0] = S.fpub[1] = 0;
     }
     if (push)
         for (int e = tid; e < my_sites * 5; e += nt) {
@@ -576,7 +590,10 @@ __global__ void __maxnreg__(128) k_coarse_proj(CoopArgs<T> a) {
     reduce_inbox<T>(&S.inbox[0][0][0], ncta, 1, S.red, nwr);
     const double nb = sqrt(fmax((double)S.red[0].x, 0.0));
     const double tol_abs = a.tol * nb;
-    int iters = 0, cycles = 0, conv = 0;
+    int iters = 0, cycles = 0, conv = 0, stop_next = 0;
+    // test probe: a bounded wait on a barrier that nothing completes
+    if (flow && a.probe && !ls_warp && !S.fault && !mbar_wait(&S.mb[3], 0u, spin)) S.fault = 1;
+    __syncthreads();
     // Least-squares update of step jc by one warp (lane = 0..31): column jc of H
     // (h1 + h2, h_{jc+1,jc}), the previous rotations applied to it, the new
     // rotation, and the stop flags from the residual estimate |g_{jc+1}|.  Reads
@@ -700,11 +717,11 @@ __global__ void __maxnreg__(128) k_coarse_proj(CoopArgs<T> a) {
         {
             Z* const w = Vl + ldv;
             dc_apply(w);
-            if (tid == 0) mbar_arm(&S.mb[0], (unsigned)ncta * zb);
+            arm(0, (unsigned)ncta * zb);
             push_gram_flow<T>(Vl, ldv, 1, w, nrows, false, ib[0], &S.mb[0], ncta, rank, nwr);
             if (!ls_warp) flow_wait(0);
             reduce_inbox<T>(ib[0], ncta, 1, S.h1, nwr);
-            if (tid == 0) mbar_arm(&S.mb[2], stage_bytes);
+            arm(2, stage_bytes);
             for (int e = tid; e < nrows; e += nt) {
                 const Z v = accum_rows<T, true>(w[e], Vl, ldv, e, S.h1, 1);
                 w[e] = v;
@@ -721,7 +738,7 @@ __global__ void __maxnreg__(128) k_coarse_proj(CoopArgs<T> a) {
                 return j - 1;
             }
             const int b = j & 1;
-            if (tid == 0) mbar_arm(&S.mb[b], (unsigned)(ncta * (2 * j + 2)) * zb);
+            arm(b, (unsigned)(ncta * (2 * j + 2)) * zb);
             push_gram_flow<T>(Vl, ldv, j, u, nrows, true, ib[b], &S.mb[b], ncta, rank, nwr);
             push_gram_flow<T>(Vl, ldv, j + 1, wl, nrows, false, ib[b] + (j + 1), &S.mb[b], ncta, rank, nwr);
             if (!ls_warp) flow_wait(b);
@@ -757,8 +774,8 @@ __global__ void __maxnreg__(128) k_coarse_proj(CoopArgs<T> a) {
                 }
                 row_warps_sync(nwr * 32);
                 if (tid <= j) S.h1[tid] = S.hnext[tid];
-                if (tid == 0) mbar_arm(&S.mb[2], stage_bytes);
-                for (int e = tid; e < nrows; e += nt) {
+                arm(2, stage_bytes);
+                for (int e = tid; e < nrows; e += nwr * 32) {  // row warps only
                     const Z v = cscale(accum_rows<T, true>(wl[e], Vl, ldv, e, S.zc, j + 1), irho);
                     wl[e] = v;
                     push_row_flow<T>(S, e, v);
@@ -776,7 +793,7 @@ __global__ void __maxnreg__(128) k_coarse_proj(CoopArgs<T> a) {
         // the last second pass: q_ms and column ms - 1
         const int b = ms & 1;
         Z* const u = Vl + (long)ms * ldv;
-        if (tid == 0) mbar_arm(&S.mb[b], (unsigned)(ncta * (ms + 1)) * zb);
+        arm(b, (unsigned)(ncta * (ms + 1)) * zb);
         push_gram_flow<T>(Vl, ldv, ms, u, nrows, true, ib[b], &S.mb[b], ncta, rank, nwr);
         if (!ls_warp) flow_wait(b);
         reduce_inbox<T>(ib[b], ncta, ms + 1, S.red, nwr);
@@ -798,8 +815,19 @@ __global__ void __maxnreg__(128) k_coarse_proj(CoopArgs<T> a) {
     };
     while (true) {
         // ---- projection onto the deflation space: d = argmin ||W^+ r - H_k d|| ----
+        if (tid == 0) S.fpub[cycles & 1] = S.fault;
         push_gram<T>(cluster, Wl, ldw, k + 1, rl, nrows, false, &S.inbox[1][0][0], nwr);
         cluster.sync();
+        // Leave together: a fault anywhere in the cluster (each CTA published its
+        // flag before this barrier, in the slot of this cycle's parity, which no
+        // CTA rewrites before the next barrier), or the previous cycle's stop,
+        // which every CTA took from identical data when none faulted.
+        if (flow) {
+            int anyf = 0;
+            for (int q = 0; q < ncta; ++q) anyf |= *cluster.map_shared_rank(&S.fpub[cycles & 1], q);
+            if (anyf) break;
+        }
+        if (stop_next) break;
         reduce_inbox<T>(&S.inbox[1][0][0], ncta, k + 1, S.red, nwr);
         for (int i = tid; i <= k; i += nt) {
             Z pdv = mk<T>(0, 0), puv = mk<T>(0, 0);
@@ -925,7 +953,7 @@ __global__ void __maxnreg__(128) k_coarse_proj(CoopArgs<T> a) {
                 if (S.ctl[0] | S.ctl[1]) break;  // step j is discarded: j columns
             }
             if (flow) {
-                if (tid == 0) mbar_arm(&S.mb[1], (unsigned)(ncta * (j + 1) * sizeof(Z)));
+                arm(1, (unsigned)(ncta * (j + 1) * sizeof(Z)));
                 push_gram_flow<T>(Vl, ldv, j + 1, wl, nrows, false, &S.inbox[1][0][0], &S.mb[1], ncta, rank, nwr);
                 if (!ls_warp) flow_wait(1);
             } else {
@@ -936,7 +964,7 @@ __global__ void __maxnreg__(128) k_coarse_proj(CoopArgs<T> a) {
             for (int e = tid; e < nrows; e += nt) wl[e] = accum_rows<T, true>(wl[e], Vl, ldv, e, S.h1, j + 1);
             __syncthreads();
             if (flow) {
-                if (tid == 0) mbar_arm(&S.mb[0], (unsigned)(ncta * (j + 2) * sizeof(Z)));
+                arm(0, (unsigned)(ncta * (j + 2) * sizeof(Z)));
                 push_gram_flow<T>(Vl, ldv, j + 1, wl, nrows, true, &S.inbox[0][0][0], &S.mb[0], ncta, rank, nwr);
                 if (!ls_warp) flow_wait(0);
             } else {
@@ -954,7 +982,7 @@ __global__ void __maxnreg__(128) k_coarse_proj(CoopArgs<T> a) {
             {
                 const T sc = hn > T(0) ? T(1) / hn : T(0);
                 Z* wg = a.V + (long)(j + 1) * n + r0;
-                if (flow && tid == 0) mbar_arm(&S.mb[2], (unsigned)(my_sites * 5 * NDOF * sizeof(Z)));
+                if (flow) arm(2, (unsigned)(my_sites * 5 * NDOF * sizeof(Z)));
                 for (int e = tid; e < nrows; e += nt) {
                     const Z v = cscale(accum_rows<T, true>(wl[e], Vl, ldv, e, S.red, j + 1), sc);
                     wl[e] = v;
@@ -1013,7 +1041,7 @@ __global__ void __maxnreg__(128) k_coarse_proj(CoopArgs<T> a) {
         }
         ++cycles;
         __syncthreads();
-        if (conv || cycles >= a.max_cycles) break;
+        stop_next = (conv || cycles >= a.max_cycles) ? 1 : 0;  // taken after the next cluster barrier
     }
     __syncthreads();
     if (flow && tid == 0 && S.fault) atomicAdd(reinterpret_cast<unsigned long long*>(&a.out->timeouts), 1ULL);
@@ -1022,6 +1050,13 @@ __global__ void __maxnreg__(128) k_coarse_proj(CoopArgs<T> a) {
         a.out->cycles += cycles;
         a.out->solves += 1;
         a.out->unconverged += conv ? 0 : 1;
+        a.out->ctas = ncta;
+        a.out->spc = a.spc;
+        a.out->flow = flow ? 1 : 0;
+        a.out->dc = dc ? 1 : 0;
+        a.out->ash = a.ash;
+        a.out->half = a.Ah ? 1 : 0;
+        a.out->paired = 0;
     }
     cluster.sync();  // no CTA leaves while others may still read its shared memory
 }
@@ -1047,6 +1082,7 @@ struct PairSmem {
     int ctl[2][8];
     unsigned long long mb[3];  // dataflow mode, as in ClusterSmem
     int fault;
+    int fpub[2];               // fault as published at a cycle's first cluster barrier, as in ClusterSmem
 };
 
 // push_gram for the two right-hand sides at once: warp task i forms product i
@@ -1194,15 +1230,23 @@ __global__ void __maxnreg__(128) k_coarse_proj_pair(CoopArgs<T> a0, CoopArgs<T> 
     // dataflow mode for the exchanges of each Arnoldi step, as in k_coarse_proj
     // (one barrier a phase for both right-hand sides: bytes of the active ones)
     const bool flow = a0.flow != 0;
+    const long spin = a0.spin > 0 ? a0.spin : FLOW_SPIN;
     unsigned fph[3] = {0u, 0u, 0u};
+    // a wait that gives up marks the CTA faulted, as in k_coarse_proj
     auto flow_wait = [&](int b) {
-        if (!S.fault && !mbar_wait(&S.mb[b], fph[b])) S.fault = 1;
+        if (!S.fault && !mbar_wait(&S.mb[b], fph[b], spin)) S.fault = 1;
         fph[b] ^= 1u;
     };
-    if (flow && tid == 0) {
-        for (int b = 0; b < 3; ++b) mbar_init(&S.mb[b], 1);
+    auto arm = [&](int b, unsigned bytes) {
+        if (tid == 0 && !S.fault) mbar_arm(&S.mb[b], bytes);
+    };
+    if (tid == 0) {
+        if (flow) {
+            for (int b = 0; b < 3; ++b) mbar_init(&S.mb[b], 1);
+            asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        }
         S.fault = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        S.fpub[0] = S.fpub[1] = 0;
     }
     // projection matrices M, N (shared deflation space), as in k_coarse_proj
     Z* Mp = Vb[1] + (long)(ms + 1) * rows_cap;
@@ -1246,11 +1290,22 @@ __global__ void __maxnreg__(128) k_coarse_proj_pair(CoopArgs<T> a0, CoopArgs<T> 
     double tol_abs[2];
     for (int b = 0; b < 2; ++b) tol_abs[b] = tol_rel[b] * sqrt(fmax((double)S.red[b][0].x, 0.0));
     int cycles = 0;
-    while (act[0] || act[1]) {
+    while (true) {
         // ---- projection onto the shared deflation space, per right-hand side ----
         const Z* const Wb[2] = {Wl, Wl};
+        if (tid == 0) S.fpub[cycles & 1] = S.fault;
         push_gram2<T>(Wb, ldw, k + 1, rlc, nrows, false, in1, act, ncta, rank, nw);
         cluster.sync();
+        // leave together on a fault anywhere in the cluster, as in k_coarse_proj;
+        // the stops of the previous cycle take effect here too
+        if (flow) {
+            int anyf = 0;
+            for (int q = 0; q < ncta; ++q) anyf |= *cluster.map_shared_rank(&S.fpub[cycles & 1], q);
+            if (anyf) break;
+        }
+        for (int b = 0; b < 2; ++b)
+            if (act[b] && (conv[b] || cycles >= a0.max_cycles)) act[b] = 0;
+        if (!act[0] && !act[1]) break;
         reduce_inbox2<T>(in1, ncta, k + 1, redp, act, nw);
         for (int t = tid; t < 2 * (k + 1); t += nt) {
             const int b = t / (k + 1), i = t - b * (k + 1);
@@ -1350,7 +1405,7 @@ __global__ void __maxnreg__(128) k_coarse_proj_pair(CoopArgs<T> a0, CoopArgs<T> 
             const Z* const Vc[2] = {Vb[0], Vb[1]};
             const Z* const wc[2] = {wl[0], wl[1]};
             if (flow) {
-                if (tid == 0) mbar_arm(&S.mb[1], (unsigned)(nact * ncta * (j + 1) * sizeof(Z)));
+                arm(1, (unsigned)(nact * ncta * (j + 1) * sizeof(Z)));
                 push_gram2<T>(Vc, ldv, j + 1, wc, nrows, false, in1, cact, ncta, rank, nw, &S.mb[1]);
                 flow_wait(1);
             } else {
@@ -1372,7 +1427,7 @@ __global__ void __maxnreg__(128) k_coarse_proj_pair(CoopArgs<T> a0, CoopArgs<T> 
             }
             __syncthreads();
             if (flow) {
-                if (tid == 0) mbar_arm(&S.mb[0], (unsigned)(nact * ncta * (j + 2) * sizeof(Z)));
+                arm(0, (unsigned)(nact * ncta * (j + 2) * sizeof(Z)));
                 push_gram2<T>(Vc, ldv, j + 1, wc, nrows, true, in0, cact, ncta, rank, nw, &S.mb[0]);
                 flow_wait(0);
             } else {
@@ -1394,7 +1449,7 @@ __global__ void __maxnreg__(128) k_coarse_proj_pair(CoopArgs<T> a0, CoopArgs<T> 
                 for (int b = 0; b < 2; ++b) hn[b] = sqrt(fmax((T)S.red[b][j + 1].x - h2[b], T(0)));
             }
             const T sc[2] = {hn[0] > T(0) ? T(1) / hn[0] : T(0), hn[1] > T(0) ? T(1) / hn[1] : T(0)};
-            if (flow && tid == 0) mbar_arm(&S.mb[2], (unsigned)(nact * my_sites * 5 * NDOF * sizeof(Z)));
+            if (flow) arm(2, (unsigned)(nact * my_sites * 5 * NDOF * sizeof(Z)));
             if (cact[0] && cact[1]) {
                 for (int rr = tid; rr < nrows; rr += nt) {
                     Z w0 = wl[0][rr], w1 = wl[1][rr];
@@ -1482,12 +1537,21 @@ __global__ void __maxnreg__(128) k_coarse_proj_pair(CoopArgs<T> a0, CoopArgs<T> 
         }
         ++cycles;
         __syncthreads();
-        for (int b = 0; b < 2; ++b)
-            if (act[b] && (conv[b] || cycles >= a0.max_cycles)) act[b] = 0;
     }
     __syncthreads();
     if (flow && tid == 0 && S.fault) atomicAdd(reinterpret_cast<unsigned long long*>(&a0.out->timeouts), 1ULL);
     if (rank == 0 && tid == 0) {
+        CoopStats* const outs[2] = {a0.out, a1.out};
+        for (int q = 0; q < 2; ++q) {
+            CoopStats* o = outs[q];
+            o->ctas = ncta;
+            o->spc = a0.spc;
+            o->flow = flow ? 1 : 0;
+            o->dc = 0;
+            o->ash = 0;
+            o->half = a0.Ah ? 1 : 0;
+            o->paired = 1;
+        }
         a0.out->iters += iters[0];
         a0.out->cycles += cycles;
         a0.out->solves += 1;

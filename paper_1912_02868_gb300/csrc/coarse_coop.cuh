@@ -11,6 +11,10 @@ constexpr int PSTR = 64;   // stride of one CTA's partial sums
 struct CoopStats {
     long long iters, cycles, solves, unconverged;
     long long timeouts;  // CTAs in which a bounded wait of the dataflow exchange gave up
+    // shape of the last launch (written by its CTA 0): cluster size, coarse
+    // sites per CTA, dataflow exchange, delayed CGS2, FP16 blocks in shared
+    // memory, FP16 operator stream, two-right-hand-side kernel
+    int ctas, spc, flow, dc, ash, half, paired, pad;
 };
 
 template <typename T>
@@ -39,6 +43,9 @@ struct CoopArgs {
     int dc;            // 1: delayed CGS2, one exchange per Arnoldi step (dataflow push mode)
     int flow;          // 1: push mode exchanges each step's values by st.async into byte-counted
                        // barriers instead of cluster barriers (set by the launcher)
+    long spin;         // try_wait rounds before a dataflow wait gives up (0: the default, 2^20)
+    int probe;         // 1 (tests): before the first cycle every row thread waits, bounded by
+                       // `spin`, on a barrier that nothing completes, so the give-up path runs
 };
 
 template <typename T>

@@ -56,10 +56,9 @@ __device__ __forceinline__ void rot_apply(double c, double2 s, double2& up, doub
     uq = csub(cscale(q, c), cmul(conj_(s), p));
 }
 
-__global__ void k_ks_start(KState* ks, const double* nrm2, double tol_rel, const double* nb2) {
-    if (threadIdx.x != 0) return;
-    const double beta = sqrt(fmax(*nrm2, 0.0));
-    const double tol_abs = tol_rel * sqrt(fmax(*nb2, 0.0));
+__device__ void ks_start_dev(KState* ks, double nrm2v, double tol_rel, double nb2v) {
+    const double beta = sqrt(fmax(nrm2v, 0.0));
+    const double tol_abs = tol_rel * sqrt(fmax(nb2v, 0.0));
     for (int i = 0; i < KLD; ++i) {
         ks->c[i] = z0();
         ks->g[i] = z0();
@@ -79,9 +78,22 @@ __global__ void k_ks_start(KState* ks, const double* nrm2, double tol_rel, const
     ks->scale = beta > 0.0 ? 1.0 / beta : 0.0;
     ks->scale_gate = 0;
 }
+__global__ void k_ks_start(KState* ks, const double* nrm2, double tol_rel, const double* nb2) {
+    if (threadIdx.x != 0) return;
+    ks_start_dev(ks, *nrm2, tol_rel, *nb2);
+}
+// right-hand side r of a batch: state ks[r], norms nrm2[r * ns] and nb2[r * nbs];
+// a closed gate starts the cycle as if from a zero vector (nothing to do)
+__global__ void k_bks_start(KState* ks, const double* nrm2, long ns, double tol_rel, const double* nb2, long nbs,
+                            Gate act) {
+    if (threadIdx.x != 0) return;
+    const int r = blockIdx.x;
+    const bool on = gate_open(act, r);
+    ks_start_dev(ks + r, on ? nrm2[r * ns] : 0.0, tol_rel, on ? nb2[r * nbs] : 0.0);
+}
 
-__global__ void k_ks_push(KState* ks, int jh) {
-    if (threadIdx.x != 0 || ks->step_gate != jh) return;
+__device__ void ks_push_dev(KState* ks, int jh) {
+    if (ks->step_gate != jh) return;
     const int j = jh;
     double2* Hc = ks->H + KLD * j;
     double2* Rc = ks->R + KLD * j;
@@ -118,6 +130,14 @@ __global__ void k_ks_push(KState* ks, int jh) {
     ks->scale_gate = (hn > 0.0) ? j + 1 : -1;
     ks->scale = (hn > 0.0) ? 1.0 / hn : 0.0;
 }
+__global__ void k_ks_push(KState* ks, int jh) {
+    if (threadIdx.x != 0) return;
+    ks_push_dev(ks, jh);
+}
+__global__ void k_bks_push(KState* ks, int jh) {
+    if (threadIdx.x != 0) return;
+    ks_push_dev(ks + blockIdx.x, jh);
+}
 
 // Back substitution R d = g over the first j columns, then rho = c - H d.
 // One warp.
@@ -144,7 +164,7 @@ __device__ void solve_upper(const double2* R, const double2* g, double2* d, int 
     }
 }
 
-__global__ void k_ks_finish(KState* ks) {
+__device__ void ks_finish_dev(KState* ks) {
     const int jj = ks->j;
     const int lane = threadIdx.x & 31;
     solve_upper(ks->R, ks->g, ks->d, jj, &ks->err);
@@ -161,6 +181,8 @@ __global__ void k_ks_finish(KState* ks) {
     for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
     if (lane == 0) ks->res = sqrt(part);
 }
+__global__ void k_ks_finish(KState* ks) { ks_finish_dev(ks); }
+__global__ void k_bks_finish(KState* ks) { ks_finish_dev(ks + blockIdx.x); }
 
 __global__ void k_ks_load_dense(KState* ks, const double2* Hk, const double2* ck, int k, double tol_abs) {
     const int lane = threadIdx.x & 31;
@@ -219,9 +241,8 @@ __global__ void k_ks_load_dense(KState* ks, const double2* Hk, const double2* ck
     }
 }
 
-__global__ void k_proj_solve(const KState* pls, const double2* cvec, double2* d, double2* u) {
-    __shared__ double2 g[KLD];
-    __shared__ double2 ds[KMAX];
+__device__ void proj_solve_dev(const KState* pls, const double2* cvec, double2* d, double2* u, double2* g,
+                               double2* ds) {
     const int lane = threadIdx.x & 31;
     const int k = pls->j;
     for (int i = lane; i < KLD; i += 32) g[i] = (i <= k) ? cvec[i] : z0();
@@ -237,6 +258,19 @@ __global__ void k_proj_solve(const KState* pls, const double2* cvec, double2* d,
         for (int l = 0; l < k; ++l) acc = cfma(pls->H[i + KLD * l], ds[l], acc);
         u[i] = acc;
     }
+}
+__global__ void k_proj_solve(const KState* pls, const double2* cvec, double2* d, double2* u) {
+    __shared__ double2 g[KLD];
+    __shared__ double2 ds[KMAX];
+    proj_solve_dev(pls, cvec, d, u, g, ds);
+}
+__global__ void k_bproj_solve(const KState* pls, const double2* cvec, long cs, double2* d, long dst, double2* u,
+                              long us, Gate act) {
+    __shared__ double2 g[KLD];
+    __shared__ double2 ds[KMAX];
+    const int r = blockIdx.x;
+    if (!gate_open(act, r)) return;
+    proj_solve_dev(pls, cvec + r * cs, d + r * dst, u + r * us, g, ds);
 }
 
 __global__ void k_set(double* out, double v) {
@@ -633,6 +667,24 @@ __global__ void __launch_bounds__(DR_THREADS) k_dr_restart(const KState* __restr
 
 void ks_start(KState* ks, const double* nrm2, double tol_rel, const double* nb2, cudaStream_t s) {
     k_ks_start<<<1, 32, 0, s>>>(ks, nrm2, tol_rel, nb2);
+    count_launch();
+}
+void bks_start(KState* ks, int nb, const double* nrm2, long ns, double tol_rel, const double* nb2, long nbs, Gate act,
+               cudaStream_t s) {
+    k_bks_start<<<nb, 32, 0, s>>>(ks, nrm2, ns, tol_rel, nb2, nbs, act);
+    count_launch();
+}
+void bks_push(KState* ks, int nb, int jh, cudaStream_t s) {
+    k_bks_push<<<nb, 32, 0, s>>>(ks, jh);
+    count_launch();
+}
+void bks_finish(KState* ks, int nb, cudaStream_t s) {
+    k_bks_finish<<<nb, 32, 0, s>>>(ks);
+    count_launch();
+}
+void bproj_solve(const KState* pls, int nb, const double2* cvec, long cs, double2* d, long ds, double2* u, long us,
+                 Gate act, cudaStream_t s) {
+    k_bproj_solve<<<nb, 32, 0, s>>>(pls, cvec, cs, d, ds, u, us, act);
     count_launch();
 }
 void scalar_set(double* out, double v, cudaStream_t s) {

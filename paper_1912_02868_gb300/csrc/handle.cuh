@@ -11,6 +11,9 @@ struct mg_handle_s;
 
 namespace mg {
 
+struct BatchWS;                  // workspaces of the lockstep block solve (solver_batch.cu)
+void destroy_batch(BatchWS* B);
+
 // CUDA-event timing of every operator apply on one grid (for roofline reports).
 struct ApplyTimer {
     bool on = false;
@@ -167,6 +170,7 @@ struct Handle {
     VGraph vg;
     std::vector<mg_handle_s*> contexts;
     size_t bytes = 0;                    // device bytes this handle allocated
+    BatchWS* bws = nullptr;              // block-solve workspaces (allocated by the first block solve)
 
     template <typename T> Level<T>* levels();
     template <typename T> CoarseWS<T>& coarse();
@@ -196,6 +200,16 @@ mg_status build_hierarchy(Handle& H, const double2* gauge_dev, const double2* st
                           const double2* nullvecs0, const double2* nullvecs1, cudaStream_t s);
 mg_status fine_deflated_solve(Handle& H, const double2* b, double2* x, double tol, cudaStream_t s, int* iters,
                               double* relres, bool* converged);
+// Lockstep FGMRES of nb <= 64 right-hand sides (host or device b, x: [nb][n0]) with
+// the batched V-cycle and tensor-core block products (solver_batch.cu); needs the
+// deflation space.  coarse_iters (optional): coarse GMRES-Proj steps of the block.
+mg_status fgmres_solve_block(Handle& H, const double2* B, double2* X, int nb, double tol, bool fp16, cudaStream_t s,
+                             int* iters, double* relres, bool* converged, long long* coarse_iters);
+// the batched coarse GMRES-Proj alone (device f, x: [nb][n2] complex64)
+mg_status coarse_solve_block(Handle& H, const float2* f, float2* x, int nb, double tol, bool fp16, cudaStream_t s,
+                             long long* iters);
+// the tensor-core block stencil of grid l alone (device x, y: [nb][n_l] complex64, nb % 8 == 0)
+mg_status apply_block(Handle& H, int l, const float2* x, float2* y, int nb, bool fp16, cudaStream_t s);
 // A solve context of `owner` (capi.cu): same hierarchy and deflation space,
 // own workspaces and stream; usable with mg_solve and released with mg_destroy
 // (before its owner).  The owner's deflation space must exist.

@@ -13,7 +13,7 @@ constexpr int KMAX = 48;          // largest Krylov dimension m (GMRES-DR(40,16)
 constexpr int KLD = KMAX + 1;     // leading dimension: column-major H[i + KLD * j]
 constexpr int NROT = KMAX * (KMAX + 1) / 2 + KMAX + 8;
 
-struct KState {
+struct alignas(16) KState {
     double2 H[KLD * KMAX];   // Arnoldi matrix as built (unrotated)
     double2 R[KLD * KMAX];   // rotated: upper triangular in columns < j
     double2 c[KLD];          // least-squares right-hand side (unrotated)
@@ -59,6 +59,21 @@ void ks_load_dense(KState* ks, const double2* Hk, const double2* ck, int k, doub
 // GMRES-Proj least squares with a prepared (ks_load_dense) state:
 // d = argmin ||cvec - H_k d||, u = H_k d.
 void proj_solve(const KState* pls, const double2* cvec, double2* d, double2* u, cudaStream_t s);
+// Batched forms over the states ks[0..nb): per right-hand side r the scalars
+// at nrm2[r * ns], nb2[r * nbs], cvec[r * cs], ...; bks_start starts a closed
+// gate's right-hand side as an empty cycle (converged, no steps).
+void bks_start(KState* ks, int nb, const double* nrm2, long ns, double tol_rel, const double* nb2, long nbs, Gate act,
+               cudaStream_t s);
+void bks_push(KState* ks, int nb, int jh, cudaStream_t s);
+void bks_finish(KState* ks, int nb, cudaStream_t s);
+void bproj_solve(const KState* pls, int nb, const double2* cvec, long cs, double2* d, long ds, double2* u, long us,
+                 Gate act, cudaStream_t s);
+// strides of KState fields across an array of states, in units of the field's type
+static_assert(sizeof(KState) % sizeof(double2) == 0, "KState arrays are strided in whole double2 units");
+constexpr long KS_INTS = (long)(sizeof(KState) / sizeof(int));
+constexpr long KS_DBLS = (long)(sizeof(KState) / sizeof(double));
+constexpr long KS_CPLX = (long)(sizeof(KState) / sizeof(double2));
+
 // GMRES-DR restart from the finished cycle in ks (harmonic Ritz vectors).
 mg_status dr_restart(const KState* ks, DRState* dr, int k, cudaStream_t s);
 // *out = 1 / sqrt(*in)

@@ -8,11 +8,18 @@ namespace mg {
 // A kernel with a gate runs only when ptr == nullptr or *ptr == val.  Krylov
 // cycles are enqueued whole; the gates make the steps after convergence no-ops
 // without a host round trip.
+//
+// Batched kernels (many right-hand sides in lockstep) read the gate of
+// right-hand side r at ptr[r * stride].
 struct Gate {
     const int* ptr = nullptr;
     int val = 0;
+    long stride = 0;
 };
 __device__ __forceinline__ bool gate_open(const Gate& g) { return g.ptr == nullptr || *g.ptr == g.val; }
+__device__ __forceinline__ bool gate_open(const Gate& g, int r) {
+    return g.ptr == nullptr || g.ptr[(long)r * g.stride] == g.val;
+}
 
 // Deterministic reductions: per-block partial sums, the last block to finish
 // adds them in block order.  One workspace per stream.

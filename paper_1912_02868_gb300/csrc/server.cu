@@ -379,6 +379,23 @@ mg_status mg_server_wait(mg_server sv, unsigned long long ticket, int* iters, do
     return R->status;
 }
 
+mg_status mg_server_poll(mg_server sv, unsigned long long ticket, int* done, int* iters, double* relres,
+                         double* latency_s) {
+    if (!sv || !done) return set_error("server or done is NULL"), MG_EINVAL;
+    Server& S = sv->s;
+    {
+        std::lock_guard<std::mutex> lk(S.mu);
+        auto f = S.reqs.find(ticket);
+        if (f == S.reqs.end()) return set_error("unknown ticket %llu", ticket), MG_EINVAL;
+        if (!f->second->done) {
+            *done = 0;
+            return MG_OK;
+        }
+    }
+    *done = 1;
+    return mg_server_wait(sv, ticket, iters, relres, latency_s);
+}
+
 mg_status mg_server_stats(mg_server sv, mg_server_info* out) {
     if (!sv || !out) return set_error("NULL argument"), MG_EINVAL;
     Server& S = sv->s;

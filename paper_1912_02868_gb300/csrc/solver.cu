@@ -546,7 +546,7 @@ mg_status fgmres_solve(Handle& H, const double2* b, double2* x, double tol, cuda
         return MG_OK;
     }
     MG_CUDA_TRY(cudaMemcpyAsync(H.fr, b, n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
-    const bool mixed = H.p.precision == MG_MIXED;
+    const bool mixed = H.p.precision != MG_FP64;
     int outer = 0;
     while (true) {
         launch_norm2<double>(r2, H.fr, n, H.red, Gate{}, s);

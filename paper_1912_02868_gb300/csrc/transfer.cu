@@ -7,7 +7,7 @@
 // (h = 1 on the fine grid, 12 on the intermediate grid).  Coarse dof k = 12c + j.
 //   restrict:  v^[B][k]           = sum_{l,a} conj(Q[B][c][j][l][a]) v[s(B,l)][c h + a]
 //   prolong:   v[s(B,l)][c h + a] = sum_j Q[B][c][j][l][a] v^[B][12 c + j]
-#include "ops.cuh"
+#include "batch.cuh"
 
 namespace mg {
 
@@ -19,10 +19,15 @@ constexpr int BS = BL * BL; // sites per block
 
 // one CTA per coarse site, one warp per coarse dof (strided), lanes over the
 // 16 h entries of that column of P.
+// blockIdx.y = right-hand side r of a batch (vectors at r * cr and r * fr, gate r)
 template <typename T>
 __global__ void __launch_bounds__(256) k_restrict(C2<T>* __restrict__ vc, const C2<T>* __restrict__ v,
-                                                  const C2<T>* __restrict__ Q, int NxF, int h, Gate g) {
-    if (!gate_open(g)) return;
+                                                  const C2<T>* __restrict__ Q, int NxF, int h, long cr, long fr,
+                                                  Gate g) {
+    const int rb = blockIdx.y;
+    if (!gate_open(g, rb)) return;
+    vc += rb * cr;
+    v += rb * fr;
     const int B = blockIdx.x;
     const int NxC = NxF / BL;
     const int bx = B % NxC, bt = B / NxC;
@@ -49,8 +54,11 @@ __global__ void __launch_bounds__(256) k_restrict(C2<T>* __restrict__ vc, const 
 template <typename T>
 __global__ void __launch_bounds__(256) k_prolong(C2<T>* __restrict__ v, const C2<T>* __restrict__ vc,
                                                  const C2<T>* __restrict__ Q, int NxF, int NtF, int h, int accumulate,
-                                                 Gate g) {
-    if (!gate_open(g)) return;
+                                                 long fr, long cr, Gate g) {
+    const int rb = blockIdx.y;
+    if (!gate_open(g, rb)) return;
+    v += rb * fr;
+    vc += rb * cr;
     const long nf = (long)NxF * NtF * 2 * h;
     const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nf) return;
@@ -71,19 +79,32 @@ __global__ void __launch_bounds__(256) k_prolong(C2<T>* __restrict__ v, const C2
 }  // namespace
 
 template <typename T>
+void launch_brestrict(C2<T>* coarse, long cr, const C2<T>* fine, long fr, const C2<T>* Q, int NxF, int NtF, int h,
+                      int nb, Gate g, cudaStream_t s) {
+    const int nc = (NxF / BL) * (NtF / BL);
+    k_restrict<T><<<dim3(nc, nb), 256, 0, s>>>(coarse, fine, Q, NxF, h, cr, fr, g);
+    count_launch();
+}
+
+template <typename T>
+void launch_bprolong(C2<T>* fine, long fr, const C2<T>* coarse, long cr, const C2<T>* Q, int NxF, int NtF, int h,
+                     bool accumulate, int nb, Gate g, cudaStream_t s) {
+    const long nf = (long)NxF * NtF * 2 * h;
+    k_prolong<T><<<dim3(nblocks(nf, 256), nb), 256, 0, s>>>(fine, coarse, Q, NxF, NtF, h, accumulate ? 1 : 0, fr, cr,
+                                                              g);
+    count_launch();
+}
+
+template <typename T>
 void launch_restrict(C2<T>* coarse, const C2<T>* fine, const C2<T>* Q, int NxF, int NtF, int h, Gate g,
                      cudaStream_t s) {
-    const int nc = (NxF / BL) * (NtF / BL);
-    k_restrict<T><<<nc, 256, 0, s>>>(coarse, fine, Q, NxF, h, g);
-    count_launch();
+    launch_brestrict<T>(coarse, 0, fine, 0, Q, NxF, NtF, h, 1, g, s);
 }
 
 template <typename T>
 void launch_prolong(C2<T>* fine, const C2<T>* coarse, const C2<T>* Q, int NxF, int NtF, int h, bool accumulate,
                     Gate g, cudaStream_t s) {
-    const long nf = (long)NxF * NtF * 2 * h;
-    k_prolong<T><<<nblocks(nf, 256), 256, 0, s>>>(fine, coarse, Q, NxF, NtF, h, accumulate ? 1 : 0, g);
-    count_launch();
+    launch_bprolong<T>(fine, 0, coarse, 0, Q, NxF, NtF, h, accumulate, 1, g, s);
 }
 
 template void launch_restrict<double>(C2<double>*, const C2<double>*, const C2<double>*, int, int, int, Gate,
@@ -94,5 +115,13 @@ template void launch_prolong<double>(C2<double>*, const C2<double>*, const C2<do
                                      cudaStream_t);
 template void launch_prolong<float>(C2<float>*, const C2<float>*, const C2<float>*, int, int, int, bool, Gate,
                                     cudaStream_t);
+template void launch_brestrict<double>(C2<double>*, long, const C2<double>*, long, const C2<double>*, int, int, int,
+                                       int, Gate, cudaStream_t);
+template void launch_brestrict<float>(C2<float>*, long, const C2<float>*, long, const C2<float>*, int, int, int, int,
+                                      Gate, cudaStream_t);
+template void launch_bprolong<double>(C2<double>*, long, const C2<double>*, long, const C2<double>*, int, int, int,
+                                      bool, int, Gate, cudaStream_t);
+template void launch_bprolong<float>(C2<float>*, long, const C2<float>*, long, const C2<float>*, int, int, int, bool,
+                                     int, Gate, cudaStream_t);
 
 }  // namespace mg

@@ -16,7 +16,7 @@
 // one 32-byte (FP64) or 16-byte (FP32) vector load each.  Neighbour spinors are
 // re-read by four threads and come from L1/L2; at 1024^2 the working set
 // (2 spinor fields + gauge) stays resident in the 129 MB L2 between applies.
-#include "ops.cuh"
+#include "batch.cuh"
 
 namespace mg {
 
@@ -33,11 +33,16 @@ __device__ __forceinline__ void load_site(const C2<T>* __restrict__ x, int s, C2
     p1 = DAG ? cneg(v.b) : v.b;
 }
 
+// blockIdx.y = right-hand side r of a batch: vectors at offset r * vr, gate r
 template <typename T, bool DAG, bool RES>
 __global__ void __launch_bounds__(256) k_wilson(C2<T>* __restrict__ y, const C2<T>* __restrict__ x,
                                                 const C2<T>* __restrict__ U, const C2<T>* __restrict__ b,
-                                                T diag, int Lx, int Lt, Gate g) {
-    if (!gate_open(g)) return;
+                                                T diag, int Lx, int Lt, long vr, Gate g) {
+    const int rb = blockIdx.y;
+    if (!gate_open(g, rb)) return;
+    y += rb * vr;
+    x += rb * vr;
+    if (RES) b += rb * vr;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= Lx * Lt) return;
     const int xx = s % Lx, t = s / Lx;
@@ -98,24 +103,40 @@ __global__ void __launch_bounds__(256) k_wilson(C2<T>* __restrict__ y, const C2<
 }  // namespace
 
 template <typename T>
-void launch_wilson(C2<T>* y, const C2<T>* x, const C2<T>* U, const C2<T>* b, double m0, int Lx, int Lt,
-                   bool dagger, Gate g, cudaStream_t s) {
+void wilson_grid(C2<T>* y, const C2<T>* x, const C2<T>* U, const C2<T>* b, double m0, int Lx, int Lt, bool dagger,
+                 long vr, int nb, Gate g, cudaStream_t s) {
     const int n = Lx * Lt;
-    const unsigned grid = nblocks(n, 256);
+    const dim3 grid(nblocks(n, 256), nb);
     const T diag = (T)(m0 + 2.0);
     if (dagger) {
-        if (b) k_wilson<T, true, true><<<grid, 256, 0, s>>>(y, x, U, b, diag, Lx, Lt, g);
-        else k_wilson<T, true, false><<<grid, 256, 0, s>>>(y, x, U, b, diag, Lx, Lt, g);
+        if (b) k_wilson<T, true, true><<<grid, 256, 0, s>>>(y, x, U, b, diag, Lx, Lt, vr, g);
+        else k_wilson<T, true, false><<<grid, 256, 0, s>>>(y, x, U, b, diag, Lx, Lt, vr, g);
     } else {
-        if (b) k_wilson<T, false, true><<<grid, 256, 0, s>>>(y, x, U, b, diag, Lx, Lt, g);
-        else k_wilson<T, false, false><<<grid, 256, 0, s>>>(y, x, U, b, diag, Lx, Lt, g);
+        if (b) k_wilson<T, false, true><<<grid, 256, 0, s>>>(y, x, U, b, diag, Lx, Lt, vr, g);
+        else k_wilson<T, false, false><<<grid, 256, 0, s>>>(y, x, U, b, diag, Lx, Lt, vr, g);
     }
     count_launch();
+}
+
+template <typename T>
+void launch_wilson(C2<T>* y, const C2<T>* x, const C2<T>* U, const C2<T>* b, double m0, int Lx, int Lt,
+                   bool dagger, Gate g, cudaStream_t s) {
+    wilson_grid<T>(y, x, U, b, m0, Lx, Lt, dagger, 0, 1, g, s);
+}
+
+template <typename T>
+void launch_bwilson(C2<T>* y, const C2<T>* x, const C2<T>* U, const C2<T>* b, double m0, int Lx, int Lt, long vr,
+                    int nb, Gate g, cudaStream_t s) {
+    wilson_grid<T>(y, x, U, b, m0, Lx, Lt, false, vr, nb, g, s);
 }
 
 template void launch_wilson<double>(C2<double>*, const C2<double>*, const C2<double>*, const C2<double>*, double,
                                     int, int, bool, Gate, cudaStream_t);
 template void launch_wilson<float>(C2<float>*, const C2<float>*, const C2<float>*, const C2<float>*, double, int,
                                    int, bool, Gate, cudaStream_t);
+template void launch_bwilson<double>(C2<double>*, const C2<double>*, const C2<double>*, const C2<double>*, double,
+                                     int, int, long, int, Gate, cudaStream_t);
+template void launch_bwilson<float>(C2<float>*, const C2<float>*, const C2<float>*, const C2<float>*, double, int,
+                                    int, long, int, Gate, cudaStream_t);
 
 }  // namespace mg
