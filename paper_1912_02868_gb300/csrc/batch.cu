@@ -274,15 +274,28 @@ __device__ __forceinline__ unsigned embed(unsigned w, int p) {
     return p ? __byte_perm(w, 0u, 0x1032) : (w ^ 0x80000000u);
 }
 
-__device__ __forceinline__ long nbr_of(long s, int d, int Nx, int Nt) {
-    const int xx = (int)(s % Nx), t = (int)(s / Nx);
+// neighbour site in direction d (self, +x, -x, +t, -t), periodic; 32-bit index
+// arithmetic (a coarse grid has far fewer than 2^31 sites)
+__device__ __forceinline__ int nbr_of(int s, int d, int Nx, int Nt) {
+    const int t = s / Nx, xx = s - t * Nx;
     switch (d) {
         case 0: return s;
         case 1: return (xx + 1 == Nx) ? s - xx : s + 1;
         case 2: return (xx == 0) ? s + Nx - 1 : s - 1;
-        case 3: return (t + 1 == Nt) ? (long)xx : s + Nx;
-        default: return (t == 0) ? s + (long)Nx * (Nt - 1) : s - Nx;
+        case 3: return (t + 1 == Nt) ? xx : s + Nx;
+        default: return (t == 0) ? s + Nx * (Nt - 1) : s - Nx;
     }
+}
+
+// FP64 -> BF16 rounded once to nearest-even: the FP64 significand is rounded at
+// BF16's 8 significant bits (bit 45 of the FP64 word is the last kept one), after
+// which the value converts to FP32 and to BF16 exactly (operator entries are far
+// inside BF16's exponent range)
+__device__ __forceinline__ unsigned short bf16_rn(double v) {
+    unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    u += 0x00000FFFFFFFFFFFull + ((u >> 45) & 1ull);
+    u &= 0xFFFFE00000000000ull;
+    return __bfloat16_as_ushort(__float2bfloat16_rn((float)__longlong_as_double((long long)u)));
 }
 
 // Fragment order of a tile (output rows 8 mt + a, input columns 8 kt + c):
@@ -305,8 +318,8 @@ __global__ void k_pack_frag(unsigned* out, const double2* __restrict__ A, long n
             re = __half_as_ushort(__double2half(v.x));
             im = __half_as_ushort(__double2half(v.y));
         } else {
-            re = __bfloat16_as_ushort(__double2bfloat16(v.x));
-            im = __bfloat16_as_ushort(__double2bfloat16(v.y));
+            re = bf16_rn(v.x);
+            im = bf16_rn(v.y);
         }
         out[w] = (im << 16) | re;
     }
@@ -321,11 +334,11 @@ __global__ void __launch_bounds__(256) k_bstencil_mma(float2* __restrict__ Y, co
                                                       Gate g) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gq = lane >> 2, t = lane & 3, p = gq & 1;
-    const long nsite = (long)Nx * Nt;
-    const long task = (long)blockIdx.x * (blockDim.x >> 5) + warp;
+    const int nsite = Nx * Nt;
+    const int task = blockIdx.x * (blockDim.x >> 5) + warp;
     if (task >= nsite * ntiles) return;
-    const long s = task / ntiles;
-    const int r0 = (int)(task - s * ntiles) * NB_TILE;
+    const int s = task / ntiles;
+    const int r0 = (task - s * ntiles) * NB_TILE;
     const bool mine = gate_open(g, r0 + gq);  // lane group gq: right-hand side r0 + gq
     if (!__any_sync(0xffffffffu, mine)) return;
     const float2* Xr = X + (long)(r0 + gq) * vr;
@@ -334,11 +347,11 @@ __global__ void __launch_bounds__(256) k_bstencil_mma(float2* __restrict__ Y, co
     for (int m = 0; m < 3; ++m)
 #pragma unroll
         for (int i = 0; i < 4; ++i) acc[m][i] = 0.f;
-    const uint4* A4 = reinterpret_cast<const uint4*>(Af) + s * (SITE_WORDS / 4) + (gq >> 1) * 4 + t;
+    const uint4* A4 = reinterpret_cast<const uint4*>(Af) + (long)s * (SITE_WORDS / 4) + (gq >> 1) * 4 + t;
 #pragma unroll 1
     for (int d = 0; d < 5; ++d) {
-        const long nb = nbr_of(s, d, Nx, Nt);
-        const float2* xn = Xr + nb * NDOF;
+        const int nb = nbr_of(s, d, Nx, Nt);
+        const float2* xn = Xr + (long)nb * NDOF;
 #pragma unroll
         for (int kt = 0; kt < 3; ++kt) {
             const float2 x0 = __ldg(xn + 8 * kt + t), x1 = __ldg(xn + 8 * kt + t + 4);
@@ -368,7 +381,7 @@ __global__ void __launch_bounds__(256) k_bstencil_mma(float2* __restrict__ Y, co
         for (int q = 0; q < 2; ++q) {
             const int r = r0 + 2 * t + q;
             if (!gate_open(g, r)) continue;
-            const long off = (long)r * vr + s * NDOF + row;
+            const long off = (long)r * vr + (long)s * NDOF + row;
             float2 o = v[q];
             if (RES) {
                 const float2 bb = __ldg(B + off);

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "batch.cuh"
+#include "coarse_block.cuh"
 #include "handle.cuh"
 
 namespace mg {
@@ -40,21 +41,25 @@ __global__ void k_gate_to_flags(int* flags, Gate g, int nb) {
 
 // after a coarse GMRES-Proj cycle: iterations, and right-hand side r stays
 // active while its cycle did not converge and the cycle limit is not reached;
-// *count = right-hand sides still active
-__global__ void k_coarse_cycle_end(int* cact, long long* citers, const KState* cks, int nb, int cycles_done,
+// *count = right-hand sides still active; *cycles counts the cycles run
+__global__ void k_coarse_cycle_end(int* cact, long long* citers, const KState* cks, int nb, int* cycles,
                                    int max_cycles, int* count) {
     __shared__ int cnt;
     if (threadIdx.x == 0) cnt = 0;
     __syncthreads();
+    const int done = *cycles + 1;
     for (int r = threadIdx.x; r < nb; r += blockDim.x) {
         if (!cact[r]) continue;
         citers[r] += cks[r].j;
-        const int on = (!cks[r].conv && cycles_done < max_cycles) ? 1 : 0;
+        const int on = (!cks[r].conv && done < max_cycles) ? 1 : 0;
         cact[r] = on;
         if (on) atomicAdd(&cnt, 1);
     }
     __syncthreads();
-    if (threadIdx.x == 0) *count = cnt;
+    if (threadIdx.x == 0) {
+        *count = cnt;
+        *cycles = done;
+    }
 }
 
 }  // namespace
@@ -77,6 +82,21 @@ struct BatchWS {
     int* cact = nullptr;
     long long* citers = nullptr;
     int* count = nullptr;
+    int* ccycles = nullptr;      // coarse cycles run by the current solve
+    int* cgb = nullptr;          // [2][nbp] coarse step gates by step parity
+    float2 *cp1 = nullptr, *cp2 = nullptr;  // fused-step partial sums
+    float2 *ch1 = nullptr, *ch2 = nullptr;  // fused-step reduced products
+    unsigned* ctk = nullptr;                // fused-step tickets
+    unsigned* cbar = nullptr;               // tile barriers of the cycle kernel
+    bool no_coop = false;                   // the cycle kernel could not be captured: use the step kernels
+    long cp_cap = 0;             // entries of cp1 / cp2
+    // the captured coarse cycle: graph, its key, and its kernel count
+    cudaGraphExec_t cyc_exec = nullptr;
+    int cyc_nb = 0, cyc_k = 0, cyc_fp16 = -1, cyc_coop = -1;
+    double cyc_tol = 0.0;
+    unsigned long long cyc_kernels = 0;
+    cudaStream_t cap = nullptr;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
     int* oflags = nullptr;       // [nbp] right-hand sides of the block still solving (host-set)
     int* gates = nullptr;        // [nbp] gathered step gates
     double* sc = nullptr;
@@ -86,6 +106,10 @@ struct BatchWS {
 
 void destroy_batch(BatchWS* B) {
     if (!B) return;
+    if (B->cyc_exec) cudaGraphExecDestroy(B->cyc_exec);
+    if (B->cap) cudaStreamDestroy(B->cap);
+    for (cudaEvent_t e : B->ev)
+        if (e) cudaEventDestroy(e);
     if (B->pin) cudaFreeHost(B->pin);
     delete B;
 }
@@ -139,7 +163,23 @@ mg_status batch_alloc(Handle& H, int nbp, bool fp16, cudaStream_t s) {
     MG_TRY(halloc_t(H, &B.cu, (size_t)nbp * KLD));
     MG_TRY(halloc_t(H, &B.cact, (size_t)nbp));
     MG_TRY(halloc_t(H, &B.citers, (size_t)nbp));
-    MG_TRY(halloc_t(H, &B.count, 1));
+    MG_TRY(halloc_t(H, &B.count, 2));  // [0] right-hand sides still active, [1] a tile barrier gave up
+    MG_CUDA_TRY(cudaMemsetAsync(B.count, 0, 2 * sizeof(int), s));
+    MG_TRY(halloc_t(H, &B.ccycles, 1));
+    MG_TRY(halloc_t(H, &B.cgb, (size_t)2 * nbp));
+    {
+        CBArgs g{};
+        cb_geometry(g, (long)H.L64[2].Nx * H.L64[2].Nt, nbp);
+        B.cp_cap = (long)nbp * CB_PB * CB_MAXCH;
+        MG_TRY(halloc_t(H, &B.cp1, (size_t)B.cp_cap));
+        MG_TRY(halloc_t(H, &B.cp2, (size_t)B.cp_cap));
+        MG_TRY(halloc_t(H, &B.ch1, (size_t)nbp * CB_PB));
+        MG_TRY(halloc_t(H, &B.ch2, (size_t)nbp * CB_PB));
+        MG_TRY(halloc_t(H, &B.ctk, (size_t)2 * NB_MAX / NB_TILE));
+        MG_CUDA_TRY(cudaMemsetAsync(B.ctk, 0, 2 * NB_MAX / NB_TILE * sizeof(unsigned), s));
+        MG_TRY(halloc_t(H, &B.cbar, (size_t)2 * NB_MAX / NB_TILE));
+        MG_CUDA_TRY(cudaMemsetAsync(B.cbar, 0, 2 * NB_MAX / NB_TILE * sizeof(unsigned), s));
+    }
     MG_TRY(halloc_t(H, &B.oflags, (size_t)nbp));
     MG_TRY(halloc_t(H, &B.gates, (size_t)nbp));
     MG_TRY(halloc_t(H, &B.sc, (size_t)nbp * NSC));
@@ -230,7 +270,9 @@ mg_status bcoarse_proj(Handle& H, const float2* f, float2* x, int nb, Gate act, 
     const int ms = std::max(H.p.dr_m - k, 1);
     if (ms > MSMAX || k + 1 > RED_MAXD)
         return set_error("coarse block solve: unsupported (m - k, k) = (%d, %d)", ms, k), MG_EINVAL;
+    if (f != B.f2 || x != B.x2) return set_error("coarse block solve: unexpected buffers"), MG_EINVAL;
     const float2* W = H.c32.W;
+    const bool fp16 = B.fp16 == 1;
     k_gate_to_flags<<<(nb + 63) / 64, 64, 0, s>>>(B.cact, act, nb);
     count_launch();
     const Gate ca{B.cact, 1, 1};
@@ -239,33 +281,109 @@ mg_status bcoarse_proj(Handle& H, const float2* f, float2* x, int nb, Gate act, 
     launch_bnorm2<float>(cnb2, NSC, f, n, n, nb, B.red, ca, s);
     MG_CUDA_TRY(cudaMemsetAsync(x, 0, (size_t)nb * n * sizeof(float2), s));
     MG_CUDA_TRY(cudaMemcpyAsync(B.cr, f, (size_t)nb * n * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+    MG_CUDA_TRY(cudaMemsetAsync(B.ccycles, 0, sizeof(int), s));
     const long row = (long)nb * n;
-    int* hcount = static_cast<int*>(B.pin);
-    for (int cycles = 0;;) {
-        // d = argmin ||W^+ r - H_k d||; x += W_k d; r -= W H_k d
-        launch_bgram<float>(B.cg, KLD, W, n, 0, k + 1, nullptr, 0, B.cr, n, n, nb, B.red, ca, s);
-        bproj_solve(H.pls, nb, B.cg, KLD, B.cd, KLD, B.cu, KLD, ca, s);
-        launch_baxpy<float>(x, n, W, n, 0, k, nullptr, 0, B.cd, KLD, 1.0, false, n, nb, nullptr, 0, B.red, ca, s);
+    CBArgs cb{};
+    cb.Af = B.Af[2];
+    cb.Nx = H.L32[2].Nx;
+    cb.Nt = H.L32[2].Nt;
+    cb.n = n;
+    cb.V = B.cV;
+    cb.row = row;
+    cb.ks = B.cks;
+    cb.gbuf = B.cgb;
+    cb.p1 = B.cp1;
+    cb.p2 = B.cp2;
+    cb.h1 = B.ch1;
+    cb.h2 = B.ch2;
+    cb.ticket = B.ctk;
+    cb.bar = B.cbar;
+    // the cycle kernel when its grid can be resident at once, else the step kernels
+    const bool coop = !B.no_coop && cb_geometry_cycle(cb, (long)cb.Nx * cb.Nt, nb, fp16);
+    if (!coop) cb_geometry(cb, (long)cb.Nx * cb.Nt, nb);
+    constexpr long CB_SPIN = 1L << 18;  // polls of a tile barrier before it gives up
+    if ((long)nb * CB_PB * CB_MAXCH > B.cp_cap || cb.nchunks > CB_MAXCH || cb.spc > CB_MAXSPC)
+        return set_error("coarse block solve: %d coarse sites exceed the fused step's chunking", cb.Nx * cb.Nt), MG_EINVAL;
+    // one cycle: projection d = argmin ||W^+ r - H_k d||, x += W_k d, r -= W H_k d,
+    // then one GMRES(ms) cycle from r, x += V d, r = V rho; every kernel gated per
+    // right-hand side, so the same sequence serves every cycle
+    auto cycle = [&](cudaStream_t cs) {
+        launch_bgram<float>(B.cg, KLD, W, n, 0, k + 1, nullptr, 0, B.cr, n, n, nb, B.red, ca, cs);
+        bproj_solve(H.pls, nb, B.cg, KLD, B.cd, KLD, B.cu, KLD, ca, cs);
+        launch_baxpy<float>(x, n, W, n, 0, k, nullptr, 0, B.cd, KLD, 1.0, false, n, nb, nullptr, 0, B.red, ca, cs);
         launch_baxpy<float>(B.cr, n, W, n, 0, k + 1, nullptr, 0, B.cu, KLD, -1.0, false, n, nb, cr2, NSC, B.red, ca,
-                            s);
-        // one GMRES(ms) cycle from r (a right-hand side already within tol starts converged)
-        bks_start(B.cks, nb, cr2, NSC, tol, cnb2, NSC, ca, s);
-        launch_bscale<float>(B.cV, n, B.cr, n, MG_DEVF(B.cks, double, scale), KS_DBLS, n, nb, scale_gate(B.cks, 0), s);
-        for (int jh = 0; jh < ms; ++jh)
-            barnoldi_step<float>(
-                B, [&](float2* w, const float2* in, Gate g) { bapply_mma(H, 2, w, in, nullptr, nb, g, s); }, B.cV, n,
-                nb, B.cks, jh, s);
-        bks_finish(B.cks, nb, s);
+                            cs);
+        bks_start(B.cks, nb, cr2, NSC, tol, cnb2, NSC, ca, cs);
+        launch_cb_gate_init(cb, cs);
+        launch_bscale<float>(B.cV, n, B.cr, n, MG_DEVF(B.cks, double, scale), KS_DBLS, n, nb, scale_gate(B.cks, 0),
+                             cs);
+        if (coop) (void)launch_cb_cycle(cb, ms, fp16, CB_SPIN, B.count + 1, cs);
+        else
+            for (int jh = 0; jh < ms; ++jh) launch_cb_step(cb, jh, fp16, cs);
+        bks_finish(B.cks, nb, cs);
         launch_baxpy<float>(x, n, B.cV, row, n, 0, MG_DEVF(B.cks, int, j), KS_INTS, MG_DEVF(B.cks, double2, d),
-                            KS_CPLX, 1.0, false, n, nb, nullptr, 0, B.red, ca, s);
+                            KS_CPLX, 1.0, false, n, nb, nullptr, 0, B.red, ca, cs);
         launch_baxpy<float>(B.cr, n, B.cV, row, n, 1, MG_DEVF(B.cks, int, j), KS_INTS, MG_DEVF(B.cks, double2, rho),
-                            KS_CPLX, 1.0, true, n, nb, nullptr, 0, B.red, ca, s);
-        ++cycles;
-        k_coarse_cycle_end<<<1, 64, 0, s>>>(B.cact, B.citers, B.cks, nb, cycles, H.p.proj_max_cycles, B.count);
+                            KS_CPLX, 1.0, true, n, nb, nullptr, 0, B.red, ca, cs);
+        k_coarse_cycle_end<<<1, 64, 0, cs>>>(B.cact, B.citers, B.cks, nb, B.ccycles, H.p.proj_max_cycles, B.count);
         count_launch();
-        MG_CUDA_TRY(cudaMemcpyAsync(hcount, B.count, sizeof(int), cudaMemcpyDeviceToHost, s));
+    };
+    // the cycle as a CUDA graph, captured once per (block size, deflation size, tolerance, format)
+    if (!B.cyc_exec || B.cyc_nb != nb || B.cyc_k != k || B.cyc_tol != tol || B.cyc_fp16 != (fp16 ? 1 : 0) ||
+        B.cyc_coop != (coop ? 1 : 0)) {
+        if (B.cyc_exec) cudaGraphExecDestroy(B.cyc_exec);
+        B.cyc_exec = nullptr;
+        if (!B.cap) MG_CUDA_TRY(cudaStreamCreateWithFlags(&B.cap, cudaStreamNonBlocking));
+        const unsigned long long before = g_launches.load();
+        MG_CUDA_TRY(cudaStreamBeginCapture(B.cap, cudaStreamCaptureModeThreadLocal));
+        cycle(B.cap);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(B.cap, &g);
+        const unsigned long long kernels = g_launches.load() - before;
+        g_launches.fetch_sub(kernels);  // counted per replay instead
+        cudaGraphExec_t ex = nullptr;
+        const cudaError_t ie = (ce == cudaSuccess) ? cudaGraphInstantiate(&ex, g, 0) : ce;
+        if (g) cudaGraphDestroy(g);
+        if (ie != cudaSuccess) {
+            (void)cudaGetLastError();
+            if (coop) {  // capture the step kernels instead
+                B.no_coop = true;
+                return bcoarse_proj(H, f, x, nb, act, tol, s);
+            }
+            return set_error("coarse cycle graph: %s", cudaGetErrorString(ie)), MG_ECUDA;
+        }
+        B.cyc_exec = ex;
+        B.cyc_nb = nb;
+        B.cyc_k = k;
+        B.cyc_tol = tol;
+        B.cyc_fp16 = fp16 ? 1 : 0;
+        B.cyc_coop = coop ? 1 : 0;
+        B.cyc_kernels = kernels;
+    }
+    for (int i = 0; i < 2; ++i)
+        if (!B.ev[i]) MG_CUDA_TRY(cudaEventCreateWithFlags(&B.ev[i], cudaEventDisableTiming));
+    // cycles replay back to back; the host reads the active count of cycle c while
+    // cycle c + 1 runs (a cycle with every right-hand side stopped changes nothing)
+    int* hc = reinterpret_cast<int*>(static_cast<char*>(B.pin) + 40960);
+    auto launch_cycle = [&](int c) -> mg_status {
+        MG_CUDA_TRY(cudaGraphLaunch(B.cyc_exec, s));
+        count_launch(B.cyc_kernels);
+        MG_CUDA_TRY(cudaMemcpyAsync(hc + 2 * (c & 1), B.count, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        MG_CUDA_TRY(cudaEventRecord(B.ev[c & 1], s));
+        return MG_OK;
+    };
+    MG_TRY(launch_cycle(0));
+    bool gave_up = false;
+    for (int c = 0; c <= H.p.proj_max_cycles; ++c) {
+        MG_TRY(launch_cycle(c + 1));
+        MG_CUDA_TRY(cudaEventSynchronize(B.ev[c & 1]));
+        gave_up = gave_up || hc[2 * (c & 1) + 1] != 0;
+        if (hc[2 * (c & 1)] == 0 || gave_up) break;
+    }
+    if (gave_up) {
         MG_CUDA_TRY(cudaStreamSynchronize(s));
-        if (*hcount == 0) break;
+        MG_CUDA_TRY(cudaMemsetAsync(B.count + 1, 0, sizeof(int), s));
+        return set_error("coarse block solve: a tile barrier gave up"), MG_ETIMEOUT;
     }
     return MG_OK;
 }

@@ -9,10 +9,13 @@ through the C ABI.
   FP16) plus FP32 accumulation over 120 complex terms: max-norm <= 3e-5 (BF16)
   and 1e-5 (FP16) relative to the output's max.
 * Batched coarse GMRES-Proj (mg_coarse_solve with MG_BF16 / MG_F16): each
-  right-hand side against the oracle's GMRES-Proj on the same rounded operator
-  and the oracle's deflation space, at a tolerance FP32 reaches: Krylov step
-  counts within 5%, the true residual with the rounded operator <= 3 tol, the
-  solution within kappa * 4 tol; a ragged block (not a multiple of 8).
+  right-hand side against the oracle's GMRES-Proj (FP64) on the same rounded
+  operator and the oracle's deflation space: Krylov step counts within 2%, the
+  solutions within 1e-4 (the same algorithm in FP32 against FP64: measured
+  1e-6 to 2e-5), and the true residual with the rounded operator no worse than
+  the oracle's own (the projection step uses the deflation relation of the
+  exact operator, so both level off near the operator's rounding, 1e-3 for
+  FP16 and 1e-2 for BF16); a ragged block (not a multiple of 8).
 * Whole block solve (mg_solve): every right-hand side meets the true FP64
   residual 1e-8 recomputed with the oracle's operator; outer counts close to
   the FP32 path's; run to 1e-7 / kappa, the solution is within 1e-7 of a sparse
@@ -37,11 +40,12 @@ def mgmod(cuda_lib):
 
 
 def bf16(a):
-    """round each part of a complex array to BF16 (round to nearest even), as FP64"""
-    a32 = np.ascontiguousarray(a, dtype=np.float32)
-    u = a32.view(np.uint32).astype(np.uint64)
-    u = ((u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
-    return u.view(np.float32).astype(np.float64)
+    """a real FP64 array rounded once to BF16 (8 significant bits, round to nearest
+    even on the FP64 significand), returned as FP64"""
+    u = np.ascontiguousarray(a, dtype=np.float64).view(np.uint64).copy()
+    u += np.uint64(0x00000FFFFFFFFFFF) + ((u >> np.uint64(45)) & np.uint64(1))
+    u &= np.uint64(0xFFFFE00000000000)
+    return u.view(np.float64)
 
 
 def round16(A, fp16):
@@ -80,6 +84,10 @@ def test_block_stencil_parity(mgmod, L, level, nrhs, fp16):
         g.close()
 
 
+def _coarse_relres(A, x, b, shape):
+    return np.linalg.norm(dirac.stencil_apply(A, x.reshape(shape)).ravel() - b) / np.linalg.norm(b)
+
+
 def _kappa(A2):
     M = dirac.stencil_sparse(A2).tocsc()
     lu = spla.splu(M)
@@ -109,14 +117,14 @@ def test_block_coarse_solve_parity(mgmod, L, nrhs, fp16):
         Xg = host(X).astype(np.complex128)
         Ar = round16(h.A2, fp16)
         defl = oc.coarse_deflation(L)
-        kappa = _kappa(Ar)
         for r in range(nrhs):
             xo, io = krylov.gmres_proj(oc.coarse_op(h, Ar), Bc[r], defl, 30, tol)
             assert conv[r] and io.converged
-            assert abs(it[r] - io.iters) <= max(2, 0.05 * io.iters), (r, it[r], io.iters)
-            res = np.linalg.norm(dirac.stencil_apply(Ar, Xg[r].reshape(h.shapes[2])).ravel() - Bc[r])
-            assert res <= 3 * tol * np.linalg.norm(Bc[r])
-            assert rel2(Xg[r], xo) <= kappa * 4 * tol
+            assert abs(it[r] - io.iters) <= max(2, 0.02 * io.iters), (r, it[r], io.iters)
+            assert rel2(Xg[r], xo) <= 1e-4
+            res_g = _coarse_relres(Ar, Xg[r], Bc[r], h.shapes[2])
+            res_o = _coarse_relres(Ar, xo, Bc[r], h.shapes[2])
+            assert res_g <= 1.5 * res_o + tol, (res_g, res_o)
     finally:
         g.close()
 

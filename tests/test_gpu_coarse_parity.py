@@ -16,7 +16,10 @@ oracle's GMRES-DR space, loaded with mg_set_deflation):
   (at least 2 steps), both meet the tolerance on the true residual computed with
   the oracle's operator, and the solutions differ by at most kappa * 2 tol;
 * FP32 with the FP16 operator copy (the mixed path's kernel): against the oracle
-  run in FP64 on the same FP16-rounded operator, at a tolerance FP32 reaches;
+  run in FP64 on the same FP16-rounded operator: step counts within 2%, the
+  solutions within 1e-4 (measured 1e-6), and a true residual with the rounded
+  operator no worse than the oracle's own (the projection uses the deflation
+  relation of the exact operator, so both level off near 1e-3);
 * delayed CGS2 and the two-right-hand-side kernel: the launch shape they report
   shows that the path ran, and the results meet the same checks;
 * a bounded wait that gives up (a probe barrier that nothing completes) makes
@@ -105,7 +108,7 @@ def test_coarse_fp32_half_operator_parity(mgmod, L):
     g, h, defl = _handle(mgmod, L, precision=mgmod.MG_MIXED)
     try:
         n2 = h.size(2)
-        tol = 1e-5  # the FP32 Krylov recurrence reaches it; its true residual levels off near 1e-6
+        tol = 1e-5
         A16 = oc.fp16(h.A2)
         b = synth.complex_gaussian((n2,), 8200 + L, 0)
         x = torch.zeros(n2, dtype=torch.complex64, device="cuda")
@@ -117,9 +120,9 @@ def test_coarse_fp32_half_operator_parity(mgmod, L):
         assert (info["ctas"], info["sites_per_cta"]) == EXPECT_SHAPE[L]
         if L == 256:
             assert info["shared_blocks"] == 1
-        assert abs(it[0] - io.iters) <= max(2, 0.05 * io.iters), (it[0], io.iters)
-        assert _relres(A16, xg, b, h.shapes[2]) <= 3 * tol
-        assert rel2(xg, xo) <= _kappa(A16) * 4 * tol
+        assert abs(it[0] - io.iters) <= max(2, 0.02 * io.iters), (it[0], io.iters)
+        assert rel2(xg, xo) <= 1e-4
+        assert _relres(A16, xg, b, h.shapes[2]) <= 1.5 * _relres(A16, xo, b, h.shapes[2]) + tol
     finally:
         g.close()
 
@@ -136,7 +139,8 @@ def test_coarse_dcgs2_path_runs(mgmod, L):
             x = torch.zeros(n2, dtype=torch.complex64, device="cuda")
             st, it, conv, info = mgmod.mg_coarse_solve(g, dev(b, torch.complex64), x, 1e-5, mgmod.MG_F32)
             assert info["dcgs2"] == dc and conv[0]
-            assert _relres(oc.fp16(h.A2), host(x).astype(np.complex128), b, h.shapes[2]) <= 3e-5
+            xo, io = krylov.gmres_proj(oc.coarse_op(h, oc.fp16(h.A2)), b, defl, 30, 1e-5)
+            assert rel2(host(x).astype(np.complex128), xo) <= 1e-4
             res[dc] = it[0]
         finally:
             g.close()
@@ -159,8 +163,9 @@ def test_coarse_pair_kernel(mgmod, L):
             x1 = torch.zeros(n2, dtype=torch.complex64, device="cuda")
             _, it1, _, _ = mgmod.mg_coarse_solve(g, dev(B[i], torch.complex64), x1, tol, mgmod.MG_F32)
             assert abs(it[i] - it1[0]) <= max(2, 0.02 * it1[0])
-            assert _relres(oc.fp16(h.A2), Xg[i].astype(np.complex128), B[i], h.shapes[2]) <= 3 * tol
-            assert rel2(Xg[i], host(x1)) <= 1e-3
+            xo, io = krylov.gmres_proj(oc.coarse_op(h, oc.fp16(h.A2)), B[i], defl, 30, tol)
+            assert rel2(Xg[i].astype(np.complex128), xo) <= 1e-4
+            assert rel2(Xg[i], host(x1)) <= 1e-4
     finally:
         g.close()
 
