@@ -36,6 +36,9 @@ constexpr int NDOF = 24;
 constexpr int TILE_WORDS = 64;
 constexpr int SITE_WORDS = 5 * 9 * TILE_WORDS;
 constexpr int MAXI = MSMAX + 1;  // basis vectors of a cycle
+#ifndef CB_APPLY_MT
+#define CB_APPLY_MT 3  // output tiles per apply task of the cycle kernel (1 or 3)
+#endif
 #ifndef CB_COOP_MINB
 #define CB_COOP_MINB 1  // resident cycle-kernel CTAs per SM the register budget is sized for
 #endif
@@ -151,6 +154,78 @@ struct CBSmem {
     WarpRed red[NB_TILE + 1];
 };
 
+// dynamic shared memory of the cycle kernel (CB_WPR warps per right-hand side)
+struct CBCycleSmem {
+    float2 ws[NB_TILE][CB_MAXSPC * NDOF];
+    float2 hs[NB_TILE * CB_WPR][MAXI];
+    float2 h1[NB_TILE][MAXI];      // chunk 0: first-pass products kept for the push
+    float hn[NB_TILE];
+    // chunk 0: the least squares of each right-hand side during the cycle (FP64):
+    // rotations, the rotated right-hand side, the tolerance, and a column
+    double rc[NB_TILE][MSMAX];
+    double2 rs[NB_TILE][MSMAX];
+    double2 g[NB_TILE][MSMAX + 1];
+    double2 col[NB_TILE][MAXI + 1];
+    double tol[NB_TILE];
+    WarpRed red[NB_TILE * CB_WPR];
+    uint4 abuf[NB_TILE * CB_WPR][SITE_WORDS / 4];  // each warp's staged operator tiles of one site
+};
+
+// Column jh of right-hand side r's least squares (the cycle kernel's push): the
+// column h1 + h2 with subdiagonal hn, rotated by the cycle's earlier rotations
+// (kept in shared memory, so no step waits on a dependent global load), a new
+// rotation, the rotated right-hand side, the residual estimate and the gates.
+// The state in global memory receives what the cycle's finish reads (H, R, g,
+// rotations, j, res, conv) without being read back.
+__device__ __forceinline__ void push_cycle(const CBArgs& a, CBCycleSmem& S, int l, int r, int jh, const float2* h2) {
+    KState* ks = a.ks + r;
+    double2* col = S.col[l];
+    for (int i = 0; i <= jh; ++i) col[i] = make_double2((double)S.h1[l][i].x + (double)h2[i].x,
+                                                        (double)S.h1[l][i].y + (double)h2[i].y);
+    const double hn = (double)S.hn[l];
+    col[jh + 1] = make_double2(hn, 0.0);
+    double2* Hc = ks->H + KLD * jh;
+    double2* Rc = ks->R + KLD * jh;
+    for (int i = 0; i <= jh + 1; ++i) Hc[i] = col[i];
+    for (int i = jh + 2; i < KLD; ++i) {
+        Hc[i] = make_double2(0.0, 0.0);
+        Rc[i] = make_double2(0.0, 0.0);
+    }
+    double2 p = col[0];
+    for (int t = 0; t < jh; ++t) {
+        double2 q = col[t + 1];
+        ksd::rot_apply(S.rc[l][t], S.rs[l][t], p, q);
+        Rc[t] = p;
+        p = q;
+    }
+    double cc;
+    double2 ss, rr;
+    ksd::givens(p, col[jh + 1], cc, ss, rr);
+    Rc[jh] = rr;
+    Rc[jh + 1] = make_double2(0.0, 0.0);
+    S.rc[l][jh] = cc;
+    S.rs[l][jh] = ss;
+    ks->rc[jh] = cc;
+    ks->rs[jh] = ss;
+    ks->ra[jh] = (short)jh;
+    ks->rb[jh] = (short)(jh + 1);
+    ksd::rot_apply(cc, ss, S.g[l][jh], S.g[l][jh + 1]);
+    ks->g[jh] = S.g[l][jh];
+    ks->g[jh + 1] = S.g[l][jh + 1];
+    const double res = ksd::cabsd(S.g[l][jh + 1]);
+    const int conv = res <= S.tol[l] ? 1 : 0, brk = hn == 0.0 ? 1 : 0;
+    const int next = (conv || brk || jh + 1 >= KMAX) ? -1 : jh + 1;
+    ks->nrot = jh + 1;
+    ks->res = res;
+    ks->j = jh + 1;
+    ks->conv = conv;
+    ks->breakdown = brk;
+    ks->step_gate = next;
+    ks->scale_gate = hn > 0.0 ? jh + 1 : -1;
+    ks->scale = hn > 0.0 ? 1.0 / hn : 0.0;
+    a.gbuf[((jh + 1) & 1) * a.nbp + r] = next;
+}
+
 // slots 0..jh (and, with norm, slot CB_PB - 1) of right-hand side r summed over
 // the chunks: lanes over the chunks in a fixed order, then lane_sums.  Lane i
 // returns slot i's total (i <= jh); with norm, *nrm is the norm's total in every
@@ -186,44 +261,53 @@ __device__ __forceinline__ float2 chunk_totals(const float2* part, int nchunks, 
 // ---------------------------------------------------------------- phases ----
 
 // w = A v_jh on the chunk's sites for the tile's eight right-hand sides (into
-// ws and, for right-hand sides with an open gate, into V[jh+1]): one warp task
-// per (site, 8-row tile of the output); the next direction's operator tiles and
-// neighbour values load while this one multiplies.  nwarps warps take part.
-template <bool F16>
-__device__ __forceinline__ void phase_apply(const CBArgs& a, int jh, int r0, int s0, int ns, const int* gate,
+// ws and, for right-hand sides whose bit is set in `wmask`, into V[jh+1]).  One
+// warp task per (site, MT consecutive 8-row tiles of the output): MT = 3 covers
+// a site with one pass over its neighbour values; the next direction's operator
+// tiles and neighbour values load while this one multiplies.  nwarps warps take
+// part.
+template <bool F16, int MT>
+__device__ __forceinline__ void phase_apply(const CBArgs& a, int jh, int r0, int s0, int ns, unsigned wmask,
                                             float2 (*ws)[CB_MAXSPC * NDOF], int nwarps) {
+    constexpr int NT = 3 / MT;  // tasks per site
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gq = lane >> 2, t = lane & 3, p = gq & 1;
     const float2* X = a.V + (long)jh * a.row;
     float2* Wt = a.V + (long)(jh + 1) * a.row;
-    for (int task = warp; task < ns * 3; task += nwarps) {
-        const int ls = task / 3, mt = task - 3 * ls;
+    for (int task = warp; task < ns * NT; task += nwarps) {
+        const int ls = task / NT, mt0 = (task - NT * ls) * MT;
         const int s = s0 + ls;
-        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        float acc[MT][4];
+#pragma unroll
+        for (int m = 0; m < MT; ++m)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[m][i] = 0.f;
         const uint4* A4 = reinterpret_cast<const uint4*>(a.Af) + (long)s * (SITE_WORDS / 4) + (gq >> 1) * 4 + t +
-                          mt * 3 * (TILE_WORDS / 4);
+                          mt0 * 3 * (TILE_WORDS / 4);
         const float2* Xr = X + (long)(r0 + gq) * a.n;
         float2 xv[3][2];
-        uint4 aw[3];
+        uint4 aw[MT][3];
         auto load = [&](int d) {
             const float2* xn = Xr + (long)nbr_of(s, d, a.Nx, a.Nt) * NDOF;
 #pragma unroll
             for (int kt = 0; kt < 3; ++kt) {
                 xv[kt][0] = __ldcg(xn + 8 * kt + t);
                 xv[kt][1] = __ldcg(xn + 8 * kt + t + 4);
-                aw[kt] = __ldg(A4 + (d * 9 + kt) * (TILE_WORDS / 4));
+#pragma unroll
+                for (int m = 0; m < MT; ++m) aw[m][kt] = __ldg(A4 + (d * 9 + m * 3 + kt) * (TILE_WORDS / 4));
             }
         };
         load(0);
 #pragma unroll 1
         for (int d = 0; d < 5; ++d) {
             float2 xc[3][2];
-            uint4 ac[3];
+            uint4 ac[MT][3];
 #pragma unroll
             for (int kt = 0; kt < 3; ++kt) {
                 xc[kt][0] = xv[kt][0];
                 xc[kt][1] = xv[kt][1];
-                ac[kt] = aw[kt];
+#pragma unroll
+                for (int m = 0; m < MT; ++m) ac[m][kt] = aw[m][kt];
             }
             if (d < 4) load(d + 1);
 #pragma unroll
@@ -232,55 +316,152 @@ __device__ __forceinline__ void phase_apply(const CBArgs& a, int jh, int r0, int
                 const unsigned h0 = pk<F16>(x0.x, x0.y), h1 = pk<F16>(x1.x, x1.y);
                 const float2 f0 = upk<F16>(h0), f1 = upk<F16>(h1);
                 const unsigned l0 = pk<F16>(x0.x - f0.x, x0.y - f0.y), l1 = pk<F16>(x1.x - f1.x, x1.y - f1.y);
-                const uint4 w = ac[kt];
-                const unsigned av[4] = {embed(w.x, p), embed(w.y, p), embed(w.z, p), embed(w.w, p)};
-                mma<F16>(acc, av, h0, h1);
-                mma<F16>(acc, av, l0, l1);
+#pragma unroll
+                for (int m = 0; m < MT; ++m) {
+                    const uint4 w = ac[m][kt];
+                    const unsigned av[4] = {embed(w.x, p), embed(w.y, p), embed(w.z, p), embed(w.w, p)};
+                    mma<F16>(acc[m], av, h0, h1);
+                    mma<F16>(acc[m], av, l0, l1);
+                }
             }
         }
         // lane (gq, t) holds component p of outputs gq / 2 and gq / 2 + 4 of
         // right-hand sides 2t, 2t + 1; lane ^ 4 holds the other component
-        const float s0v = p ? acc[0] : acc[2], s1v = p ? acc[1] : acc[3];
-        const float o0 = __shfl_xor_sync(0xffffffffu, s0v, 4), o1 = __shfl_xor_sync(0xffffffffu, s1v, 4);
-        const int row = 8 * mt + (gq >> 1) + (p ? 4 : 0);
-        const float2 v0 = p ? make_float2(o0, acc[2]) : make_float2(acc[0], o0);
-        const float2 v1 = p ? make_float2(o1, acc[3]) : make_float2(acc[1], o1);
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int rl = 2 * t + q;
-            const float2 v = q ? v1 : v0;
-            ws[rl][ls * NDOF + row] = v;
-            if (__ldcg(gate + r0 + rl) == jh) Wt[(long)(r0 + rl) * a.n + (long)s * NDOF + row] = v;
+        for (int m = 0; m < MT; ++m) {
+            const float s0v = p ? acc[m][0] : acc[m][2], s1v = p ? acc[m][1] : acc[m][3];
+            const float o0 = __shfl_xor_sync(0xffffffffu, s0v, 4), o1 = __shfl_xor_sync(0xffffffffu, s1v, 4);
+            const int row = 8 * (mt0 + m) + (gq >> 1) + (p ? 4 : 0);
+            const float2 v0 = p ? make_float2(o0, acc[m][2]) : make_float2(acc[m][0], o0);
+            const float2 v1 = p ? make_float2(o1, acc[m][3]) : make_float2(acc[m][1], o1);
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int rl = 2 * t + q;
+                const float2 v = q ? v1 : v0;
+                ws[rl][ls * NDOF + row] = v;
+                if ((wmask >> rl) & 1u) Wt[(long)(r0 + rl) * a.n + (long)s * NDOF + row] = v;
+            }
         }
     }
 }
 
+// The cycle kernel's apply: one warp task per site (all three output tiles).
+// The site's operator tiles (5 x 9 x 256 bytes) go to the warp's shared buffer
+// by 16-byte asynchronous copies, and the neighbour values of all five
+// directions to registers, all issued at once: one memory latency per site.
+template <bool F16>
+__device__ __forceinline__ void phase_apply_staged(const CBArgs& a, int jh, int r0, int s0, int ns, unsigned wmask,
+                                                   float2 (*ws)[CB_MAXSPC * NDOF], uint4* abuf, int nwarps) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gq = lane >> 2, t = lane & 3, p = gq & 1;
+    const float2* X = a.V + (long)jh * a.row;
+    float2* Wt = a.V + (long)(jh + 1) * a.row;
+    constexpr int SITE_U4 = SITE_WORDS / 4;  // 720 sixteen-byte pieces
+    const unsigned sbuf = (unsigned)__cvta_generic_to_shared(abuf);
+    for (int ls = warp; ls < ns; ls += nwarps) {
+        const int s = s0 + ls;
+        const uint4* Ag = reinterpret_cast<const uint4*>(a.Af) + (long)s * SITE_U4;
+        __syncwarp();  // the previous site's reads of the buffer are done
+        for (int q = lane; q < SITE_U4; q += 32)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sbuf + 16u * q), "l"(Ag + q) : "memory");
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        const float2* Xr = X + (long)(r0 + gq) * a.n;
+        float2 xv[5][3][2];
+#pragma unroll
+        for (int d = 0; d < 5; ++d) {
+            const float2* xn = Xr + (long)nbr_of(s, d, a.Nx, a.Nt) * NDOF;
+#pragma unroll
+            for (int kt = 0; kt < 3; ++kt) {
+                xv[d][kt][0] = __ldcg(xn + 8 * kt + t);
+                xv[d][kt][1] = __ldcg(xn + 8 * kt + t + 4);
+            }
+        }
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        __syncwarp();
+        float acc[3][4];
+#pragma unroll
+        for (int m = 0; m < 3; ++m)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[m][i] = 0.f;
+        const uint4* A4 = abuf + (gq >> 1) * 4 + t;
+#pragma unroll
+        for (int d = 0; d < 5; ++d) {
+#pragma unroll
+            for (int kt = 0; kt < 3; ++kt) {
+                const float2 x0 = xv[d][kt][0], x1 = xv[d][kt][1];
+                const unsigned h0 = pk<F16>(x0.x, x0.y), h1 = pk<F16>(x1.x, x1.y);
+                const float2 f0 = upk<F16>(h0), f1 = upk<F16>(h1);
+                const unsigned l0 = pk<F16>(x0.x - f0.x, x0.y - f0.y), l1 = pk<F16>(x1.x - f1.x, x1.y - f1.y);
+#pragma unroll
+                for (int m = 0; m < 3; ++m) {
+                    const uint4 w = A4[(d * 9 + m * 3 + kt) * (TILE_WORDS / 4)];
+                    const unsigned av[4] = {embed(w.x, p), embed(w.y, p), embed(w.z, p), embed(w.w, p)};
+                    mma<F16>(acc[m], av, h0, h1);
+                    mma<F16>(acc[m], av, l0, l1);
+                }
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            const float s0v = p ? acc[m][0] : acc[m][2], s1v = p ? acc[m][1] : acc[m][3];
+            const float o0 = __shfl_xor_sync(0xffffffffu, s0v, 4), o1 = __shfl_xor_sync(0xffffffffu, s1v, 4);
+            const int row = 8 * m + (gq >> 1) + (p ? 4 : 0);
+            const float2 v0 = p ? make_float2(o0, acc[m][2]) : make_float2(acc[m][0], o0);
+            const float2 v1 = p ? make_float2(o1, acc[m][3]) : make_float2(acc[m][1], o1);
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int rl = 2 * t + q;
+                const float2 v = q ? v1 : v0;
+                ws[rl][ls * NDOF + row] = v;
+                if ((wmask >> rl) & 1u) Wt[(long)(r0 + rl) * a.n + (long)s * NDOF + row] = v;
+            }
+        }
+    }
+}
+
+// the bits of the tile's right-hand sides whose gate opens step jh
+__device__ __forceinline__ unsigned gate_mask(const int* gate, int r0, int jh) {
+    unsigned m = 0u;
+#pragma unroll
+    for (int q = 0; q < NB_TILE; ++q) m |= (__ldcg(gate + r0 + q) == jh ? 1u : 0u) << q;
+    return m;
+}
+
 // partial sums over the chunk of V^+ w (w in ws) for right-hand side r, one
 // warp; JB >= jh + 1 bounds the rows at compile time
+// Elements e0, e0 + es, ... of the chunk; slot: this warp's partial-sum slot.
+// For JB <= 16 two elements per iteration, so twice the loads are in flight.
 template <int JB>
-__device__ __forceinline__ void phase_gram1(const CBArgs& a, int jh, int r, int c, int s0, int ne, const float2* wsr,
-                                            WarpRed& red) {
+__device__ __forceinline__ void phase_gram1(const CBArgs& a, int jh, int r, int slot, int s0, int ne, int e0, int es,
+                                            const float2* wsr, WarpRed& red) {
+    constexpr int U = JB <= 16 ? 2 : 1;
     const int lane = threadIdx.x & 31;
     const float2* Vr = a.V + (long)r * a.n + (long)s0 * NDOF;
     float2 acc[JB];
 #pragma unroll
     for (int i = 0; i < JB; ++i) acc[i] = make_float2(0.f, 0.f);
-    for (int e = lane; e < ne; e += 32) {
-        const float2 we = wsr[e];
+    for (int e = e0; e < ne; e += U * es) {
 #pragma unroll
-        for (int i = 0; i < JB; ++i)
-            if (i <= jh) acc[i] = cfmac(__ldcg(Vr + (long)i * a.row + e), we, acc[i]);
+        for (int u = 0; u < U; ++u) {
+            const int eu = e + u * es;
+            if (eu < ne) {
+                const float2 we = wsr[eu];
+#pragma unroll
+                for (int i = 0; i < JB; ++i)
+                    if (i <= jh) acc[i] = cfmac(__ldcg(Vr + (long)i * a.row + eu), we, acc[i]);
+            }
+        }
     }
     const float2 t = lane_sums<JB>(acc, jh + 1, red);
-    if (lane <= jh) *part_slot(a.p1, r, lane, c) = t;
+    if (lane <= jh) *part_slot(a.p1, r, lane, slot) = t;
 }
 
 // w -= V h1 (h1 in hs) on the chunk, and partial sums of V^+ w and ||w||^2, one
 // warp.  The chunk's basis rows are written only by this CTA; NC: they were
 // written by an earlier launch, so the read-only path may cache them.
 template <bool NC, int JB>
-__device__ __forceinline__ void phase_update_gram(const CBArgs& a, int jh, int r, int c, int s0, int ne,
-                                                  const float2* hs, WarpRed& red) {
+__device__ __forceinline__ void phase_update_gram(const CBArgs& a, int jh, int r, int slot, int s0, int ne, int e0,
+                                                  int es, const float2* hs, WarpRed& red) {
     const int lane = threadIdx.x & 31;
     const float2* Vr = a.V + (long)r * a.n + (long)s0 * NDOF;
     float2* w = a.V + (long)(jh + 1) * a.row + (long)r * a.n + (long)s0 * NDOF;
@@ -288,7 +469,7 @@ __device__ __forceinline__ void phase_update_gram(const CBArgs& a, int jh, int r
 #pragma unroll
     for (int i = 0; i < JB; ++i) acc[i] = make_float2(0.f, 0.f);
     float nn = 0.f;
-    for (int e = lane; e < ne; e += 32) {
+    for (int e = e0; e < ne; e += es) {
         float2 wv = __ldcg(w + e);
         // rows 0..jh are not written in this phase: the second pass finds them in L1
 #pragma unroll
@@ -306,29 +487,35 @@ __device__ __forceinline__ void phase_update_gram(const CBArgs& a, int jh, int r
         w[e] = wv;
     }
     const float2 t = lane_sums<JB>(acc, jh + 1, red);
-    if (lane <= jh) *part_slot(a.p2, r, lane, c) = t;
+    if (lane <= jh) *part_slot(a.p2, r, lane, slot) = t;
     const float2 nv = warp_sum2(make_float2(nn, 0.f));
-    if (lane == 0) *part_slot(a.p2, r, CB_PB - 1, c) = nv;
+    if (lane == 0) *part_slot(a.p2, r, CB_PB - 1, slot) = nv;
 }
 
 // v_{jh+1} = (w - V h2) * inv on the chunk (h2 in hs), one warp
 template <int JB>
-__device__ __forceinline__ void phase_update(const CBArgs& a, int jh, int r, int s0, int ne, const float2* hs,
-                                             float inv) {
-    const int lane = threadIdx.x & 31;
+__device__ __forceinline__ void phase_update(const CBArgs& a, int jh, int r, int s0, int ne, int e0, int es,
+                                             const float2* hs, float inv) {
+    constexpr int U = JB <= 16 ? 2 : 1;
     const float2* Vr = a.V + (long)r * a.n + (long)s0 * NDOF;
     float2* w = a.V + (long)(jh + 1) * a.row + (long)r * a.n + (long)s0 * NDOF;
-    for (int e = lane; e < ne; e += 32) {
-        float2 wv = __ldcg(w + e);
+    for (int e = e0; e < ne; e += U * es) {
 #pragma unroll
-        for (int i = 0; i < JB; ++i)
-            if (i <= jh) {
-                const float2 vi = __ldcg(Vr + (long)i * a.row + e);
-                const float2 h = hs[i];
-                wv.x -= vi.x * h.x - vi.y * h.y;
-                wv.y -= vi.x * h.y + vi.y * h.x;
+        for (int u = 0; u < U; ++u) {
+            const int eu = e + u * es;
+            if (eu < ne) {
+                float2 wv = __ldcg(w + eu);
+#pragma unroll
+                for (int i = 0; i < JB; ++i)
+                    if (i <= jh) {
+                        const float2 vi = __ldcg(Vr + (long)i * a.row + eu);
+                        const float2 h = hs[i];
+                        wv.x -= vi.x * h.x - vi.y * h.y;
+                        wv.y -= vi.x * h.y + vi.y * h.x;
+                    }
+                w[eu] = make_float2(wv.x * inv, wv.y * inv);
             }
-        w[e] = make_float2(wv.x * inv, wv.y * inv);
+        }
     }
 }
 
@@ -381,11 +568,11 @@ __global__ void __launch_bounds__(CB_THREADS, 2) k_cb_apply_gram(CBArgs a, int j
     const int ns = min(a.spc, nsite - s0);
     const int* gate = a.gbuf + (jh & 1) * a.nbp;
     if (!__syncthreads_or(threadIdx.x < NB_TILE && __ldcg(gate + r0 + threadIdx.x) == jh)) return;
-    phase_apply<F16>(a, jh, r0, s0, ns, gate, ws, CB_THREADS / 32);
+    phase_apply<F16, 1>(a, jh, r0, s0, ns, gate_mask(gate, r0, jh), ws, CB_THREADS / 32);
     __syncthreads();
     const int r = r0 + warp;
     const bool on = __ldcg(gate + r) == jh;
-    if (on) CB_DISPATCH(jh, (phase_gram1<JB>(a, jh, r, c, s0, ns * NDOF, ws[warp], S.red[warp])));
+    if (on) CB_DISPATCH(jh, (phase_gram1<JB>(a, jh, r, c, s0, ns * NDOF, lane, 32, ws[warp], S.red[warp])));
     // the last chunk of the tile adds the partials: h1 of every right-hand side
     if (!last_chunk(a.ticket + blockIdx.y, a.nchunks)) return;
     if (on) {
@@ -415,7 +602,7 @@ __global__ void __launch_bounds__(CB_THREADS, 2) k_cb_update_gram(CBArgs a, int 
     if (on) {
         if (lane <= jh) hs[warp][lane] = __ldcg(a.h1 + (long)r * CB_PB + lane);
         __syncwarp();
-        CB_DISPATCH(jh, (phase_update_gram<true, JB>(a, jh, r, c, s0, ns * NDOF, hs[warp], S.red[warp])));
+        CB_DISPATCH(jh, (phase_update_gram<true, JB>(a, jh, r, c, s0, ns * NDOF, lane, 32, hs[warp], S.red[warp])));
     }
     // the last chunk of the tile: h2, ||w||^2, h_{j+1,j}, and the least-squares push
     if (!last_chunk(a.ticket + a.nbp / NB_TILE + blockIdx.y, a.nchunks)) return;
@@ -451,7 +638,7 @@ __global__ void __launch_bounds__(CB_THREADS, 2) k_cb_update_push(CBArgs a, int 
     if (lane <= jh) hs[warp][lane] = __ldcg(a.h2 + (long)r * CB_PB + lane);
     const float inv = __ldcg(a.h2 + (long)r * CB_PB + CB_PB - 1).y;
     __syncwarp();
-    CB_DISPATCH(jh, (phase_update<JB>(a, jh, r, s0, ns * NDOF, hs[warp], inv)));
+    CB_DISPATCH(jh, (phase_update<JB>(a, jh, r, s0, ns * NDOF, lane, 32, hs[warp], inv)));
 }
 
 // ---------------------------------------------------------- cycle kernel ----
@@ -485,6 +672,30 @@ __device__ __forceinline__ void tile_sync(unsigned* bar, unsigned n, long spin, 
     __syncthreads();
 }
 
+#ifdef CB_PHASE_CLOCKS
+// phase timing of CTA (0, 0) (a build with -DCB_PHASE_CLOCKS): per step the time
+// to the end of each phase's own work and of each barrier, printed for the first
+// launches
+__device__ unsigned cb_clock_launches = 0;
+__device__ __forceinline__ unsigned long long gtime() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+#define CB_STAMP(k)                                        \
+    do {                                                   \
+        if (clk && threadIdx.x == 0) {                     \
+            const unsigned long long now = gtime();        \
+            acc_t[k] += now - t_prev;                      \
+            t_prev = now;                                  \
+        }                                                  \
+    } while (0)
+#else
+#define CB_STAMP(k) \
+    do {            \
+    } while (0)
+#endif
+
 // All ms steps of one GMRES cycle for every right-hand side of the block; the
 // grid (chunks x tiles) is resident at once (cooperative launch).  Warps 0..7
 // own the tile's right-hand sides; warp 8 pushes the least-squares columns of
@@ -492,10 +703,7 @@ __device__ __forceinline__ void tile_sync(unsigned* bar, unsigned n, long spin, 
 template <bool F16>
 __global__ void __launch_bounds__(CB_COOP_THREADS, CB_COOP_MINB) k_cb_cycle(CBArgs a, int ms, long spin, int* err) {
     extern __shared__ __align__(16) unsigned char cb_smem[];
-    CBSmem& S = *reinterpret_cast<CBSmem*>(cb_smem);
-    auto& ws = S.ws;
-    auto& hs = S.hs;
-    auto& hn_s = S.hn;
+    CBCycleSmem& S = *reinterpret_cast<CBCycleSmem*>(cb_smem);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int tile = blockIdx.y, r0 = tile * NB_TILE, c = blockIdx.x;
     const int nsite = a.Nx * a.Nt;
@@ -503,55 +711,100 @@ __global__ void __launch_bounds__(CB_COOP_THREADS, CB_COOP_MINB) k_cb_cycle(CBAr
     const int ns = min(a.spc, nsite - s0);
     const int ne = ns * NDOF;
     unsigned* bar = a.bar + 2 * tile;
-    const int r = r0 + (warp < NB_TILE ? warp : 0);
-    for (int jh = 0; jh < ms; ++jh) {
+    // warps 0 .. 8 CB_WPR - 1: right-hand side r0 + (warp % 8), element part warp / 8
+    // (its own partial-sum slot); warp 8 CB_WPR: the pushes of chunk 0
+    constexpr int NRW = NB_TILE * CB_WPR;
+    const bool rw = warp < NRW;
+    const int rl = warp % NB_TILE, part = warp / NB_TILE;
+    const int r = r0 + rl;
+    const int slot = c * CB_WPR + part, nslot = a.nchunks * CB_WPR;
+    const int e0 = part * 32 + lane, es = 32 * CB_WPR;
+#ifdef CB_PHASE_CLOCKS
+    __shared__ unsigned clk_s;
+    if (threadIdx.x == 0) clk_s = (c == 0 && tile == 0) ? atomicAdd(&cb_clock_launches, 1u) < 3 : 0;
+    __syncthreads();
+    const bool clk = clk_s != 0;
+    unsigned long long acc_t[7] = {0, 0, 0, 0, 0, 0, 0}, t_prev = gtime();
+    int steps = 0;
+#endif
+    if (c == 0 && warp == NRW && lane < NB_TILE) {  // the least squares as the cycle's start left it
+        const KState* ks = a.ks + r0 + lane;
+        for (int i = 0; i <= MSMAX; ++i) S.g[lane][i] = ks->g[i];
+        S.tol[lane] = ks->tol_abs;
+    }
+    __syncthreads();
+    // The push of step jh - 1 (warp NRW of chunk 0) runs while the other warps
+    // apply A for step jh to every right-hand side that took step jh - 1: its
+    // stop decisions are read after the first barrier, and a right-hand side that
+    // stopped at jh - 1 leaves its speculative phase-1 values unused (they go to
+    // basis row jh + 1 beyond its last column, and to partial slots nothing reads).
+    unsigned spec = gate_mask(a.gbuf, r0, 0);  // right-hand sides taking step 0
+    int jh = 0;
+    for (; jh < ms && spec; ++jh) {
         const int* gate = a.gbuf + (jh & 1) * a.nbp;
-        // the same gates in every CTA of the tile (read from L2, which every SM
-        // sees alike): all leave the loop together
-        int any = 0;
-#pragma unroll
-        for (int q = 0; q < NB_TILE; ++q) any |= __ldcg(gate + r0 + q) == jh;
-        if (!any) break;
-        const bool on = warp < NB_TILE && __ldcg(gate + r) == jh;
-        // phase 1: w = A v_jh, partial sums of V^+ w
-        if (warp < NB_TILE) phase_apply<F16>(a, jh, r0, s0, ns, gate, ws, NB_TILE);
+        const bool spec_on = rw && ((spec >> rl) & 1u);
+        // phase 1: w = A v_jh, partial sums of V^+ w (speculative for step jh > 0)
+        if (rw) phase_apply_staged<F16>(a, jh, r0, s0, ns, spec, S.ws, S.abuf[warp], NRW);
+        else if (jh > 0 && warp == NRW && c == 0 && lane < NB_TILE &&
+                 __ldcg(a.gbuf + ((jh - 1) & 1) * a.nbp + r0 + lane) == jh - 1)
+            push_cycle(a, S, lane, r0 + lane, jh - 1, S.hs[lane]);  // warp `lane` (part 0) holds h2
         __syncthreads();
-        if (on) CB_DISPATCH(jh, (phase_gram1<JB>(a, jh, r, c, s0, ne, ws[warp], S.red[warp])));
+        CB_STAMP(6);
+        if (spec_on) CB_DISPATCH(jh, (phase_gram1<JB>(a, jh, r, slot, s0, ne, e0, es, S.ws[rl], S.red[warp])));
+        CB_STAMP(0);
         tile_sync(bar, a.nchunks, spin, err);
-        // phase 2: h1 (every CTA adds the chunk partials in the same order), w -= V h1,
+        CB_STAMP(1);
+        // the gates of step jh are now final (the same in every CTA of the tile, read
+        // from L2, which every SM sees alike): all leave the loop together
+        const unsigned live = gate_mask(gate, r0, jh);
+        if (!live) break;
+        const bool on = rw && ((live >> rl) & 1u);
+        // phase 2: h1 (every warp adds the chunk partials in the same order), w -= V h1,
         // partial sums of V^+ w and ||w||^2
         if (on) {
             float2 t;
-            CB_DISPATCH(jh, (t = chunk_totals<JB>(a.p1, a.nchunks, r, jh, false, nullptr, S.red[warp])));
+            CB_DISPATCH(jh, (t = chunk_totals<JB>(a.p1, nslot, r, jh, false, nullptr, S.red[warp])));
             if (lane <= jh) {
-                hs[warp][lane] = t;
-                if (c == 0) a.ks[r].hA[lane] = make_double2(t.x, t.y);
+                S.hs[warp][lane] = t;
+                if (c == 0 && part == 0) S.h1[rl][lane] = t;
             }
             __syncwarp();
-            CB_DISPATCH(jh, (phase_update_gram<false, JB>(a, jh, r, c, s0, ne, hs[warp], S.red[warp])));
+            CB_DISPATCH(jh, (phase_update_gram<false, JB>(a, jh, r, slot, s0, ne, e0, es, S.hs[warp], S.red[warp])));
         }
+        CB_STAMP(2);
         tile_sync(bar, a.nchunks, spin, err);
-        // phase 3: h2 and h_{j+1,j}; v_{j+1}; chunk 0 pushes the columns
+        CB_STAMP(3);
+        // phase 3: h2 and h_{j+1,j}; v_{j+1} (its push comes with the next step)
         if (on) {
             float2 t;
             float nrm = 0.f;
-            CB_DISPATCH(jh, (t = chunk_totals<JB>(a.p2, a.nchunks, r, jh, true, &nrm, S.red[warp])));
+            CB_DISPATCH(jh, (t = chunk_totals<JB>(a.p2, nslot, r, jh, true, &nrm, S.red[warp])));
             const float hn = subdiag(t, jh, nrm);
-            if (lane <= jh) {
-                hs[warp][lane] = t;
-                if (c == 0) a.ks[r].hB[lane] = make_double2(t.x, t.y);
-            }
-            if (lane == 0) hn_s[warp] = hn;
+            if (lane <= jh) S.hs[warp][lane] = t;
+            if (lane == 0 && part == 0) S.hn[rl] = hn;
+            __syncwarp();
+            CB_DISPATCH(jh, (phase_update<JB>(a, jh, r, s0, ne, e0, es, S.hs[warp], hn > 0.f ? 1.f / hn : 0.f)));
         }
-        __syncthreads();
-        if (on) {
-            const float hn = hn_s[warp];
-            CB_DISPATCH(jh, (phase_update<JB>(a, jh, r, s0, ne, hs[warp], hn > 0.f ? 1.f / hn : 0.f)));
-        } else if (warp == NB_TILE && c == 0 && lane < NB_TILE && __ldcg(gate + r0 + lane) == jh) {
-            push_column(a, jh, r0 + lane, hn_s[lane]);
-        }
+        CB_STAMP(4);
         tile_sync(bar, a.nchunks, spin, err);
+        CB_STAMP(5);
+        spec = live;
+#ifdef CB_PHASE_CLOCKS
+        ++steps;
+#endif
     }
+    // the last step's push, when the loop ran to the cycle length (after an early
+    // exit every push has run: the exit follows the phase that pushed)
+    if (jh == ms && warp == NRW && c == 0 && lane < NB_TILE &&
+        __ldcg(a.gbuf + ((ms - 1) & 1) * a.nbp + r0 + lane) == ms - 1)
+        push_cycle(a, S, lane, r0 + lane, ms - 1, S.hs[lane]);
+#ifdef CB_PHASE_CLOCKS
+    if (clk && threadIdx.x == 0 && steps > 0)
+        printf("cb_cycle phases (ns/step over %d steps, %d chunks): apply %llu, gram1 %llu, bar1 %llu, "
+               "update+gram2 %llu, bar2 %llu, update %llu, bar3 %llu\n",
+               steps, a.nchunks, acc_t[6] / steps, acc_t[0] / steps, acc_t[1] / steps, acc_t[2] / steps,
+               acc_t[3] / steps, acc_t[4] / steps, acc_t[5] / steps);
+#endif
 }
 
 __global__ void k_cb_gate_init(CBArgs a) {
@@ -590,8 +843,9 @@ mg_status cb_configure() {
     MG_CUDA_TRY(cudaFuncSetAttribute(k_cb_apply_gram<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
     MG_CUDA_TRY(cudaFuncSetAttribute(k_cb_update_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
     MG_CUDA_TRY(cudaFuncSetAttribute(k_cb_update_push, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-    MG_CUDA_TRY(cudaFuncSetAttribute(k_cb_cycle<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-    MG_CUDA_TRY(cudaFuncSetAttribute(k_cb_cycle<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    const int smc = (int)sizeof(CBCycleSmem);
+    MG_CUDA_TRY(cudaFuncSetAttribute(k_cb_cycle<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smc));
+    MG_CUDA_TRY(cudaFuncSetAttribute(k_cb_cycle<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smc));
     done[dev] = true;
     return MG_OK;
 }
@@ -600,7 +854,7 @@ bool cb_geometry_cycle(CBArgs& a, long nsite, int nbp, bool fp16) {
     const int ntiles = nbp / NB_TILE;
     int per_sm = 0;
     if (cb_configure() != MG_OK) return false;
-    const size_t sm = sizeof(CBSmem);
+    const size_t sm = sizeof(CBCycleSmem);
     cudaError_t e = fp16 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cb_cycle<true>, CB_COOP_THREADS, sm)
                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cb_cycle<false>, CB_COOP_THREADS, sm);
     if (e != cudaSuccess || per_sm < 1) {
@@ -612,7 +866,7 @@ bool cb_geometry_cycle(CBArgs& a, long nsite, int nbp, bool fp16) {
     long spc = (nsite * ntiles + resident - 1) / resident;
     spc = std::max(1L, spc);
     const long nch = (nsite + spc - 1) / spc;
-    if (spc > CB_MAXSPC || nch > CB_MAXCH || nch * ntiles > resident) return false;
+    if (spc > CB_MAXSPC || nch * CB_WPR > CB_MAXCH || nch * ntiles > resident) return false;
     a.spc = (int)spc;
     a.nchunks = (int)nch;
     a.nbp = nbp;
@@ -644,7 +898,7 @@ mg_status launch_cb_cycle(const CBArgs& a, int ms, bool fp16, long spin, int* er
     MG_TRY(cb_configure());
     cfg.gridDim = dim3(a.nchunks, a.nbp / NB_TILE);
     cfg.blockDim = dim3(CB_COOP_THREADS);
-    cfg.dynamicSmemBytes = sizeof(CBSmem);
+    cfg.dynamicSmemBytes = sizeof(CBCycleSmem);
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 1;

@@ -1,5 +1,6 @@
 // Fused Arnoldi step of the batched coarse GMRES-Proj (coarse_block.cu).
 #pragma once
+#include "batch.cuh"
 #include "coarse_coop.cuh"
 
 namespace mg {
@@ -7,7 +8,11 @@ namespace mg {
 constexpr int CB_PB = 32;       // partial slots per right-hand side: basis products, norm in the last
 constexpr int CB_MAXCH = 256;   // site chunks (the partials of a slot are adjacent, one per chunk)
 constexpr int CB_THREADS = 256;
-constexpr int CB_COOP_THREADS = 288;  // the cycle kernel: 8 warps of right-hand sides and one pushing warp
+#ifndef CB_WPR_DEF
+#define CB_WPR_DEF 1
+#endif
+constexpr int CB_WPR = CB_WPR_DEF;     // the cycle kernel's warps per right-hand side
+constexpr int CB_COOP_THREADS = (NB_TILE * CB_WPR + 1) * 32;  // and one pushing warp
 constexpr int CB_MAXSPC = 16;   // coarse sites per chunk
 
 struct CBArgs {
