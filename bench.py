@@ -38,6 +38,7 @@ METRIC = "MG-FGMRES solves/s to true rel-res 1e-8 (mixed vs FP64); p50/p99 laten
 L = 256
 NCONF = 10
 TOL = 1e-8
+H_DR_M = 30  # GMRES-DR / GMRES-Proj m (k = 10)
 
 
 def parse():
@@ -53,6 +54,7 @@ def parse():
     ap.add_argument("--no-serving", action="store_true", help="skip the served-stream sample")
     ap.add_argument("--no-partial", action="store_true", help="skip the partial-intermediate-solve variant")
     ap.add_argument("--no-batching", action="store_true", help="skip the 64-right-hand-side batching sample")
+    ap.add_argument("--no-scale", action="store_true", help="skip the 1024^2 x 16-right-hand-side block solve")
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-rate", type=float, default=0.8,
                     help="Poisson arrival rate, requests/s (0.8: about 0.9x the measured saturated rate of this mix)")
@@ -178,6 +180,99 @@ def fine_roofline(mg, dev, peaks, peak_kind, Lb=2048, launches=20, warm=3):
             "frac": ach / peaks["hbm_gbs"], "kernel": f"k_wilson<float> (fine Wilson-Dirac apply, {Lb}^2 x 2)",
             "bytes_per_launch": nbytes, "avg_launch_us": avg_s * 1e6, "launches": launches,
             "l2": "flushed before every launch", "peak_source": peak_kind}
+
+
+def timed_launches(torch, dev, fn, launches=10, warm=3):
+    """Mean CUDA-event time (s) of fn() on the current stream, L2 flushed (a 256 MB
+    write) before every launch."""
+    import numpy as np
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ms = []
+    for i in range(warm + launches):
+        flush.fill_(i & 0xFF)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if i >= warm:
+            ms.append(e0.elapsed_time(e1))
+    del flush
+    return float(np.mean(ms)) / 1e3
+
+
+def run_scale(mg, torch, np, dev, peaks, peak_kind, nrhs=16, Ls=1024):
+    """The scale-up workload: one 1024^2 configuration (2000 sweeps, tuned m0),
+    hierarchy 1024^2 x 2 -> 256^2 x 24 -> 64^2 x 24, GMRES-DR(40,16) on the
+    first right-hand side, then 16 right-hand sides in one lockstep block solve
+    with FP16 tensor-core block products, FP64 outer residual to 1e-8.  Beside
+    it, the HBM fractions of the fine Wilson apply (FP32) and of the 24-dof
+    block stencil of the intermediate grid (256^2 x 24) at this size, each timed
+    alone with L2 flushed: the FP32 single-vector kernel and the FP16 tensor-core
+    kernel on the 16 right-hand sides."""
+    import synth
+    t0 = time.perf_counter()
+    U = synth.gauge_field(Ls, 0, gpu=True)
+    gen_s = time.perf_counter() - t0
+    fp_ok = synth.check_fingerprint(Ls, 0, U)
+    m0 = synth.m0_for(Ls, 0)
+    Ud = torch.from_numpy(U).to(dev)
+    t0 = time.perf_counter()
+    h = mg.mg_setup(Ud, Ls, Ls, m0, params=mg.default_params(precision=mg.MG_MIXED_FP16, dr_m=40, dr_k=16),
+                    starts0=torch.from_numpy(synth.nullvec_starts(Ls, 0, 0, 12, Ls * Ls * 2)).to(dev),
+                    starts1=torch.from_numpy(synth.nullvec_starts(Ls, 0, 1, 12, (Ls // 4) ** 2 * 24)).to(dev))
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream(dev)
+    try:
+        B = torch.from_numpy(synth.rhs(Ls, 0, 200, nrhs=1 + 2 * nrhs)).to(dev)
+        X = torch.zeros_like(B)
+        t0 = time.perf_counter()
+        _, it0, rr0, _ = mg.mg_solve(h, B[0], X[0], 1, TOL)  # GMRES-DR: builds the deflation space
+        dr_s = time.perf_counter() - t0
+        mg.mg_solve(h, B[1:1 + nrhs], X[1:1 + nrhs], nrhs, TOL)  # warm: graphs, block workspaces
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = mg.mg_kernel_launches()
+        e0.record(stream)
+        _, its, rrs, sd = mg.mg_solve(h, B[1 + nrhs:], X[1 + nrhs:], nrhs, TOL)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        launches = mg.mg_kernel_launches() - l0
+        ms = e0.elapsed_time(e1)
+        assert max(rrs) <= TOL and rr0[0] <= TOL
+        # K3 at this size: the intermediate-grid block stencil, 256^2 x 24
+        n1 = (Ls // 4) ** 2 * 24
+        s1 = (Ls // 4) ** 2
+        x1 = torch.complex(torch.randn((nrhs, n1), device=dev), torch.randn((nrhs, n1), device=dev))
+        y1 = torch.empty_like(x1)
+        t_mma = timed_launches(torch, dev, lambda: mg.mg_apply_block(h, 1, x1, y1, nrhs, mg.MG_F16))
+        b_mma = 5 * 576 * 4 * s1 + 2 * nrhs * n1 * 8  # FP16 operator once, 16 vectors in and out (complex64)
+        t_f32 = timed_launches(torch, dev, lambda: mg.mg_apply(h, 1, x1[0], y1[0], precision=mg.MG_F32))
+        b_f32 = (5 * 576 + 2 * 24) * 8 * s1
+    finally:
+        h.close()
+    fine = fine_roofline(mg, dev, peaks, peak_kind, Lb=Ls)
+    hb = peaks["hbm_gbs"]
+    return {"metric": "MG-FGMRES solves/s to true rel-res 1e-8", "value": nrhs / (ms / 1e3), "unit": "solves/s",
+            "workload": f"{Ls}^2 config 0 x {nrhs} RHS in one lockstep block solve, GMRES-DR(40,16)/"
+                        "GMRES-Proj(40,16), FP16 tensor-core block products, FP32 V-cycle, FP64 outer",
+            "ms": ms, "outer_iters_mean": float(np.mean(its)), "outer_iters_max": int(max(its)),
+            "coarse_iters": sd["coarse_iters"], "max_relres": float(max(rrs)), "gpu_launches": int(launches),
+            "first_rhs_gmres_dr_s": dr_s, "setup_s": setup_s, "field_gen_s": gen_s,
+            "field": "GPU heatbath, bit-identical to the host generator", "m0_fingerprint_match": fp_ok,
+            "k1_wilson_roofline": fine,
+            "k3_block_stencil_roofline": {
+                "bound": "hbm", "kernel": f"k_bstencil_mma<fp16> (256^2 x 24, {nrhs} RHS)",
+                "achieved": b_mma / t_mma / 1e9, "peak": hb, "unit": "GB/s", "frac": b_mma / t_mma / 1e9 / hb,
+                "bytes_per_launch": b_mma, "avg_launch_us": t_mma * 1e6, "l2": "flushed before every launch",
+                "peak_source": peak_kind},
+            "k3_stencil_f32_roofline": {
+                "bound": "hbm", "kernel": "k_stencil_f32 (256^2 x 24, one vector)",
+                "achieved": b_f32 / t_f32 / 1e9, "peak": hb, "unit": "GB/s", "frac": b_f32 / t_f32 / 1e9 / hb,
+                "bytes_per_launch": b_f32, "avg_launch_us": t_f32 * 1e6, "l2": "flushed before every launch",
+                "peak_source": peak_kind}}
 
 
 def dist_env():
@@ -388,6 +483,7 @@ def run_native(args):
                 cnt += b
                 mg.mg_timing_enable(h, lev, False)
             kt[lev] = (tot, cnt)
+        kt["wall_ms"] = ms
         kt["coarse_iters"] = sum(r[3]["coarse_iters"] for r in res)
         kt["coarse_solves"] = sum(r[3]["coarse_solves"] for r in res)
         kt["dr_solves"] = sum(r[3]["dr_solves"] for r in res)
@@ -438,13 +534,15 @@ def run_native(args):
             with open(tpath) as f:
                 return json.load(f).get("dram_bytes_per_launch")
         return None
+    # share of the ten solve streams' time spent in the coarse kernel (the timing pass)
+    share = (c_ms / (nconf * kt["wall_ms"])) if kt.get("wall_ms") else None
     roofline = {"bound": "hbm", "achieved": c_ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": c_ach / peaks["hbm_gbs"], "traffic": traffic_of("coarse_proj_f32_256.json"),
                 "kernel": "k_coarse_proj<float> (whole coarse GMRES-Proj solve, 16^2 x 24, FP16 operator, "
                           "cluster of 16 CTAs)",
                 "bytes_per_launch": c_bytes, "steps_per_launch": steps_per_launch,
                 "us_per_step": 1e6 * c_avg / max(steps_per_launch, 1), "avg_launch_us": c_avg * 1e6,
-                "launches": c_n, "share_of_timed_gpu_time": None, "peak_source": peak_kind,
+                "launches": c_n, "share_of_timed_gpu_time": share, "peak_source": peak_kind,
                 "note": "latency-bound: each Krylov step is two DSMEM reductions and a neighbour exchange, "
                         "counted on mbarriers; the stencil operand (5.9 MB) is L2-resident, so HBM is not the "
                         "binding limit"}
@@ -493,32 +591,67 @@ def run_native(args):
         for h in hsp:
             h.close()
 
+    pool.shutdown(wait=True)  # the per-configuration solve threads end here, not at interpreter exit
+
     # ---------- batching: 64 right-hand sides of one 256^2 configuration ----------
     batching = None
+    block_roofline = None
     if not args.no_batching:
-        batching = {"rhs": 64, "config": 0, "precision": "mixed"}
+        batching = {"rhs": 64, "config": 0}
         B64 = torch.stack([torch.from_numpy(synth.rhs(L, 0, 50000 + i)[0]) for i in range(64)]).to(dev)
-        for mode, over in (("contexts", dict(parallel=7)), ("pairs", dict(parallel=7, pair_rhs=1))):
+        n2 = (L // 16) ** 2 * 24
+        for mode, prec, over in (("block_bf16", mg.MG_MIXED_BF16, {}), ("block_fp16", mg.MG_MIXED_FP16, {}),
+                                 ("contexts_fp32", mg.MG_MIXED, dict(parallel=7))):
             h = mg.mg_setup(torch.from_numpy(Us[0]).to(dev), L, L, m0s[0],
-                            params=mg.default_params(precision=mg.MG_MIXED, **over),
+                            params=mg.default_params(precision=prec, **over),
                             starts0=torch.from_numpy(synth.nullvec_starts(L, 0, 0, 12, n0)).to(dev),
                             starts1=torch.from_numpy(synth.nullvec_starts(L, 0, 1, 12, (L // 4) ** 2 * 24)).to(dev))
             X64 = torch.zeros_like(B64)
             mg.mg_solve(h, B64[0], X64[0], 1, TOL)  # builds the deflation space
-            mg.mg_solve(h, B64[1:15], X64[1:15], 14, TOL)  # contexts created, warm
+            mg.mg_solve(h, B64[1:15], X64[1:15], 14, TOL)  # graphs captured, contexts created, warm
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            _, it64, rr64, _ = mg.mg_solve(h, B64, X64, 64, TOL)
+            _, it64, rr64, sd64 = mg.mg_solve(h, B64, X64, 64, TOL)
             e1.record(stream)
             torch.cuda.synchronize()
             assert max(rr64) <= TOL
             ms_b = max_over_ranks(e0.elapsed_time(e1))
-            batching[mode] = {"solves_per_s": 64 / (ms_b / 1e3), "ms": ms_b, "outer_iters_mean": float(np.mean(it64))}
+            batching[mode] = {"solves_per_s": 64 / (ms_b / 1e3), "ms": ms_b, "outer_iters_mean": float(np.mean(it64)),
+                              "coarse_iters": sd64["coarse_iters"]}
+            if mode == "block_bf16":
+                # the dominant kernel of the block solve: the batched coarse GMRES-Proj (one
+                # cooperative kernel per GMRES cycle), timed alone on 64 coarse right-hand sides
+                Bc = torch.stack([torch.from_numpy(synth.complex_gaussian((n2,), 77, r)) for r in range(64)]
+                                 ).to(torch.complex64).to(dev)
+                Xc = torch.zeros_like(Bc)
+                mg.mg_coarse_solve(h, Bc, Xc, TOL, mg.MG_BF16, nrhs=64)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                _, itc, _, _ = mg.mg_coarse_solve(h, Bc, Xc, TOL, mg.MG_BF16, nrhs=64)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                cms = e0.elapsed_time(e1)
+                steps = max(itc)  # lockstep: the block takes as many steps as its slowest right-hand side
+                ms_cyc = max(H_DR_M - 10, 1)
+                # algorithmic bytes of one lockstep step: the BF16 operator once (4 bytes an entry),
+                # and per right-hand side v_j in, w out, and the two CGS2 passes over V_0..V_j
+                # ((ms + 1) / 2 vectors each on average over a cycle of ms steps), complex64
+                step_bytes = (5 * 576 * 4) * (L // 16) ** 2 + 64 * (2 + ms_cyc + 1) * n2 * 8
+                ach = step_bytes * steps / (cms / 1e3) / 1e9
+                block_roofline = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                  "frac": ach / peaks["hbm_gbs"], "traffic": None,
+                                  "kernel": "k_cb_cycle<bf16> (batched coarse GMRES-Proj, 16^2 x 24, 64 RHS, "
+                                            "one cooperative kernel per GMRES cycle)",
+                                  "us_per_step": 1e3 * cms / steps, "steps": steps, "bytes_per_step": step_bytes,
+                                  "ms": cms, "peak_source": peak_kind,
+                                  "note": "the Krylov bases of the 64 right-hand sides (65 MB) stay in L2; each "
+                                          "step is three tile barriers apart"}
             h.close()
-        batching["what"] = ("64 right-hand sides of one 256^2 configuration in one mg_solve: 7 concurrent solve "
-                            "contexts, one right-hand side each, against 7 workers with two right-hand sides each "
-                            "in lockstep, their coarsest solves sharing one cluster kernel")
+        batching["what"] = ("64 right-hand sides of one 256^2 configuration in one mg_solve: lockstep block "
+                            "solve with the 24x24 block products of the intermediate and coarsest grids on tensor "
+                            "cores (BF16 or FP16 operator, FP32 vectors split into two 16-bit parts, FP32 "
+                            "accumulation), against 7 concurrent FP32 solve contexts")
 
     # ---------------- comparison arms of the 256^2 study (Section 2) ----------------
     arms = None
@@ -547,6 +680,11 @@ def run_native(args):
                           "first_rhs": True, "configs": narm, "precision": "f64",
                           "wall_s": time.perf_counter() - t0}
 
+    # ---------------- scale-up: 1024^2, 16 right-hand sides, FP16 tensor cores ----------------
+    scale = None
+    if not args.no_scale:
+        scale = run_scale(mg, torch, np, dev, peaks, peak_kind)
+
     # ---------------- served stream (continuous batching over many operators) ----------------
     serving = None
     if not args.no_serving:
@@ -574,11 +712,13 @@ def run_native(args):
         "fp64": fp64,
         "partial_solve": partial,
         "batching_64rhs": batching,
+        "scale_1024": scale,
         "arms_256": arms,
         "serving": serving,
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": nconf * n0 * 16,
                 "d2h_bytes_per_step": nconf * n0 * 16 + nconf * 8},
         "roofline": roofline,
+        "block_roofline": block_roofline,
         "stencil_roofline": stencil_roofline,
         "fine_roofline": fine,
         "cpu_baseline": cpu,

@@ -8,7 +8,10 @@ arrays are complex128 (complex64 for the FP32 operator-level calls).
 """
 from __future__ import annotations
 
+import atexit
 import ctypes
+import sys
+import weakref
 
 import numpy as np
 
@@ -67,13 +70,34 @@ def default_params(**overrides) -> MGParams:
     return p
 
 
+# Handles and servers not yet closed.  An exit hook closes them, servers first
+# (their workers solve on handles they own), while the interpreter and the CUDA
+# runtime are still whole: exit hooks run before the interpreter tears its
+# modules down and before the C runtime's static destructors.  A destructor that
+# runs during interpreter finalization does not call into the library.
+_live = weakref.WeakSet()
+
+
+def _close_live():
+    for o in sorted(list(_live), key=lambda o: 0 if isinstance(o, Server) else 1):
+        try:
+            o.close()
+        except Exception:
+            pass
+
+
+atexit.register(_close_live)
+
+
 class Handle:
-    """Owner of an mg_handle; mg_destroy runs on close() or garbage collection."""
+    """Owner of an mg_handle; mg_destroy runs on close(), at garbage collection
+    or at interpreter exit."""
 
     def __init__(self, ptr: int, Lx: int, Lt: int, params: MGParams):
         self.ptr = ptr
         self.Lx, self.Lt = Lx, Lt
         self.params = params
+        _live.add(self)
 
     def close(self):
         if self.ptr:
@@ -81,6 +105,8 @@ class Handle:
             self.ptr = None
 
     def __del__(self):
+        if sys.is_finalizing():
+            return
         try:
             self.close()
         except Exception:
@@ -247,6 +273,7 @@ class Server:
         _lib.check(load().mg_server_create(ctypes.byref(self.params), int(hbm_budget_bytes), int(workers),
                                            ctypes.byref(out)), "mg_server_create")
         self.ptr = out.value
+        _live.add(self)
         self._keep = {}
 
     def submit(self, key, gauge, Lx, Lt, m0, b, x, nrhs, tol, starts0=None, starts1=None) -> int:
@@ -291,6 +318,8 @@ class Server:
             self.ptr = None
 
     def __del__(self):
+        if sys.is_finalizing():
+            return
         try:
             self.close()
         except Exception:

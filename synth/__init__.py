@@ -5,6 +5,8 @@ This module holds no arithmetic of the solver.  It makes:
 * quenched U(1) gauge fields at beta = 6.0 from a deterministic heatbath
   (``heatbath.c``), standing in for the paper's QCDLAB configurations
   (Section 2, "Methods": 10 configurations per lattice size at beta = 6.0);
+  ``heatbath_gpu.cu`` is the same generator on the GPU, bit-identical to it,
+  for the large lattices a benchmark needs in seconds;
 * complex-Gaussian right-hand sides and null-vector start vectors
   (E|z|^2 = 1, i.e. real and imaginary parts each N(0, 1/2));
 * Z(4) noise (the paper's right-hand sides, Section 2) as an option;
@@ -29,8 +31,11 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "_heatbath.so")
 _SRC = os.path.join(_HERE, "heatbath.c")
+_SO_GPU = os.path.join(_HERE, "_heatbath_gpu.so")
+_SRC_GPU = os.path.join(_HERE, "heatbath_gpu.cu")
 _lock = threading.Lock()
 _lib = None
+_lib_gpu = None
 
 BETA = 6.0
 
@@ -44,6 +49,28 @@ def build(force: bool = False) -> str:
         subprocess.run(cmd, check=True)
         os.replace(tmp, _SO)
     return _SO
+
+
+def _nvcc():
+    for cand in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc"):
+        if cand and os.path.exists(cand):
+            return cand
+    return None
+
+
+def build_gpu(force: bool = False) -> str | None:
+    """Compile the GPU heatbath in place (nvcc, sm_103a, no FMA contraction);
+    None when no CUDA toolkit is installed."""
+    cc = _nvcc()
+    if cc is None:
+        return None
+    if force or not os.path.exists(_SO_GPU) or os.path.getmtime(_SO_GPU) < os.path.getmtime(_SRC_GPU):
+        tmp = _SO_GPU + f".{os.getpid()}.tmp"
+        cmd = [cc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-fmad=false", "-shared",
+               "-Xcompiler", "-fPIC", _SRC_GPU, "-o", tmp, "-lcudart"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _SO_GPU)
+    return _SO_GPU
 
 
 def _load():
@@ -61,6 +88,32 @@ def _load():
             lib.synth_exp.argtypes = [ctypes.c_double]
             _lib = lib
     return _lib
+
+
+def _load_gpu():
+    global _lib_gpu
+    with _lock:
+        if _lib_gpu is None:
+            if build_gpu() is None:
+                raise RuntimeError("the GPU heatbath needs the CUDA toolkit (nvcc)")
+            lib = ctypes.CDLL(_SO_GPU)
+            lib.synth_heatbath_gpu.restype = ctypes.c_int
+            lib.synth_heatbath_gpu.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                               ctypes.c_int, ctypes.c_uint64, ctypes.c_void_p]
+            _lib_gpu = lib
+    return _lib_gpu
+
+
+def heatbath_gpu(Lx: int, Lt: int, beta: float, sweeps: int, seed: int) -> np.ndarray:
+    """heatbath() computed on the current CUDA device; bit-identical result."""
+    import torch
+    U = torch.empty((Lt, Lx, 2), dtype=torch.complex128, device="cuda")
+    stream = torch.cuda.current_stream()
+    rc = _load_gpu().synth_heatbath_gpu(U.data_ptr(), Lx, Lt, float(beta), int(sweeps),
+                                        int(seed) & (2**64 - 1), ctypes.c_void_p(stream.cuda_stream))
+    if rc != 0:
+        raise RuntimeError(f"GPU heatbath failed ({rc}) for Lx={Lx} Lt={Lt} beta={beta} sweeps={sweeps}")
+    return U.cpu().numpy()
 
 
 def default_sweeps(L: int) -> int:
@@ -89,13 +142,18 @@ _CACHE_DIR = os.path.join(_HERE, "_cache")
 
 
 def gauge_field(L: int, config: int, sweeps: int | None = None, beta: float = BETA,
-                cache: bool = True) -> np.ndarray:
-    """Configuration `config` of the L x L pool (seed 1000 L + config)."""
+                cache: bool = True, gpu: bool = False) -> np.ndarray:
+    """Configuration `config` of the L x L pool (seed 1000 L + config); with
+    gpu=True a field not in the cache is generated on the current CUDA device
+    (the same bits)."""
     sweeps = default_sweeps(L) if sweeps is None else sweeps
     path = os.path.join(_CACHE_DIR, f"gauge_L{L}_c{config}_s{sweeps}_b{beta:g}.npy")
     if cache and os.path.exists(path):
         return np.load(path)
-    U = heatbath(L, L, beta, sweeps, gauge_seed(L, config))
+    if gpu:
+        U = heatbath_gpu(L, L, beta, sweeps, gauge_seed(L, config))
+    else:
+        U = heatbath(L, L, beta, sweeps, gauge_seed(L, config))
     if cache:
         os.makedirs(_CACHE_DIR, exist_ok=True)
         tmp = path + f".{os.getpid()}.tmp.npy"
