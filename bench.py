@@ -55,92 +55,137 @@ def parse():
     ap.add_argument("--no-partial", action="store_true", help="skip the partial-intermediate-solve variant")
     ap.add_argument("--no-batching", action="store_true", help="skip the 64-right-hand-side batching sample")
     ap.add_argument("--no-scale", action="store_true", help="skip the 1024^2 x 16-right-hand-side block solve")
-    ap.add_argument("--serve-requests", type=int, default=24)
-    ap.add_argument("--serve-rate", type=float, default=0.8,
-                    help="Poisson arrival rate, requests/s (0.8: about 0.9x the measured saturated rate of this mix)")
+    ap.add_argument("--serve-requests", type=int, default=64, help="requests per phase of the served stream")
+    ap.add_argument("--serve-budget-gib", type=float, default=48.0,
+                    help="HBM budget of the server's resident hierarchies (below the stream's total need)")
+    ap.add_argument("--serve-workers", type=int, default=8)
     return ap.parse_args()
 
 
 SERVE_SIZES = (64, 128, 256, 512)
-SERVE_CONFIGS = 3
+SERVE_CONFIGS = 10
+SERVE_RATES = (0.5, 0.9, 1.2)  # offered load as a fraction of the measured saturated rate
 
 
-def run_serving(mg, torch, np, dev, rank, nreq=24, rate=3.0, workers=10):
-    """Served stream: Poisson arrivals of requests over 4 lattice sizes x 3
-    configurations (12 operators), nrhs ~ U{1..32}, tol 1e-8, mixed precision.
-    Hierarchies are built by a warm-up request per operator (cold starts,
-    reported separately); then the stream is timed: per-request latency from
-    submission to completion, and right-hand sides per second over the stream.
-    The plain FP64 sequential reference time of the same stream is estimated
-    from warm FP64 solves of each lattice size."""
+def run_serving(mg, torch, np, dev, rank):
+    """Served stream over a pool of 10 configurations at each of 64^2, 128^2,
+    256^2 and 512^2 (40 operators), each request carrying U{1..32} complex-
+    Gaussian right-hand sides at tol 1e-8, keys drawn uniformly.  The server runs
+    the block precision (BF16 tensor-core block products, FP32 V-cycle, FP64
+    outer): queued right-hand sides of one operator, from any request, are
+    solved together.  Hierarchies are admitted under an HBM budget below what
+    keeping all 40 resident would take, so the stream evicts and rebuilds.
+
+    Phases, each a fresh draw of requests: a saturated one (every request
+    submitted at once; right-hand sides per second over the makespan), then
+    Poisson arrivals offering 0.5x, 0.9x and 1.2x that saturated rate.  Per
+    phase: right-hand sides per second from the first submission to the last
+    completion, p50/p99 request latency (submission to completion), cold starts
+    and evictions.  The plain FP64 sequential reference time of each phase's
+    requests is estimated from warm FP64 GPU solves at each lattice size."""
     import synth
     args = parse()
-    nreq, rate = args.serve_requests, args.serve_rate
+    nreq = args.serve_requests
+    budget = int(args.serve_budget_gib * (1 << 30))
     rng = np.random.default_rng(1234 + rank)
     keys = [(L_, c) for L_ in SERVE_SIZES for c in range(SERVE_CONFIGS)]
-    fields = {k: synth.gauge_field(k[0], k[1]) for k in keys}
+    t0 = time.perf_counter()
+    fields = {k: synth.gauge_field(k[0], k[1], gpu=True) for k in keys}
+    gen_s = time.perf_counter() - t0
+    fp_ok = all(synth.check_fingerprint(k[0], k[1], fields[k]) for k in keys)
+    starts = {k: (torch.from_numpy(synth.nullvec_starts(k[0], k[1], 0, 12, k[0] * k[0] * 2)),
+                  torch.from_numpy(synth.nullvec_starts(k[0], k[1], 1, 12, (k[0] // 4) ** 2 * 24))) for k in keys}
+    gauges = {k: torch.from_numpy(fields[k]) for k in keys}
 
     def key_id(k):
         return k[0] * 1000 + k[1]
 
-    def submit(srv, k, nrhs, seed):
-        L_, c = k
-        b = torch.from_numpy(synth.rhs(L_, c, 70000 + seed, nrhs=nrhs)).pin_memory()
-        x = torch.zeros_like(b).pin_memory()
-        U = torch.from_numpy(fields[k])
-        t = srv.submit(key_id(k), U, L_, L_, synth.m0_for(L_, c), b, x, nrhs, TOL,
-                       starts0=torch.from_numpy(synth.nullvec_starts(L_, c, 0, 12, L_ * L_ * 2)),
-                       starts1=torch.from_numpy(synth.nullvec_starts(L_, c, 1, 12, (L_ // 4) ** 2 * 24)))
-        return t, nrhs
+    def plan_of(n):
+        return [(keys[rng.integers(len(keys))], int(rng.integers(1, 33))) for _ in range(n)]
 
-    srv = mg.Server(mg.default_params(precision=mg.MG_MIXED), workers=workers)
-    try:
-        t0 = time.perf_counter()
-        warm = [submit(srv, k, 1, i) for i, k in enumerate(keys)]
-        for t, n in warm:
-            srv.wait(t, n)
-        cold_s = time.perf_counter() - t0
-        plan = [(keys[rng.integers(len(keys))], int(rng.integers(1, 33))) for _ in range(nreq)]
-        gaps = rng.exponential(1.0 / rate, size=nreq)
+    def run_phase(srv, plan, gaps, seed0):
+        # the requests' right-hand sides, in pinned host memory, made before the clock starts
+        bufs = []
+        for i, (k, n) in enumerate(plan):
+            b = torch.from_numpy(synth.rhs(k[0], k[1], seed0 + i, nrhs=n)).pin_memory()
+            bufs.append((b, torch.zeros_like(b).pin_memory()))
+        s0 = srv.stats()
         tickets = []
         t_start = time.perf_counter()
-        for i, (k, n) in enumerate(plan):
-            if i:
-                time.sleep(gaps[i])
-            tickets.append((submit(srv, k, n, 1000 + i), k))
+        arrive = np.concatenate([[0.0], np.cumsum(gaps[1:])]) if gaps is not None else np.zeros(len(plan))
+        for i, ((k, n), (b, x)) in enumerate(zip(plan, bufs)):
+            wait = t_start + arrive[i] - time.perf_counter()
+            if wait > 0:
+                time.sleep(wait)
+            t = srv.submit(key_id(k), gauges[k], k[0], k[0], synth.m0_for(k[0], k[1]), b, x, n, TOL,
+                           starts0=starts[k][0], starts1=starts[k][1])
+            tickets.append((t, n))
         lat, worst, solved = [], 0.0, 0
-        for (t, n), k in tickets:
+        for t, n in tickets:
             st, it, rr, l = srv.wait(t, n)
             lat.append(l)
             worst = max(worst, max(rr))
             solved += n
         t_end = time.perf_counter()
+        s1 = srv.stats()
+        assert worst <= TOL, f"a served solve missed the tolerance: {worst}"
+        return {"solves_per_s": solved / (t_end - t_start), "rhs": solved, "requests": len(plan),
+                "wall_s": t_end - t_start,
+                "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                "cold_starts": int(s1["cold_starts"] - s0["cold_starts"]),
+                "evictions": int(s1["evictions"] - s0["evictions"]),
+                "batches": int(s1["batches"] - s0["batches"]), "max_batch": int(s1["max_batch"])}
+
+    params = mg.default_params(precision=mg.MG_MIXED_BF16, rhs_block=32)
+    srv = mg.Server(params, hbm_budget_bytes=budget, workers=args.serve_workers)
+    phases, plans = {}, {}
+    try:
+        plans["saturated"] = plan_of(nreq)
+        sat = run_phase(srv, plans["saturated"], None, 100000)
+        phases["saturated"] = sat
+        mean_rhs = 16.5
+        for j, frac in enumerate(SERVE_RATES):
+            rate = frac * sat["solves_per_s"] / mean_rhs
+            plan = plan_of(nreq)
+            gaps = rng.exponential(1.0 / rate, size=nreq)
+            ph = run_phase(srv, plan, gaps, 200000 + 10000 * j)
+            ph["offered_req_per_s"] = rate
+            ph["offered_fraction_of_saturated"] = frac
+            phases[f"rate_{frac:g}x"] = ph
+            plans[f"rate_{frac:g}x"] = plan
         info = srv.stats()
     finally:
         srv.close()
-    assert worst <= TOL
-    # FP64 sequential reference: warm per-RHS time of each size (2 solves after the deflating one)
+    # FP64 sequential reference: warm per-right-hand-side time at each size (one solve
+    # after the deflation-building one)
     per_rhs = {}
     for L_ in SERVE_SIZES:
         k = (L_, 0)
-        h = mg.mg_setup(torch.from_numpy(fields[k]).to(dev), L_, L_, synth.m0_for(L_, 0),
-                        params=mg.default_params(precision=mg.MG_FP64))
-        b = torch.from_numpy(synth.rhs(L_, 0, 90000, nrhs=3)).to(dev)
+        h = mg.mg_setup(gauges[k].to(dev), L_, L_, synth.m0_for(L_, 0),
+                        params=mg.default_params(precision=mg.MG_FP64),
+                        starts0=starts[k][0].to(dev), starts1=starts[k][1].to(dev))
+        b = torch.from_numpy(synth.rhs(L_, 0, 90000, nrhs=2)).to(dev)
         x = torch.zeros_like(b)
         mg.mg_solve(h, b[0], x[0], 1, TOL)
         torch.cuda.synchronize()
         ts = time.perf_counter()
-        mg.mg_solve(h, b[1:], x[1:], 2, TOL)
-        per_rhs[L_] = (time.perf_counter() - ts) / 2
+        mg.mg_solve(h, b[1], x[1], 1, TOL)
+        per_rhs[L_] = time.perf_counter() - ts
         h.close()
-    seq = sum(per_rhs[k[0]] * n for k, n in plan)
-    return {"value": solved / (t_end - t_start), "unit": "solves/s", "requests": nreq, "rhs": solved,
-            "rate_req_per_s": rate, "workers": workers, "operators": len(keys),
-            "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
-            "cold_start_s": cold_s, "cold_starts": int(info["cold_starts"]), "evictions": int(info["evictions"]),
-            "fp64_sequential_est_solves_per_s": solved / seq,
+    for name, ph in phases.items():
+        seq = sum(per_rhs[k[0]] * n for k, n in plans[name])
+        ph["fp64_sequential_est_s"] = seq
+        ph["fp64_sequential_est_solves_per_s"] = ph["rhs"] / seq
+    served = phases[f"rate_{SERVE_RATES[1]:g}x"]
+    return {"value": served["solves_per_s"], "unit": "solves/s", "what": f"Poisson stream at {SERVE_RATES[1]:g}x "
+            "the saturated rate", "p50_ms": served["p50_ms"], "p99_ms": served["p99_ms"],
+            "phases": phases, "operators": len(keys), "sizes": list(SERVE_SIZES), "configs_per_size": SERVE_CONFIGS,
+            "nrhs": "U{1..32}", "tol": TOL, "precision": "mixed, BF16 tensor-core block products",
+            "workers": args.serve_workers, "rhs_block": 32,
+            "hbm_budget_bytes": budget, "demand_bytes_all_resident": int(info["demand_bytes"]),
+            "cold_starts": int(info["cold_starts"]), "evictions": int(info["evictions"]),
             "fp64_seq_ms_per_rhs": {str(k): 1e3 * v for k, v in per_rhs.items()},
-            "precision": "mixed", "sizes": list(SERVE_SIZES), "nrhs": "U{1..32}", "tol": TOL}
+            "field_gen_s": gen_s, "m0_fingerprints_match": fp_ok}
 
 
 def fine_roofline(mg, dev, peaks, peak_kind, Lb=2048, launches=20, warm=3):

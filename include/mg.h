@@ -291,8 +291,12 @@ typedef struct {
  *   flags      MG_COARSE_PROBE_TIMEOUT (tests): before the first cycle every CTA
  *              waits, bounded by `spin`, on a barrier that nothing completes, so
  *              the give-up path runs; the call then returns MG_ETIMEOUT and the
- *              handle stays usable
- *   spin       try_wait rounds before a bounded wait gives up (0: 2^20)
+ *              handle stays usable.  MG_BF16 / MG_F16: every CTA of the batched
+ *              cycle kernel waits so at the start of each cycle (info->timeouts
+ *              = 1); the probe needs the cycle kernel's resident grid (MG_EINVAL
+ *              on coarse grids that run the three-kernel steps)
+ *   spin       try_wait rounds (MG_BF16 / MG_F16: tile-barrier polls) before a
+ *              bounded wait gives up (0: 2^20; 2^18 polls)
  *   iters      host long long[nrhs] or NULL: Krylov steps per right-hand side
  *   converged  host int[nrhs] or NULL
  *   info       host or NULL: the launch shape
@@ -341,6 +345,10 @@ typedef struct {
     long long cold_starts;          /* hierarchies built */
     long long completed;            /* requests finished */
     long long queued_items;         /* right-hand sides waiting for a worker */
+    long long batches;              /* solve calls run by the workers */
+    int max_batch;                  /* most right-hand sides solved together in one call */
+    unsigned long long demand_bytes;/* estimated device bytes of all keys ever requested, i.e.
+                                       what keeping every one of them resident would take */
 } mg_server_info;
 
 /*
@@ -354,6 +362,14 @@ typedef struct {
  * came first.  Hierarchies stay resident (LRU) while the estimated device bytes
  * stay within hbm_budget_bytes (0 = unlimited); a new key waits until an idle
  * hierarchy can be evicted.
+ * With p->precision MG_MIXED_BF16 or MG_MIXED_FP16 a key runs one lockstep block
+ * solve at a time on its hierarchy (no solve contexts): the worker that takes
+ * an item also takes every queued item of the same key and tolerance, from any
+ * request, up to p->rhs_block, and solves them together with tensor-core block
+ * products; items that arrive meanwhile join the next block.  A block gathered
+ * from several requests is staged in a device buffer of the worker (counted in
+ * device_bytes).  Results then depend on the block they ran in only through
+ * rounding: each meets its tolerance either way.
  */
 mg_status mg_server_create(const mg_params* p, unsigned long long hbm_budget_bytes, int workers,
                            mg_server* out);

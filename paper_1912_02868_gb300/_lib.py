@@ -56,6 +56,7 @@ class MGServerInfo(ctypes.Structure):
     _fields_ = [
         ("resident_keys", ctypes.c_int), ("device_bytes", ctypes.c_ulonglong), ("evictions", ctypes.c_longlong),
         ("cold_starts", ctypes.c_longlong), ("completed", ctypes.c_longlong), ("queued_items", ctypes.c_longlong),
+        ("batches", ctypes.c_longlong), ("max_batch", ctypes.c_int), ("demand_bytes", ctypes.c_ulonglong),
     ]
 
 

@@ -90,18 +90,22 @@ mg_status mg_coarse_solve(mg_handle h, int precision, int nrhs, const void* b, v
     if (flags & ~MG_COARSE_PROBE_TIMEOUT) return set_error("unknown flags %d", flags), MG_EINVAL;
     if (precision == MG_BF16 || precision == MG_F16) {  // the batched tensor-core solve
         if (nrhs < 1 || nrhs > 64) return set_error("nrhs must be in [1, 64]"), MG_EINVAL;
-        if (flags) return set_error("flags apply to the cluster kernels only"), MG_EINVAL;
         MG_TRY(device_vectors(b, "b"));
         MG_TRY(device_vectors(x, "x"));
         std::vector<long long> it(nrhs, 0);
-        MG_TRY(coarse_solve_block(H, static_cast<const float2*>(b), static_cast<float2*>(x), nrhs, tol,
-                                  precision == MG_F16, static_cast<cudaStream_t>(stream), it.data()));
+        const mg_status st = coarse_solve_block(H, static_cast<const float2*>(b), static_cast<float2*>(x), nrhs, tol,
+                                                precision == MG_F16, static_cast<cudaStream_t>(stream), it.data(),
+                                                (flags & MG_COARSE_PROBE_TIMEOUT) != 0, (long)spin);
+        if (st != MG_OK && st != MG_ETIMEOUT) return st;
         for (int r = 0; r < nrhs; ++r) {
             if (iters) iters[r] = it[r];
             if (converged) converged[r] = it[r] < (long long)H.p.proj_max_cycles * std::max(H.p.dr_m - H.defl_k, 1);
         }
-        if (info) *info = mg_coarse_info{};
-        return MG_OK;
+        if (info) {
+            *info = mg_coarse_info{};
+            info->timeouts = st == MG_ETIMEOUT ? 1 : 0;
+        }
+        return st;
     }
     if (precision != MG_F64 && precision != MG_F32) return set_error("unknown precision %d", precision), MG_EINVAL;
     if (nrhs < 1 || nrhs > 2 || (nrhs == 2 && precision != MG_F32))

@@ -727,6 +727,17 @@ __global__ void __launch_bounds__(CB_COOP_THREADS, CB_COOP_MINB) k_cb_cycle(CBAr
     unsigned long long acc_t[7] = {0, 0, 0, 0, 0, 0, 0}, t_prev = gtime();
     int steps = 0;
 #endif
+    if (a.probe && threadIdx.x == 0) {  // test probe: a wait that nothing ends gives up
+        const volatile unsigned* never = a.bar + 2 * (NB_MAX / NB_TILE);
+        long it = 0;
+        while (*never == 0u) {
+            if (++it > spin) {
+                atomicExch(err, 1);
+                break;
+            }
+            __nanosleep(32);
+        }
+    }
     if (c == 0 && warp == NRW && lane < NB_TILE) {  // the least squares as the cycle's start left it
         const KState* ks = a.ks + r0 + lane;
         for (int i = 0; i <= MSMAX; ++i) S.g[lane][i] = ks->g[i];

@@ -28,9 +28,11 @@ struct CBArgs {
     float2* h1;          // [nbp][CB_PB] reduced first-pass products
     float2* h2;          // [nbp][CB_PB] reduced second-pass products; slot CB_PB - 1: (h_{j+1,j}, 1 / h_{j+1,j})
     unsigned* ticket;    // [2][nbp / 8] arrivals of the chunks of a tile, per pass (step kernels)
-    unsigned* bar;       // [nbp / 8][2] tile barrier (count, generation) of the cycle kernel
+    unsigned* bar;       // [nbp / 8][2] tile barrier (count, generation) of the cycle kernel, then
+                         // one word that nothing writes (the probe's)
     int spc, nchunks, nbp;
     int coop;            // 1: geometry of the cycle kernel
+    int probe;           // test probe: every CTA first waits (bounded) on the word nothing writes
 };
 
 // chunk size for nsite coarse sites and nbp right-hand sides (nbp % 8 == 0):

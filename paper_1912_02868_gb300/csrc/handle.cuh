@@ -205,9 +205,11 @@ mg_status fine_deflated_solve(Handle& H, const double2* b, double2* x, double to
 // deflation space.  coarse_iters (optional): coarse GMRES-Proj steps of the block.
 mg_status fgmres_solve_block(Handle& H, const double2* B, double2* X, int nb, double tol, bool fp16, cudaStream_t s,
                              int* iters, double* relres, bool* converged, long long* coarse_iters);
-// the batched coarse GMRES-Proj alone (device f, x: [nb][n2] complex64)
+// the batched coarse GMRES-Proj alone (device f, x: [nb][n2] complex64); probe: every
+// CTA of the cycle kernel first waits on a word nothing writes, giving up after
+// `spin` polls (spin 0: the default limit); MG_ETIMEOUT when a wait gave up
 mg_status coarse_solve_block(Handle& H, const float2* f, float2* x, int nb, double tol, bool fp16, cudaStream_t s,
-                             long long* iters);
+                             long long* iters, bool probe = false, long spin = 0);
 // the tensor-core block stencil of grid l alone (device x, y: [nb][n_l] complex64, nb % 8 == 0)
 mg_status apply_block(Handle& H, int l, const float2* x, float2* y, int nb, bool fp16, cudaStream_t s);
 // A solve context of `owner` (capi.cu): same hierarchy and deflation space,

@@ -10,11 +10,17 @@
 //   requests and different lattice sizes overlap on the device, and a request
 //   that arrives while others run is admitted as soon as a worker and, for a
 //   new key, memory are free.
+// * With a block precision (MG_MIXED_BF16 / MG_MIXED_FP16) a key runs one
+//   lockstep block solve at a time on its hierarchy: the worker that takes an
+//   item also takes every queued item of the same key and tolerance, up to
+//   rhs_block, from any request, and solves them together (tensor-core block
+//   products).  Items that arrive while a block runs join the next block.
 // * The deflation space of a new key is built by GMRES-DR on a fixed seeded
 //   right-hand side (not on a request's), so every later solve of that key -
 //   alone or in any mix - runs the same arithmetic and gives the same result.
 // * Nothing here waits on the device except through the library's own calls;
 //   every wait on the host is a condition variable tied to a queue change.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -67,12 +73,20 @@ struct Item {
     int rhs;
 };
 
+// device staging of a block gathered from several requests (one per worker)
+struct Staging {
+    double2* b = nullptr;
+    double2* x = nullptr;
+    size_t cap = 0;  // bytes of each buffer
+};
+
 }  // namespace
 
 struct Server {
     mg_params p{};
     size_t budget = 0;
     int nworkers = 1;
+    bool block = false;  // lockstep block solves (block precisions)
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<Item> queue;
@@ -82,14 +96,19 @@ struct Server {
     bool stop = false;
     unsigned long long next_ticket = 1, tick = 0;
     size_t bytes = 0;
-    long long evictions = 0, completed = 0, cold_starts = 0;
+    long long evictions = 0, completed = 0, cold_starts = 0, batches = 0;
+    std::map<unsigned long long, size_t> demand;  // estimated bytes of every key ever requested
+    int max_batch = 0;
     int device = 0;
 
     void worker_loop();
-    bool pick(Item& it, Entry*& e, mg_handle& ctx, bool& cold, bool& new_ctx);
+    bool pick(std::vector<Item>& batch, Entry*& e, mg_handle& ctx, bool& cold, bool& new_ctx);
+    void take_more(std::vector<Item>& batch);
     void evict_for(size_t need);
-    void finish_item(const Item& it, Entry* e, mg_handle ctx, int iters, double relres, mg_status st,
-                     const std::string& err);
+    void finish_batch(const std::vector<Item>& batch, Entry* e, mg_handle ctx, const int* iters,
+                      const double* relres, mg_status st, const std::string& err);
+    mg_status solve_batch(const std::vector<Item>& batch, Entry* e, mg_handle ctx, Staging& stg, int* iters,
+                          double* relres);
 };
 
 namespace {
@@ -117,7 +136,16 @@ size_t estimate_bytes(const mg_params& p, int Lx, int Lt) {
     // hierarchy (FP64 + FP32 copies) + one set of workspaces, rounded up
     const double s0 = (double)Lx * Lt, s1 = s0 / 16, s2 = s0 / 256;
     const double hier = 24.0 * s0 * 2 + (5 * 576 * 24.0) * (s1 + s2) + 24.0 * 24 * 16 * (s1 + s2 * 12);
-    const double ws = 16.0 * 2 * s0 * (2 * p.fgmres_m + 12) + 16.0 * 24 * s1 * 12 + 16.0 * 24 * s2 * 4 * (p.dr_m + 1);
+    double ws = 16.0 * 2 * s0 * (2 * p.fgmres_m + 12) + 16.0 * 24 * s1 * 12 + 16.0 * 24 * s2 * 4 * (p.dr_m + 1);
+    if (p.precision == MG_MIXED_BF16 || p.precision == MG_MIXED_FP16) {
+        // lockstep block workspaces for rhs_block right-hand sides (rounded up to 8):
+        // FP64 FGMRES basis and vectors, FP32 V-cycle vectors, the coarse bases, and
+        // the 16-bit operator copies of the two coarse grids
+        const double nbp = 8.0 * ((p.rhs_block + 7) / 8);
+        const double per = 16.0 * 2 * s0 * (2 * p.fgmres_m + 4) + 8.0 * 2 * s0 * 2 + 8.0 * 24 * s1 * (p.smooth_steps + 4) +
+                           8.0 * 24 * s2 * (p.dr_m + 4);
+        ws += nbp * per + 4.0 * 5 * 576 * (s1 + s2);
+    }
     return (size_t)((hier + ws) * 1.15) + (8u << 20);
 }
 
@@ -143,10 +171,25 @@ void Server::evict_for(size_t need) {
     }
 }
 
-// Under the lock: the first queued item that can run now.  On success the item
-// is removed from the queue and, unless `cold` or `new_ctx`, ctx is an idle
-// context of e.
-bool Server::pick(Item& it, Entry*& e, mg_handle& ctx, bool& cold, bool& new_ctx) {
+// Under the lock, block mode: append to `batch` the queued items of the same key
+// and tolerance as batch[0], in arrival order, up to rhs_block items.
+void Server::take_more(std::vector<Item>& batch) {
+    const mg_request& r0 = batch[0].req->r;
+    for (auto q = queue.begin(); q != queue.end() && (int)batch.size() < p.rhs_block;) {
+        const mg_request& r = q->req->r;
+        if (r.key == r0.key && r.tol == r0.tol) {
+            batch.push_back(*q);
+            q = queue.erase(q);
+        } else {
+            ++q;
+        }
+    }
+}
+
+// Under the lock: the first queued item that can run now (in block mode with
+// the queued items that join it).  On success the items are removed from the
+// queue and, unless `cold` or `new_ctx`, ctx is an idle context of e.
+bool Server::pick(std::vector<Item>& batch, Entry*& e, mg_handle& ctx, bool& cold, bool& new_ctx) {
     for (auto q = queue.begin(); q != queue.end(); ++q) {
         const mg_request& r = q->req->r;
         auto f = cache.find(r.key);
@@ -175,7 +218,7 @@ bool Server::pick(Item& it, Entry*& e, mg_handle& ctx, bool& cold, bool& new_ctx
             } else if (!e->free_ctx.empty()) {
                 ctx = e->free_ctx.back();
                 e->free_ctx.pop_back();
-            } else if ((int)e->all_ctx.size() + 1 < nworkers) {
+            } else if (!block && (int)e->all_ctx.size() + 1 < nworkers) {
                 const size_t need = estimate_bytes(p, e->Lx, e->Lt) / 4;
                 if (budget && bytes + need > budget) evict_for(need);
                 if (budget && bytes + need > budget) continue;
@@ -184,8 +227,9 @@ bool Server::pick(Item& it, Entry*& e, mg_handle& ctx, bool& cold, bool& new_ctx
                 continue;
             }
         }
-        it = *q;
+        batch.assign(1, *q);
         queue.erase(q);
+        if (block && !cold && !e->failed) take_more(batch);
         e->active += 1;
         e->last_use = ++tick;
         return true;
@@ -193,40 +237,107 @@ bool Server::pick(Item& it, Entry*& e, mg_handle& ctx, bool& cold, bool& new_ctx
     return false;
 }
 
-void Server::finish_item(const Item& it, Entry* e, mg_handle ctx, int iters, double relres, mg_status st,
-                         const std::string& err) {
+void Server::finish_batch(const std::vector<Item>& batch, Entry* e, mg_handle ctx, const int* iters,
+                          const double* relres, mg_status st, const std::string& err) {
     std::lock_guard<std::mutex> lk(mu);
     if (ctx) e->free_ctx.push_back(ctx);
     e->active -= 1;
-    Request& R = *it.req;
-    R.iters[it.rhs] = iters;
-    R.relres[it.rhs] = relres;
-    if (st != MG_OK && R.status == MG_OK) {
-        R.status = st;
-        R.error = err;
+    ++batches;
+    max_batch = std::max(max_batch, (int)batch.size());
+    if (block && e->owner) {  // the block workspaces are allocated by the first block solve
+        const size_t now = handle_device_bytes(e->owner);
+        if (now > e->bytes) {
+            bytes += now - e->bytes;
+            e->bytes = now;
+        }
     }
-    if (--R.remaining == 0) {
-        R.t_done = clk::now();
-        R.done = true;
-        ++completed;
-        cv_done.notify_all();
+    for (size_t i = 0; i < batch.size(); ++i) {
+        const Item& it = batch[i];
+        Request& R = *it.req;
+        R.iters[it.rhs] = iters[i];
+        R.relres[it.rhs] = relres[i];
+        if (st != MG_OK && R.status == MG_OK) {
+            R.status = st;
+            R.error = err;
+        }
+        if (--R.remaining == 0) {
+            R.t_done = clk::now();
+            R.done = true;
+            ++completed;
+            cv_done.notify_all();
+        }
     }
     cv_work.notify_all();
 }
 
+// Solve the items of `batch` (one key, one tolerance) on ctx.  Consecutive
+// right-hand sides of one request are solved in place; a block gathered from
+// several requests goes through the worker's device staging buffers.
+mg_status Server::solve_batch(const std::vector<Item>& batch, Entry* e, mg_handle ctx, Staging& stg, int* iters,
+                              double* relres) {
+    const mg_request& r0 = batch[0].req->r;
+    const long n0 = (long)r0.L_x * r0.L_t * 2;  // complex entries of one right-hand side
+    const int nb = (int)batch.size();
+    cudaStream_t cs = (ctx == e->owner) ? e->ostream : handle_stream(ctx);
+    bool contiguous = true;
+    for (int i = 1; i < nb; ++i)
+        contiguous = contiguous && batch[i].req == batch[0].req && batch[i].rhs == batch[0].rhs + i;
+    if (contiguous) {
+        const double2* b = static_cast<const double2*>(r0.b) + (long)batch[0].rhs * n0;
+        double2* x = static_cast<double2*>(r0.x) + (long)batch[0].rhs * n0;
+        return mg_solve(ctx, b, x, nb, r0.tol, cs, iters, relres, nullptr);
+    }
+    const size_t need = (size_t)nb * n0 * sizeof(double2);
+    if (stg.cap < need) {
+        if (stg.b) cudaFree(stg.b);
+        if (stg.x) cudaFree(stg.x);
+        stg.b = stg.x = nullptr;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            bytes -= std::min(bytes, 2 * stg.cap);
+        }
+        stg.cap = 0;
+        if (cudaMalloc(&stg.b, need) != cudaSuccess || cudaMalloc(&stg.x, need) != cudaSuccess) {
+            (void)cudaGetLastError();
+            if (stg.b) cudaFree(stg.b);
+            stg.b = nullptr;
+            return set_error("out of device memory for a block of %d right-hand sides", nb), MG_ENOMEM;
+        }
+        stg.cap = need;
+        std::lock_guard<std::mutex> lk(mu);
+        bytes += 2 * need;
+    }
+    const size_t vb = (size_t)n0 * sizeof(double2);
+    for (int i = 0; i < nb; ++i) {
+        const mg_request& r = batch[i].req->r;
+        MG_CUDA_TRY(cudaMemcpyAsync(stg.b + (long)i * n0, static_cast<const double2*>(r.b) + (long)batch[i].rhs * n0,
+                                    vb, cudaMemcpyDefault, cs));
+    }
+    mg_status st = mg_solve(ctx, stg.b, stg.x, nb, r0.tol, cs, iters, relres, nullptr);
+    if (st != MG_OK && st != MG_ENOTCONV) return st;
+    for (int i = 0; i < nb; ++i) {
+        const mg_request& r = batch[i].req->r;
+        MG_CUDA_TRY(cudaMemcpyAsync(static_cast<double2*>(r.x) + (long)batch[i].rhs * n0, stg.x + (long)i * n0, vb,
+                                    cudaMemcpyDefault, cs));
+    }
+    MG_CUDA_TRY(cudaStreamSynchronize(cs));
+    return st;
+}
+
 void Server::worker_loop() {
     cudaSetDevice(device);
+    Staging stg;
     while (true) {
-        Item it;
+        std::vector<Item> batch;
         Entry* e = nullptr;
         mg_handle ctx = nullptr;
         bool cold = false, new_ctx = false;
         {
             std::unique_lock<std::mutex> lk(mu);
-            cv_work.wait(lk, [&] { return stop || (!queue.empty() && pick(it, e, ctx, cold, new_ctx)); });
-            if (stop && !it.req) return;
+            cv_work.wait(lk, [&] { return stop || (!queue.empty() && pick(batch, e, ctx, cold, new_ctx)); });
+            if (stop && batch.empty()) break;
         }
-        const mg_request& r = it.req->r;
+        const mg_request& r = batch[0].req->r;
         mg_status st = MG_OK;
         std::string err;
         if (cold) {
@@ -265,6 +376,7 @@ void Server::worker_loop() {
                 e->bytes = handle_device_bytes(h);
                 bytes += e->bytes;
                 ctx = h;  // run this item on the owner
+                if (block) take_more(batch);  // and the items of this key that queued meanwhile
             } else {
                 if (h) mg_destroy(h);
                 if (os) cudaStreamDestroy(os);
@@ -284,22 +396,22 @@ void Server::worker_loop() {
                 ctx = c;
             }
         }
-        int iters = 0;
-        double relres = INFINITY;
+        std::vector<int> iters(batch.size(), 0);
+        std::vector<double> relres(batch.size(), INFINITY);
         if (st == MG_OK && e->failed) {
             st = MG_ECUDA;
             err = "the hierarchy of this key could not be built";
         }
         if (st == MG_OK) {
-            const long n0 = (long)r.L_x * r.L_t;
-            const double2* b = static_cast<const double2*>(r.b) + (long)it.rhs * n0 * 2;
-            double2* x = static_cast<double2*>(r.x) + (long)it.rhs * n0 * 2;
-            cudaStream_t cs = (ctx == e->owner) ? e->ostream : handle_stream(ctx);
-            st = mg_solve(ctx, b, x, 1, r.tol, cs, &iters, &relres, nullptr);
+            st = solve_batch(batch, e, ctx, stg, iters.data(), relres.data());
             if (st != MG_OK && st != MG_ENOTCONV) err = mg_last_error();
         }
-        finish_item(it, e, ctx, iters, relres, st, err);
+        finish_batch(batch, e, ctx, iters.data(), relres.data(), st, err);
     }
+    if (stg.b) cudaFree(stg.b);
+    if (stg.x) cudaFree(stg.x);
+    std::lock_guard<std::mutex> lk(mu);
+    bytes -= std::min(bytes, 2 * stg.cap);
 }
 
 }  // namespace mg
@@ -323,6 +435,7 @@ mg_status mg_server_create(const mg_params* p, unsigned long long hbm_budget_byt
     if (p) S.p = *p;
     S.budget = (size_t)hbm_budget_bytes;
     S.nworkers = workers;
+    S.block = S.p.precision == MG_MIXED_BF16 || S.p.precision == MG_MIXED_FP16;
     if (cudaGetDevice(&S.device) != cudaSuccess) {
         delete sv;
         return set_error("no CUDA device"), MG_ECUDA;
@@ -351,6 +464,7 @@ mg_status mg_server_submit(mg_server sv, const mg_request* r, unsigned long long
         R->ticket = S.next_ticket++;
         S.reqs[R->ticket] = R;
         for (int i = 0; i < r->nrhs; ++i) S.queue.push_back(Item{R, i});
+        S.demand[r->key] = estimate_bytes(S.p, r->L_x, r->L_t);
         *ticket = R->ticket;
     }
     S.cv_work.notify_all();
@@ -406,6 +520,11 @@ mg_status mg_server_stats(mg_server sv, mg_server_info* out) {
     out->cold_starts = S.cold_starts;
     out->completed = S.completed;
     out->queued_items = (long long)S.queue.size();
+    out->batches = S.batches;
+    unsigned long long d = 0;
+    for (const auto& kv : S.demand) d += kv.second;
+    out->demand_bytes = d;
+    out->max_batch = S.max_batch;
     return MG_OK;
 }
 

@@ -89,10 +89,13 @@ struct BatchWS {
     unsigned* ctk = nullptr;                // fused-step tickets
     unsigned* cbar = nullptr;               // tile barriers of the cycle kernel
     bool no_coop = false;                   // the cycle kernel could not be captured: use the step kernels
+    int probe = 0;                          // coarse test probe (mg_coarse_solve): a wait that gives up
+    long spin = 0;                          // polls of a tile barrier before it gives up (0: default)
     long cp_cap = 0;             // entries of cp1 / cp2
     // the captured coarse cycle: graph, its key, and its kernel count
     cudaGraphExec_t cyc_exec = nullptr;
-    int cyc_nb = 0, cyc_k = 0, cyc_fp16 = -1, cyc_coop = -1;
+    int cyc_nb = 0, cyc_k = 0, cyc_fp16 = -1, cyc_coop = -1, cyc_probe = -1;
+    long cyc_spin = -1;
     double cyc_tol = 0.0;
     unsigned long long cyc_kernels = 0;
     cudaStream_t cap = nullptr;
@@ -177,8 +180,8 @@ mg_status batch_alloc(Handle& H, int nbp, bool fp16, cudaStream_t s) {
         MG_TRY(halloc_t(H, &B.ch2, (size_t)nbp * CB_PB));
         MG_TRY(halloc_t(H, &B.ctk, (size_t)2 * NB_MAX / NB_TILE));
         MG_CUDA_TRY(cudaMemsetAsync(B.ctk, 0, 2 * NB_MAX / NB_TILE * sizeof(unsigned), s));
-        MG_TRY(halloc_t(H, &B.cbar, (size_t)2 * NB_MAX / NB_TILE));
-        MG_CUDA_TRY(cudaMemsetAsync(B.cbar, 0, 2 * NB_MAX / NB_TILE * sizeof(unsigned), s));
+        MG_TRY(halloc_t(H, &B.cbar, (size_t)2 * NB_MAX / NB_TILE + 1));
+        MG_CUDA_TRY(cudaMemsetAsync(B.cbar, 0, (2 * NB_MAX / NB_TILE + 1) * sizeof(unsigned), s));
     }
     MG_TRY(halloc_t(H, &B.oflags, (size_t)nbp));
     MG_TRY(halloc_t(H, &B.gates, (size_t)nbp));
@@ -298,10 +301,12 @@ mg_status bcoarse_proj(Handle& H, const float2* f, float2* x, int nb, Gate act, 
     cb.h2 = B.ch2;
     cb.ticket = B.ctk;
     cb.bar = B.cbar;
+    cb.probe = B.probe;
     // the cycle kernel when its grid can be resident at once, else the step kernels
     const bool coop = !B.no_coop && cb_geometry_cycle(cb, (long)cb.Nx * cb.Nt, nb, fp16);
     if (!coop) cb_geometry(cb, (long)cb.Nx * cb.Nt, nb);
-    constexpr long CB_SPIN = 1L << 18;  // polls of a tile barrier before it gives up
+    const long spin = B.spin > 0 ? B.spin : 1L << 18;  // polls of a tile barrier before it gives up
+    if (B.probe && !coop) return set_error("the coarse timeout probe is built into the cycle kernel only"), MG_EINVAL;
     if ((long)nb * CB_PB * CB_MAXCH > B.cp_cap || cb.nchunks > CB_MAXCH || cb.spc > CB_MAXSPC)
         return set_error("coarse block solve: %d coarse sites exceed the fused step's chunking", cb.Nx * cb.Nt), MG_EINVAL;
     // one cycle: projection d = argmin ||W^+ r - H_k d||, x += W_k d, r -= W H_k d,
@@ -317,7 +322,7 @@ mg_status bcoarse_proj(Handle& H, const float2* f, float2* x, int nb, Gate act, 
         launch_cb_gate_init(cb, cs);
         launch_bscale<float>(B.cV, n, B.cr, n, MG_DEVF(B.cks, double, scale), KS_DBLS, n, nb, scale_gate(B.cks, 0),
                              cs);
-        if (coop) (void)launch_cb_cycle(cb, ms, fp16, CB_SPIN, B.count + 1, cs);
+        if (coop) (void)launch_cb_cycle(cb, ms, fp16, spin, B.count + 1, cs);
         else
             for (int jh = 0; jh < ms; ++jh) launch_cb_step(cb, jh, fp16, cs);
         bks_finish(B.cks, nb, cs);
@@ -330,7 +335,7 @@ mg_status bcoarse_proj(Handle& H, const float2* f, float2* x, int nb, Gate act, 
     };
     // the cycle as a CUDA graph, captured once per (block size, deflation size, tolerance, format)
     if (!B.cyc_exec || B.cyc_nb != nb || B.cyc_k != k || B.cyc_tol != tol || B.cyc_fp16 != (fp16 ? 1 : 0) ||
-        B.cyc_coop != (coop ? 1 : 0)) {
+        B.cyc_coop != (coop ? 1 : 0) || B.cyc_probe != B.probe || B.cyc_spin != spin) {
         if (B.cyc_exec) cudaGraphExecDestroy(B.cyc_exec);
         B.cyc_exec = nullptr;
         if (!B.cap) MG_CUDA_TRY(cudaStreamCreateWithFlags(&B.cap, cudaStreamNonBlocking));
@@ -358,6 +363,8 @@ mg_status bcoarse_proj(Handle& H, const float2* f, float2* x, int nb, Gate act, 
         B.cyc_tol = tol;
         B.cyc_fp16 = fp16 ? 1 : 0;
         B.cyc_coop = coop ? 1 : 0;
+        B.cyc_probe = B.probe;
+        B.cyc_spin = spin;
         B.cyc_kernels = kernels;
     }
     for (int i = 0; i < 2; ++i)
@@ -381,8 +388,11 @@ mg_status bcoarse_proj(Handle& H, const float2* f, float2* x, int nb, Gate act, 
         if (hc[2 * (c & 1)] == 0 || gave_up) break;
     }
     if (gave_up) {
+        // every launch has ended (each wait is bounded); the barrier counts may be
+        // left mid-count, so they restart from zero with the error flag
         MG_CUDA_TRY(cudaStreamSynchronize(s));
         MG_CUDA_TRY(cudaMemsetAsync(B.count + 1, 0, sizeof(int), s));
+        MG_CUDA_TRY(cudaMemsetAsync(B.cbar, 0, (2 * NB_MAX / NB_TILE + 1) * sizeof(unsigned), s));
         return set_error("coarse block solve: a tile barrier gave up"), MG_ETIMEOUT;
     }
     return MG_OK;
@@ -533,7 +543,7 @@ mg_status fgmres_solve_block(Handle& H, const double2* Bv, double2* X, int nb, d
 
 // batched coarse GMRES-Proj alone (the C ABI's parity entry): device f, x [nb][n2]
 mg_status coarse_solve_block(Handle& H, const float2* f, float2* x, int nb, double tol, bool fp16, cudaStream_t s,
-                             long long* iters) {
+                             long long* iters, bool probe, long spin) {
     const int nbp = ((nb + NB_TILE - 1) / NB_TILE) * NB_TILE;
     MG_TRY(batch_alloc(H, nbp, fp16, s));
     BatchWS& B = *H.bws;
@@ -545,12 +555,17 @@ mg_status coarse_solve_block(Handle& H, const float2* f, float2* x, int nb, doub
     for (int r = 0; r < nbp; ++r) hf[r] = r < nb ? 1 : 0;
     int* dflags = B.oflags;
     MG_CUDA_TRY(cudaMemcpyAsync(dflags, hf, (size_t)nbp * sizeof(int), cudaMemcpyHostToDevice, s));
-    MG_TRY(bcoarse_proj(H, B.f2, B.x2, nbp, Gate{dflags, 1, 1}, tol, s));
+    B.probe = probe ? 1 : 0;
+    B.spin = spin;
+    const mg_status st = bcoarse_proj(H, B.f2, B.x2, nbp, Gate{dflags, 1, 1}, tol, s);
+    B.probe = 0;
+    B.spin = 0;
+    if (st != MG_OK && st != MG_ETIMEOUT) return st;
     MG_CUDA_TRY(cudaMemcpyAsync(x, B.x2, (size_t)nb * n2 * sizeof(float2), cudaMemcpyDeviceToDevice, s));
     MG_CUDA_TRY(cudaMemcpyAsync(B.pin, B.citers, (size_t)nbp * sizeof(long long), cudaMemcpyDeviceToHost, s));
     MG_CUDA_TRY(cudaStreamSynchronize(s));
     if (iters) std::memcpy(iters, B.pin, (size_t)nb * sizeof(long long));
-    return MG_OK;
+    return st;
 }
 
 // block stencil apply alone (parity entry): device x, y [nb][n_l] complex64, grid l = 1, 2

@@ -189,3 +189,36 @@ def test_block_solve_accuracy_and_edge_cases(mgmod):
             g2.close()
     finally:
         g.close()
+
+
+def test_block_coarse_probe_times_out_and_handle_stays_usable(mgmod):
+    """A tile-barrier wait of the batched cycle kernel that gives up (the probe: a
+    word nothing writes) makes the coarse solve return MG_ETIMEOUT; the barrier
+    state is reset, so the next solve is bitwise the one before the probe, and a
+    whole block solve on the same handle still meets its tolerance."""
+    import torch
+    L, nrhs = 256, 16
+    g, U, m0, h = _handle(mgmod, L)
+    try:
+        n2 = h.size(2)
+        Bc = dev(np.stack([synth.complex_gaussian((n2,), 9300, r) for r in range(nrhs)]), torch.complex64)
+        X0 = torch.zeros((nrhs, n2), dtype=torch.complex64, device="cuda")
+        st0, it0, conv0, _ = mgmod.mg_coarse_solve(g, Bc, X0, 1e-5, mgmod.MG_BF16, nrhs=nrhs)
+        assert st0 == mgmod.MG_OK and all(conv0)
+        Xp = torch.zeros_like(X0)
+        st, _, _, info = mgmod.mg_coarse_solve(g, Bc, Xp, 1e-5, mgmod.MG_BF16, nrhs=nrhs,
+                                               flags=mgmod.MG_COARSE_PROBE_TIMEOUT, spin=64,
+                                               allow=(mgmod.MG_ETIMEOUT,))
+        assert st == mgmod.MG_ETIMEOUT and info["timeouts"] == 1
+        X1 = torch.zeros_like(X0)
+        st1, it1, _, info1 = mgmod.mg_coarse_solve(g, Bc, X1, 1e-5, mgmod.MG_BF16, nrhs=nrhs)
+        assert st1 == mgmod.MG_OK and info1["timeouts"] == 0 and it1 == it0
+        assert torch.equal(X0, X1)
+        B = synth.rhs(L, 0, 40, nrhs=8)
+        X = torch.zeros(B.shape, dtype=torch.complex128, device="cuda")
+        _, iters, relres, _ = mgmod.mg_solve(g, dev(B), X, 8, 1e-8)
+        Xh = host(X)
+        for i in range(8):
+            assert relres[i] <= 1e-8 and _true_relres(U, m0, Xh[i], B[i]) <= 1.0001e-8
+    finally:
+        g.close()

@@ -120,3 +120,69 @@ def test_server_budget_evicts_and_stays_correct(mgmod):
                 assert _true_relres(U, synth.m0_for(r[1], r[2]), x[j], b[j]) <= 1.0001e-8
         info = srv.stats()
         assert info["evictions"] >= 2 and info["resident_keys"] == 1
+
+
+def _kappa(U, m0):
+    """||D|| ||D^-1|| by power iterations (sparse LU for the inverse)."""
+    import scipy.sparse.linalg as spla
+    M = dirac.stencil_sparse(dirac.wilson_stencil(U, m0)).tocsc()
+    lu = spla.splu(M)
+    v = synth.complex_gaussian((M.shape[0],), 99)
+    for _ in range(30):
+        v = lu.solve(lu.solve(v), trans="H")
+        v /= np.linalg.norm(v)
+    inv = np.sqrt(np.linalg.norm(lu.solve(lu.solve(v), trans="H")))
+    u = synth.complex_gaussian((M.shape[0],), 98)
+    for _ in range(30):
+        u = M.conj().T @ (M @ u)
+        u /= np.linalg.norm(u)
+    return np.sqrt(np.linalg.norm(M.conj().T @ (M @ u))) * inv
+
+
+def test_block_server_batches_across_requests(mgmod):
+    """Block precision: queued items of one key from several requests are solved
+    together.  Every result meets the tolerance on the true residual, and a result
+    differs from the same request served alone by at most what two solutions that
+    both meet the tolerance can differ by (kappa (rr_alone + rr_mix))."""
+    reqs = _requests()
+    p = mgmod.default_params(precision=mgmod.MG_MIXED_BF16)
+    alone = []
+    with mgmod.Server(p, workers=3) as srv:
+        for i, r in enumerate(reqs):
+            t, U, b, x = _submit(srv, r, i)
+            st, it, rr, lat = srv.wait(t, r[3])
+            alone.append((x, rr))
+        assert srv.stats()["max_batch"] == max(r[3] for r in reqs)
+    kap = {}
+    with mgmod.Server(p, workers=3) as srv:
+        subs = [_submit(srv, r, i) for i, r in enumerate(reqs)]
+        for (t, U, b, x), r, (xa, rra) in zip(subs, reqs, alone):
+            st, it, rr, lat = srv.wait(t, r[3])
+            m0 = synth.m0_for(r[1], r[2])
+            if r[0] not in kap:
+                kap[r[0]] = _kappa(U, m0)
+            for j in range(r[3]):
+                assert rr[j] <= 1e-8
+                assert _true_relres(U, m0, x[j], b[j]) <= 1.0001e-8
+                assert rel2(x[j], xa[j]) <= kap[r[0]] * (rr[j] + rra[j]), (r, j)
+        info = srv.stats()
+        assert info["completed"] == len(reqs) and info["resident_keys"] == 4
+        # the items of a key queued during its cold start ran as one gathered block
+        assert info["max_batch"] > max(r[3] for r in reqs)
+        assert info["batches"] < sum(r[3] for r in reqs)
+
+
+def test_block_server_budget_evicts_and_stays_correct(mgmod):
+    p = mgmod.default_params(precision=mgmod.MG_MIXED_FP16, rhs_block=16)
+    reqs = [(1032, 32, 0, 2), (2032, 32, 1, 3), (1032, 32, 0, 1), (2032, 32, 1, 1)]
+    with mgmod.Server(p, hbm_budget_bytes=1, workers=2) as srv:  # room for one hierarchy at a time
+        outs = []
+        for i, r in enumerate(reqs):
+            t, U, b, x = _submit(srv, r, i)
+            st, it, rr, lat = srv.wait(t, r[3])
+            outs.append((U, b, x, r))
+        for U, b, x, r in outs:
+            for j in range(r[3]):
+                assert _true_relres(U, synth.m0_for(r[1], r[2]), x[j], b[j]) <= 1.0001e-8
+        info = srv.stats()
+        assert info["evictions"] >= 2 and info["resident_keys"] == 1
