@@ -55,10 +55,17 @@ def parse():
     ap.add_argument("--no-partial", action="store_true", help="skip the partial-intermediate-solve variant")
     ap.add_argument("--no-batching", action="store_true", help="skip the 64-right-hand-side batching sample")
     ap.add_argument("--no-scale", action="store_true", help="skip the 1024^2 x 16-right-hand-side block solve")
-    ap.add_argument("--serve-requests", type=int, default=64, help="requests per phase of the served stream")
-    ap.add_argument("--serve-budget-gib", type=float, default=48.0,
+    ap.add_argument("--serve-requests", type=int, default=48, help="requests per phase of the served stream")
+    ap.add_argument("--serve-budget-gib", type=float, default=96.0,
                     help="HBM budget of the server's resident hierarchies (below the stream's total need)")
     ap.add_argument("--serve-workers", type=int, default=8)
+    ap.add_argument("--micro", choices=["bstencil", "coarse_block"], default=None,
+                    help="time one kernel alone (the target of the ncu captures) instead of the benchmark")
+    ap.add_argument("--micro-lattice", type=int, default=256)
+    ap.add_argument("--micro-nrhs", default="8,64", help="comma-separated block sizes")
+    ap.add_argument("--micro-reps", type=int, default=10)
+    ap.add_argument("--micro-level", type=int, default=1, help="grid of the block stencil (1 or 2)")
+    ap.add_argument("--micro-fp16", action="store_true", help="FP16 instead of BF16 operator")
     return ap.parse_args()
 
 
@@ -773,8 +780,67 @@ def run_native(args):
     print(json.dumps(line), flush=True)
 
 
+def run_micro(args):
+    """One kernel alone, one JSON line per block size.  bstencil: the tensor-core
+    block stencil of grid 1 or 2 (L2 flushed before every launch; algorithmic
+    bytes and flops per launch as in the kernel table).  coarse_block: one batched
+    coarse GMRES-Proj solve of nrhs right-hand sides to 1e-8 on the coarsest grid
+    (the cycle kernel), after the deflation-building first solve; time per
+    lockstep Arnoldi step."""
+    import numpy as np
+    import torch
+    import paper_1912_02868_gb300 as mg
+    import synth
+    dev = torch.device("cuda:0")
+    Lm = args.micro_lattice
+    prec = mg.MG_MIXED_FP16 if args.micro_fp16 else mg.MG_MIXED_BF16
+    op = mg.MG_F16 if args.micro_fp16 else mg.MG_BF16
+    U = synth.gauge_field(Lm, 0, gpu=True)
+    h = mg.mg_setup(torch.from_numpy(U).to(dev), Lm, Lm, synth.m0_for(Lm, 0), params=mg.default_params(precision=prec),
+                    starts0=torch.from_numpy(synth.nullvec_starts(Lm, 0, 0, 12, Lm * Lm * 2)).to(dev),
+                    starts1=torch.from_numpy(synth.nullvec_starts(Lm, 0, 1, 12, (Lm // 4) ** 2 * 24)).to(dev))
+    try:
+        for nb in [int(v) for v in args.micro_nrhs.split(",")]:
+            if args.micro == "bstencil":
+                nx, nt, dof = mg.mg_level_shape(h, args.micro_level)
+                n1, s1 = nx * nt * dof, nx * nt
+                x = torch.complex(torch.randn((nb, n1), device=dev), torch.randn((nb, n1), device=dev))
+                y = torch.empty_like(x)
+                t = timed_launches(torch, dev, lambda: mg.mg_apply_block(h, args.micro_level, x, y, nb, op),
+                                   launches=args.micro_reps, warm=1)
+                nbytes = 5 * 576 * 4 * s1 + 2 * nb * n1 * 8
+                out = {"kernel": "k_bstencil_mma", "level": args.micro_level, "sites": s1, "nrhs": nb,
+                       "us": t * 1e6, "GB_per_s": nbytes / t / 1e9, "TFLOP_per_s": 46080 * nb * s1 / t / 1e12,
+                       "bytes": nbytes}
+            else:
+                b = synth.rhs(Lm, 0, 0)[0]
+                mg.mg_solve(h, torch.from_numpy(b).to(dev), torch.zeros(b.shape, dtype=torch.complex128, device=dev),
+                            1, TOL)
+                n2 = (Lm // 16) ** 2 * 24
+                Bc = torch.from_numpy(np.stack([synth.complex_gaussian((n2,), 77, r) for r in range(nb)])).to(
+                    torch.complex64).to(dev)
+                Xc = torch.zeros_like(Bc)
+                ms = []
+                for i in range(1 + args.micro_reps):
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    _, it, _, _ = mg.mg_coarse_solve(h, Bc, Xc, TOL, op, nrhs=nb)
+                    torch.cuda.synchronize()
+                    if i:
+                        ms.append(time.perf_counter() - t0)
+                t = float(np.mean(ms))
+                out = {"kernel": "k_cb_cycle", "coarse_sites": (Lm // 16) ** 2, "nrhs": nb, "ms": t * 1e3,
+                       "steps": int(max(it)), "us_per_step": t * 1e6 / max(it)}
+            print(json.dumps(out), flush=True)
+    finally:
+        h.close()
+
+
 def main():
     args = parse()
+    if args.micro:
+        run_micro(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -23,6 +23,8 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <mutex>
+#include <vector>
 
 #include "batch.cuh"
 #include "coarse_block.cuh"
@@ -154,9 +156,10 @@ struct CBSmem {
     WarpRed red[NB_TILE + 1];
 };
 
-// dynamic shared memory of the cycle kernel (CB_WPR warps per right-hand side)
+// dynamic shared memory of the cycle kernel (CB_WPR warps per right-hand side);
+// it is followed by w of the chunk's sites, NB_TILE rows of spc * NDOF entries
+// (sized at launch, so larger coarse grids can take larger chunks)
 struct CBCycleSmem {
-    float2 ws[NB_TILE][CB_MAXSPC * NDOF];
     float2 hs[NB_TILE * CB_WPR][MAXI];
     float2 h1[NB_TILE][MAXI];      // chunk 0: first-pass products kept for the push
     float hn[NB_TILE];
@@ -351,7 +354,7 @@ __device__ __forceinline__ void phase_apply(const CBArgs& a, int jh, int r0, int
 // directions to registers, all issued at once: one memory latency per site.
 template <bool F16>
 __device__ __forceinline__ void phase_apply_staged(const CBArgs& a, int jh, int r0, int s0, int ns, unsigned wmask,
-                                                   float2 (*ws)[CB_MAXSPC * NDOF], uint4* abuf, int nwarps) {
+                                                   float2* ws, int wst, uint4* abuf, int nwarps) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gq = lane >> 2, t = lane & 3, p = gq & 1;
     const float2* X = a.V + (long)jh * a.row;
@@ -412,7 +415,7 @@ __device__ __forceinline__ void phase_apply_staged(const CBArgs& a, int jh, int 
             for (int q = 0; q < 2; ++q) {
                 const int rl = 2 * t + q;
                 const float2 v = q ? v1 : v0;
-                ws[rl][ls * NDOF + row] = v;
+                ws[rl * wst + ls * NDOF + row] = v;
                 if ((wmask >> rl) & 1u) Wt[(long)(r0 + rl) * a.n + (long)s * NDOF + row] = v;
             }
         }
@@ -719,6 +722,8 @@ __global__ void __launch_bounds__(CB_COOP_THREADS, CB_COOP_MINB) k_cb_cycle(CBAr
     const int r = r0 + rl;
     const int slot = c * CB_WPR + part, nslot = a.nchunks * CB_WPR;
     const int e0 = part * 32 + lane, es = 32 * CB_WPR;
+    const int wst = a.spc * NDOF;
+    float2* wsb = reinterpret_cast<float2*>(cb_smem + sizeof(CBCycleSmem));
 #ifdef CB_PHASE_CLOCKS
     __shared__ unsigned clk_s;
     if (threadIdx.x == 0) clk_s = (c == 0 && tile == 0) ? atomicAdd(&cb_clock_launches, 1u) < 3 : 0;
@@ -755,13 +760,13 @@ __global__ void __launch_bounds__(CB_COOP_THREADS, CB_COOP_MINB) k_cb_cycle(CBAr
         const int* gate = a.gbuf + (jh & 1) * a.nbp;
         const bool spec_on = rw && ((spec >> rl) & 1u);
         // phase 1: w = A v_jh, partial sums of V^+ w (speculative for step jh > 0)
-        if (rw) phase_apply_staged<F16>(a, jh, r0, s0, ns, spec, S.ws, S.abuf[warp], NRW);
+        if (rw) phase_apply_staged<F16>(a, jh, r0, s0, ns, spec, wsb, wst, S.abuf[warp], NRW);
         else if (jh > 0 && warp == NRW && c == 0 && lane < NB_TILE &&
                  __ldcg(a.gbuf + ((jh - 1) & 1) * a.nbp + r0 + lane) == jh - 1)
             push_cycle(a, S, lane, r0 + lane, jh - 1, S.hs[lane]);  // warp `lane` (part 0) holds h2
         __syncthreads();
         CB_STAMP(6);
-        if (spec_on) CB_DISPATCH(jh, (phase_gram1<JB>(a, jh, r, slot, s0, ne, e0, es, S.ws[rl], S.red[warp])));
+        if (spec_on) CB_DISPATCH(jh, (phase_gram1<JB>(a, jh, r, slot, s0, ne, e0, es, wsb + rl * wst, S.red[warp])));
         CB_STAMP(0);
         tile_sync(bar, a.nchunks, spin, err);
         CB_STAMP(1);
@@ -842,6 +847,19 @@ void cb_geometry(CBArgs& a, long nsite, int nbp) {
     a.coop = 0;
 }
 
+// dynamic shared memory of the cycle kernel for chunks of spc sites
+size_t cb_cycle_smem(long spc) { return sizeof(CBCycleSmem) + (size_t)NB_TILE * spc * NDOF * sizeof(float2); }
+// the most the device allows one CTA (opt-in), which bounds spc
+int cb_cycle_smem_max() {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+                                                 cudaSuccess) {
+        (void)cudaGetLastError();
+        return (int)cb_cycle_smem(CB_MAXSPC);
+    }
+    return v;
+}
+
 // shared memory of every coarse block kernel, allowed once per device
 mg_status cb_configure() {
     static bool done[64] = {};
@@ -854,36 +872,82 @@ mg_status cb_configure() {
     MG_CUDA_TRY(cudaFuncSetAttribute(k_cb_apply_gram<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
     MG_CUDA_TRY(cudaFuncSetAttribute(k_cb_update_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
     MG_CUDA_TRY(cudaFuncSetAttribute(k_cb_update_push, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-    const int smc = (int)sizeof(CBCycleSmem);
+    const int smc = cb_cycle_smem_max();
     MG_CUDA_TRY(cudaFuncSetAttribute(k_cb_cycle<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smc));
     MG_CUDA_TRY(cudaFuncSetAttribute(k_cb_cycle<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smc));
     done[dev] = true;
     return MG_OK;
 }
 
+namespace {
+bool cb_geometry_cycle_uncached(CBArgs& a, long nsite, int nbp, bool fp16);
+}
+
+// cb_geometry_cycle_uncached per (device, coarse sites, block, format), computed
+// once (its occupancy queries would otherwise cost host time every coarse solve)
 bool cb_geometry_cycle(CBArgs& a, long nsite, int nbp, bool fp16) {
-    const int ntiles = nbp / NB_TILE;
-    int per_sm = 0;
-    if (cb_configure() != MG_OK) return false;
-    const size_t sm = sizeof(CBCycleSmem);
-    cudaError_t e = fp16 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cb_cycle<true>, CB_COOP_THREADS, sm)
-                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cb_cycle<false>, CB_COOP_THREADS, sm);
-    if (e != cudaSuccess || per_sm < 1) {
+    struct Entry {
+        int dev;
+        long nsite;
+        int nbp;
+        bool fp16, ok;
+        int spc, nchunks;
+    };
+    static std::mutex mu;
+    static std::vector<Entry> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
         (void)cudaGetLastError();
         return false;
     }
-    const long resident = (long)per_sm * sm_count();
-    // the fewest sites per chunk whose grid is resident at once
-    long spc = (nsite * ntiles + resident - 1) / resident;
-    spc = std::max(1L, spc);
-    const long nch = (nsite + spc - 1) / spc;
-    if (spc > CB_MAXSPC || nch * CB_WPR > CB_MAXCH || nch * ntiles > resident) return false;
-    a.spc = (int)spc;
-    a.nchunks = (int)nch;
-    a.nbp = nbp;
-    a.coop = 1;
-    return true;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        for (const Entry& e : cache)
+            if (e.dev == dev && e.nsite == nsite && e.nbp == nbp && e.fp16 == fp16) {
+                if (!e.ok) return false;
+                a.spc = e.spc;
+                a.nchunks = e.nchunks;
+                a.nbp = nbp;
+                a.coop = 1;
+                return true;
+            }
+    }
+    const bool ok = cb_geometry_cycle_uncached(a, nsite, nbp, fp16);
+    std::lock_guard<std::mutex> lock(mu);
+    cache.push_back(Entry{dev, nsite, nbp, fp16, ok, ok ? a.spc : 0, ok ? a.nchunks : 0});
+    return ok;
 }
+
+namespace {
+bool cb_geometry_cycle_uncached(CBArgs& a, long nsite, int nbp, bool fp16) {
+    const int ntiles = nbp / NB_TILE;
+    if (cb_configure() != MG_OK) return false;
+    const size_t smax = (size_t)cb_cycle_smem_max();
+    // the fewest sites per chunk whose grid is resident at once; the shared memory
+    // of w grows with the chunk, so the resident count is queried per candidate
+    for (long spc = std::max(1L, (nsite * ntiles + (long)sm_count() * 4 - 1) / ((long)sm_count() * 4)); spc <= nsite;
+         ++spc) {
+        const size_t sm = cb_cycle_smem(spc);
+        if (sm > smax) return false;
+        const long nch = (nsite + spc - 1) / spc;
+        if (nch * CB_WPR > CB_MAXCH) continue;
+        int per_sm = 0;
+        cudaError_t e = fp16 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cb_cycle<true>, CB_COOP_THREADS, sm)
+                             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cb_cycle<false>, CB_COOP_THREADS, sm);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            return false;
+        }
+        if (per_sm < 1 || nch * ntiles > (long)per_sm * sm_count()) continue;
+        a.spc = (int)spc;
+        a.nchunks = (int)nch;
+        a.nbp = nbp;
+        a.coop = 1;
+        return true;
+    }
+    return false;
+}
+}  // namespace
 
 void launch_cb_gate_init(const CBArgs& a, cudaStream_t s) {
     k_cb_gate_init<<<(a.nbp + 63) / 64, 64, 0, s>>>(a);
@@ -909,7 +973,7 @@ mg_status launch_cb_cycle(const CBArgs& a, int ms, bool fp16, long spin, int* er
     MG_TRY(cb_configure());
     cfg.gridDim = dim3(a.nchunks, a.nbp / NB_TILE);
     cfg.blockDim = dim3(CB_COOP_THREADS);
-    cfg.dynamicSmemBytes = sizeof(CBCycleSmem);
+    cfg.dynamicSmemBytes = cb_cycle_smem(a.spc);
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 1;

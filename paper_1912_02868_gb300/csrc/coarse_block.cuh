@@ -13,7 +13,7 @@ constexpr int CB_THREADS = 256;
 #endif
 constexpr int CB_WPR = CB_WPR_DEF;     // the cycle kernel's warps per right-hand side
 constexpr int CB_COOP_THREADS = (NB_TILE * CB_WPR + 1) * 32;  // and one pushing warp
-constexpr int CB_MAXSPC = 16;   // coarse sites per chunk
+constexpr int CB_MAXSPC = 16;   // coarse sites per chunk of the step kernels (the cycle kernel sizes its own)
 
 struct CBArgs {
     const unsigned* Af;  // coarsest operator in MMA fragment order (launch_pack_frag)

@@ -307,7 +307,7 @@ mg_status bcoarse_proj(Handle& H, const float2* f, float2* x, int nb, Gate act, 
     if (!coop) cb_geometry(cb, (long)cb.Nx * cb.Nt, nb);
     const long spin = B.spin > 0 ? B.spin : 1L << 18;  // polls of a tile barrier before it gives up
     if (B.probe && !coop) return set_error("the coarse timeout probe is built into the cycle kernel only"), MG_EINVAL;
-    if ((long)nb * CB_PB * CB_MAXCH > B.cp_cap || cb.nchunks > CB_MAXCH || cb.spc > CB_MAXSPC)
+    if ((long)nb * CB_PB * CB_MAXCH > B.cp_cap || cb.nchunks > CB_MAXCH || (!coop && cb.spc > CB_MAXSPC))
         return set_error("coarse block solve: %d coarse sites exceed the fused step's chunking", cb.Nx * cb.Nt), MG_EINVAL;
     // one cycle: projection d = argmin ||W^+ r - H_k d||, x += W_k d, r -= W H_k d,
     // then one GMRES(ms) cycle from r, x += V d, r = V rho; every kernel gated per
