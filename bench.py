@@ -234,6 +234,24 @@ def fine_roofline(mg, dev, peaks, peak_kind, Lb=2048, launches=20, warm=3):
             "l2": "flushed before every launch", "peak_source": peak_kind}
 
 
+def l2_copy_rate(torch, dev, mb=24, reps=50):
+    """Aggregate L2-resident copy rate (GB/s, bytes read + written): a 24 MB
+    tensor copied into another, both held in L2 (126 MB) across the timed
+    copies."""
+    x = torch.empty(mb << 20, dtype=torch.uint8, device=dev).fill_(1)
+    y = torch.empty_like(x)
+    for _ in range(5):
+        y.copy_(x)
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        y.copy_(x)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return 2 * (mb << 20) * reps / (e0.elapsed_time(e1) / 1e3) / 1e9
+
+
 def timed_launches(torch, dev, fn, launches=10, warm=3):
     """Mean CUDA-event time (s) of fn() on the current stream, L2 flushed (a 256 MB
     write) before every launch."""
@@ -330,6 +348,15 @@ def run_scale(mg, torch, np, dev, peaks, peak_kind, nrhs=16, Ls=1024):
 def dist_env():
     from paper_1912_02868_gb300 import replicas
     return replicas.rank_env()
+
+
+def profile_of(name):
+    """Figures of a committed ncu summary (profiles/*.json), {} when absent."""
+    path = os.path.join(ROOT, "profiles", name)
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f)
+    return {}
 
 
 def measured_peaks():
@@ -580,16 +607,12 @@ def run_native(args):
     c_bytes = steps_per_launch * step_bytes
     c_ach = c_bytes / c_avg / 1e9
 
-    def traffic_of(name):
-        tpath = os.path.join(ROOT, "profiles", name)
-        if os.path.exists(tpath):
-            with open(tpath) as f:
-                return json.load(f).get("dram_bytes_per_launch")
-        return None
-    # share of the ten solve streams' time spent in the coarse kernel (the timing pass)
-    share = (c_ms / (nconf * kt["wall_ms"])) if kt.get("wall_ms") else None
+    # share of the steady-state GPU time from the committed ncu launch list (cold,
+    # serialised launches: the share, not the absolute times, carries over)
+    share = profile_of("coarse_proj_f32_256.json").get("share_of_steady_state_gpu_time")
     roofline = {"bound": "hbm", "achieved": c_ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": c_ach / peaks["hbm_gbs"], "traffic": traffic_of("coarse_proj_f32_256.json"),
+                "frac": c_ach / peaks["hbm_gbs"],
+                "traffic": profile_of("coarse_proj_f32_256.json").get("dram_bytes_per_launch"),
                 "kernel": "k_coarse_proj<float> (whole coarse GMRES-Proj solve, 16^2 x 24, FP16 operator, "
                           "cluster of 16 CTAs)",
                 "bytes_per_launch": c_bytes, "steps_per_launch": steps_per_launch,
@@ -598,6 +621,24 @@ def run_native(args):
                 "note": "latency-bound: each Krylov step is two DSMEM reductions and a neighbour exchange, "
                         "counted on mbarriers; the stencil operand (5.9 MB) is L2-resident, so HBM is not the "
                         "binding limit"}
+    # second bound: per Arnoldi step each of the 16 CTAs reads its two L2-streamed
+    # FP16 operator directions (16 sites x 2 x 576 x 4 B) from L2, and from shared
+    # memory the three held directions plus the basis rows of the two CGS2 passes
+    # (2 x (ms + 1) / 2 rows of 16 x 24 complex64 on average over a cycle)
+    l2_total = l2_copy_rate(torch, dev)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    l2_sm = l2_total / sms
+    smem_sm = 128 * 2.07  # GB/s per SM: 128 B per cycle at the maximum SM clock (nominal)
+    ms_c = max(H_DR_M - 10, 1)
+    l2_b = 16 * 2 * 576 * 4
+    sm_b = 16 * 3 * 576 * 4 + (ms_c + 1) * 16 * 24 * 8
+    t_floor = max(l2_b / (l2_sm * 1e9), sm_b / (smem_sm * 1e9))
+    roofline["second_bound"] = {
+        "what": "per-SM L2 and shared-memory rates; step floor = max(L2 bytes / L2 rate, SMEM bytes / SMEM rate)",
+        "l2_bytes_per_cta_step": l2_b, "smem_bytes_per_cta_step": sm_b,
+        "l2_gbs_per_sm": l2_sm, "l2_source": f"L2-resident copy over all {sms} SMs (torch), divided by the SM count",
+        "smem_gbs_per_sm": smem_sm, "smem_source": "nominal 128 B/cycle at 2.07 GHz",
+        "floor_us_per_step": t_floor * 1e6, "frac": t_floor * 1e6 / roofline["us_per_step"]}
     # the bandwidth-bound kernel of the V-cycle: the intermediate-grid 24x24 block stencil (FP32)
     s1 = (L // 4) ** 2
     bytes_per_launch = (5 * 576 + 2 * 24) * 8 * s1  # blocks + input + output, complex64
@@ -605,7 +646,8 @@ def run_native(args):
     avg_s = kt_ms / 1e3 / max(kt_n, 1)
     achieved = bytes_per_launch / avg_s / 1e9
     stencil_roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                        "frac": achieved / peaks["hbm_gbs"], "traffic": traffic_of("stencil_f32_256.json"),
+                        "frac": achieved / peaks["hbm_gbs"],
+                        "traffic": profile_of("stencil_f32_256.json").get("dram_bytes_per_launch"),
                         "kernel": "k_stencil_f32 (intermediate grid, 64^2 x 24)",
                         "bytes_per_launch": bytes_per_launch, "avg_launch_us": avg_s * 1e6, "launches": kt_n,
                         "peak_source": peak_kind}
@@ -692,7 +734,9 @@ def run_native(args):
                 step_bytes = (5 * 576 * 4) * (L // 16) ** 2 + 64 * (2 + ms_cyc + 1) * n2 * 8
                 ach = step_bytes * steps / (cms / 1e3) / 1e9
                 block_roofline = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                                  "frac": ach / peaks["hbm_gbs"], "traffic": None,
+                                  "frac": ach / peaks["hbm_gbs"],
+                                  "traffic": profile_of("cb_cycle_bf16_256_64rhs.json").get("dram_bytes_per_step"),
+                                  "traffic_unit": "bytes per lockstep step",
                                   "kernel": "k_cb_cycle<bf16> (batched coarse GMRES-Proj, 16^2 x 24, 64 RHS, "
                                             "one cooperative kernel per GMRES cycle)",
                                   "us_per_step": 1e3 * cms / steps, "steps": steps, "bytes_per_step": step_bytes,
