@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--no-partial", action="store_true", help="skip the partial-intermediate-solve variant")
     ap.add_argument("--no-batching", action="store_true", help="skip the 64-right-hand-side batching sample")
     ap.add_argument("--no-scale", action="store_true", help="skip the 1024^2 x 16-right-hand-side block solve")
-    ap.add_argument("--serve-requests", type=int, default=48, help="requests per phase of the served stream")
+    ap.add_argument("--serve-requests", type=int, default=32, help="requests per phase of the served stream")
     ap.add_argument("--serve-budget-gib", type=float, default=96.0,
                     help="HBM budget of the server's resident hierarchies (below the stream's total need)")
     ap.add_argument("--serve-workers", type=int, default=8)
@@ -66,6 +66,11 @@ def parse():
     ap.add_argument("--micro-reps", type=int, default=10)
     ap.add_argument("--micro-level", type=int, default=1, help="grid of the block stencil (1 or 2)")
     ap.add_argument("--micro-fp16", action="store_true", help="FP16 instead of BF16 operator")
+    ap.add_argument("--study", choices=["table1", "massgap"], default=None,
+                    help="counter study of the paper's Section 3 instead of the benchmark")
+    ap.add_argument("--study-sizes", default="64,128,256", help="the paper's lattice sizes")
+    ap.add_argument("--study-gaps", default="1e-1,1e-2,1e-3,1e-4")
+    ap.add_argument("--study-configs", type=int, default=2)
     return ap.parse_args()
 
 
@@ -147,6 +152,10 @@ def run_serving(mg, torch, np, dev, rank):
     srv = mg.Server(params, hbm_budget_bytes=budget, workers=args.serve_workers)
     phases, plans = {}, {}
     try:
+        # cold starts first: one single-right-hand-side request per operator, so the
+        # saturated phase measures solving rather than set-up (the budget still evicts)
+        plans["warm"] = [(k, 1) for k in keys]
+        warm = run_phase(srv, plans["warm"], None, 300000)
         plans["saturated"] = plan_of(nreq)
         sat = run_phase(srv, plans["saturated"], None, 100000)
         phases["saturated"] = sat
@@ -183,6 +192,7 @@ def run_serving(mg, torch, np, dev, rank):
         seq = sum(per_rhs[k[0]] * n for k, n in plans[name])
         ph["fp64_sequential_est_s"] = seq
         ph["fp64_sequential_est_solves_per_s"] = ph["rhs"] / seq
+    phases["cold_start"] = warm
     served = phases[f"rate_{SERVE_RATES[1]:g}x"]
     return {"value": served["solves_per_s"], "unit": "solves/s", "what": f"Poisson stream at {SERVE_RATES[1]:g}x "
             "the saturated rate", "p50_ms": served["p50_ms"], "p99_ms": served["p99_ms"],
@@ -824,6 +834,108 @@ def run_native(args):
     print(json.dumps(line), flush=True)
 
 
+def study_methods(mg):
+    """mg_params overrides of the six methods of the paper's Table 1."""
+    return {
+        "deflated_mg_partial": dict(partial_tol=0.2),
+        "deflated_mg": dict(),
+        # GMRES-DR(30,10) on the fine grid near criticality needs far more cycles than
+        # the coarse grid's limits allow (the paper used m = 200 there for that reason)
+        "gmres_dr": dict(method=mg.MG_METHOD_FINE_DEFLATION, dr_max_cycles=20000, dr_stall_cycles=1000),
+        "nondeflated_mg_partial": dict(coarse_solver=mg.MG_COARSE_CGNE, partial_tol=0.2),
+        "cgne": dict(method=mg.MG_METHOD_FINE_CGNE),
+        "nondeflated_mg": dict(coarse_solver=mg.MG_COARSE_CGNE),
+    }
+
+
+def run_study(args):
+    """Counter studies of the paper's Section 3 on the synthetic configurations,
+    FP64, one Z(4) right-hand side (the paper's noise) per configuration and
+    method, first solve of a fresh handle (the deflated methods build their
+    space in it), tol 1e-8.  The mass gap g sets m0 = g - Re lambda_min(D(0)) from
+    the tuned table; only configurations whose leftmost eigenvalue is real are
+    used, so min |lambda(D)| = g.
+      table1: fine-equivalent Mvps (Eq. 1) against lattice size at g = 1e-4 for
+              the six methods of Table 1, and the fitted power alpha in
+              Mvps = size^alpha (least squares on log-log, size = L^2 sites;
+              alpha per L is twice that);
+      massgap: at 64^2, 128^2, 256^2 and g = 1e-1 .. 1e-4: fine Mvps and the
+              average coarse and intermediate Mvps per outer iteration (Figs. 1
+              and 4), deflated and non-deflated, with and without the partial
+              intermediate solve."""
+    import numpy as np
+    import torch
+    import paper_1912_02868_gb300 as mg
+    import synth
+    dev = torch.device("cuda:0")
+    table = synth.m0_table()["entries"]
+    methods = study_methods(mg)
+
+    def real_configs(L, count):
+        out = []
+        for c in range(SERVE_CONFIGS):
+            e = table.get(f"{L}:{c}")
+            if e is not None and abs(e.get("lambda_min_im", 1.0)) < 1e-6:
+                out.append((c, e["lambda_min_re"]))
+            if len(out) == count:
+                break
+        return out
+
+    def solve_once(L, c, lam, gap, over):
+        U = torch.from_numpy(synth.gauge_field(L, c, gpu=True)).to(dev)
+        p = mg.default_params(precision=mg.MG_FP64, cgne_max_iters=400000, **over)
+        h = mg.mg_setup(U, L, L, gap - lam, params=p,
+                        starts0=torch.from_numpy(synth.nullvec_starts(L, c, 0, 12, L * L * 2)).to(dev),
+                        starts1=torch.from_numpy(synth.nullvec_starts(L, c, 1, 12, (L // 4) ** 2 * 24)).to(dev))
+        try:
+            b = torch.from_numpy(synth.z4_noise((L, L, 2), 0x5A34, L, c)).to(dev)
+            x = torch.zeros_like(b)
+            t0 = time.perf_counter()
+            st, it, rr, sd = mg.mg_solve(h, b, x, 1, TOL, allow_notconv=True)
+            torch.cuda.synchronize()
+            return {"L": L, "config": c, "gap": gap, "outer": it[0], "relres": rr[0],
+                    "fine_equiv_mvps": sd["fine_equiv_mvps"], "mvps": list(sd["mvps"]),
+                    "coarse_iters": sd["coarse_iters"], "s": time.perf_counter() - t0}
+        finally:
+            h.close()
+
+    out = {"study": args.study, "precision": "f64", "rhs": "Z(4) noise, one per configuration", "tol": TOL}
+    if args.study == "table1":
+        sizes = [int(v) for v in args.study_sizes.split(",")]
+        runs, fits = [], {}
+        for name, over in methods.items():
+            per_size = []
+            for L in sizes:
+                rs = [solve_once(L, c, lam, 1e-4, over) for c, lam in real_configs(L, args.study_configs)]
+                runs += [dict(r, method=name) for r in rs]
+                per_size.append(float(np.mean([r["fine_equiv_mvps"] for r in rs])))
+            xv = np.log(np.array(sizes, dtype=float) ** 2)
+            yv = np.log(np.array(per_size))
+            A = np.stack([xv, np.ones_like(xv)], axis=1)
+            coef, res, _, _ = np.linalg.lstsq(A, yv, rcond=None)
+            dof = max(len(sizes) - 2, 1)
+            s2 = float(np.sum((yv - A @ coef) ** 2)) / dof
+            se = float(np.sqrt(s2 * np.linalg.inv(A.T @ A)[0, 0]))
+            fits[name] = {"alpha_volume": float(coef[0]), "alpha_volume_se": se, "alpha_per_L": 2 * float(coef[0]),
+                          "mean_fine_equiv_mvps": dict(zip(map(str, sizes), per_size))}
+        out.update({"gap": 1e-4, "sizes": sizes, "fits": fits, "runs": runs})
+    else:
+        sizes = [int(v) for v in args.study_sizes.split(",")]
+        gaps = [float(v) for v in args.study_gaps.split(",")]
+        runs = []
+        for name in ("deflated_mg", "nondeflated_mg", "deflated_mg_partial", "nondeflated_mg_partial"):
+            for L in sizes:
+                for gap in gaps:
+                    for c, lam in real_configs(L, args.study_configs):
+                        r = solve_once(L, c, lam, gap, methods[name])
+                        r["method"] = name
+                        r["coarse_mvps_per_outer"] = r["mvps"][2] / max(r["outer"], 1)
+                        r["intermediate_mvps_per_outer"] = r["mvps"][1] / max(r["outer"], 1)
+                        runs.append(r)
+        out.update({"sizes": sizes, "gaps": gaps, "runs": runs})
+    print(json.dumps(out), flush=True)
+
+
 def run_micro(args):
     """One kernel alone, one JSON line per block size.  bstencil: the tensor-core
     block stencil of grid 1 or 2 (L2 flushed before every launch; algorithmic
@@ -884,6 +996,9 @@ def main():
     args = parse()
     if args.micro:
         run_micro(args)
+        return
+    if args.study:
+        run_study(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -325,42 +325,69 @@ __global__ void k_pack_frag(unsigned* out, const double2* __restrict__ A, long n
     }
 }
 
-// One warp per (site, tile of 8 right-hand sides); a CTA's warps take
-// consecutive tasks, so the warps of one CTA share a site's operator (L1).
+// One CTA per group of G = max(1, 8 / ntiles) sites, one warp per (site, tile of
+// 8 right-hand sides).  The CTA stages the operator of its sites into shared
+// memory once (cp.async, 11.5 KB a site), so every tile of a site reads the same
+// copy; each warp issues all its neighbour-vector loads before it waits, so a
+// CTA pays one round of memory latency.
 template <bool F16, bool RES>
-__global__ void __launch_bounds__(256) k_bstencil_mma(float2* __restrict__ Y, const float2* __restrict__ X,
-                                                      const float2* __restrict__ B, long vr,
-                                                      const unsigned* __restrict__ Af, int Nx, int Nt, int ntiles,
-                                                      Gate g) {
+__global__ void __launch_bounds__(256, 2) k_bstencil_mma(float2* __restrict__ Y, const float2* __restrict__ X,
+                                                         const float2* __restrict__ B, long vr,
+                                                         const unsigned* __restrict__ Af, int Nx, int Nt, int ntiles,
+                                                         Gate g) {
+    extern __shared__ uint4 bst_op[];  // G sites x SITE_WORDS / 4
+    constexpr int SITE_U4 = SITE_WORDS / 4;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gq = lane >> 2, t = lane & 3, p = gq & 1;
     const int nsite = Nx * Nt;
-    const int task = blockIdx.x * (blockDim.x >> 5) + warp;
-    if (task >= nsite * ntiles) return;
-    const int s = task / ntiles;
-    const int r0 = (task - s * ntiles) * NB_TILE;
-    const bool mine = gate_open(g, r0 + gq);  // lane group gq: right-hand side r0 + gq
-    if (!__any_sync(0xffffffffu, mine)) return;
-    const float2* Xr = X + (long)(r0 + gq) * vr;
+    const int G = ntiles >= 8 ? 1 : 8 / ntiles;
+    const int sg = blockIdx.x * G;                 // first site of the group
+    const int ng = min(G, nsite - sg);             // sites of the group
+    // stage the group's operator
+    const uint4* Ag = reinterpret_cast<const uint4*>(Af) + (long)sg * SITE_U4;
+    const unsigned sbuf = (unsigned)__cvta_generic_to_shared(bst_op);
+    for (int q = threadIdx.x; q < ng * SITE_U4; q += blockDim.x)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sbuf + 16u * q), "l"(Ag + q) : "memory");
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    // this warp's task: site sg + warp / ntiles, tile warp % ntiles
+    const int ls = warp / ntiles;
+    const int r0 = (warp - ls * ntiles) * NB_TILE;
+    const int s = sg + ls;
+    const bool task = ls < ng && warp < G * ntiles;
+    const bool run = task && __any_sync(0xffffffffu, gate_open(g, r0 + gq));
+    float2 xv[5][3][2];
+    if (run) {
+        const float2* Xr = X + (long)(r0 + gq) * vr;
+#pragma unroll
+        for (int d = 0; d < 5; ++d) {
+            const float2* xn = Xr + (long)nbr_of(s, d, Nx, Nt) * NDOF;
+#pragma unroll
+            for (int kt = 0; kt < 3; ++kt) {
+                xv[d][kt][0] = __ldg(xn + 8 * kt + t);
+                xv[d][kt][1] = __ldg(xn + 8 * kt + t + 4);
+            }
+        }
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncthreads();
+    if (!run) return;
     float acc[3][4];
 #pragma unroll
     for (int m = 0; m < 3; ++m)
 #pragma unroll
         for (int i = 0; i < 4; ++i) acc[m][i] = 0.f;
-    const uint4* A4 = reinterpret_cast<const uint4*>(Af) + (long)s * (SITE_WORDS / 4) + (gq >> 1) * 4 + t;
-#pragma unroll 1
+    const uint4* A4 = bst_op + ls * SITE_U4 + (gq >> 1) * 4 + t;
+#pragma unroll
     for (int d = 0; d < 5; ++d) {
-        const int nb = nbr_of(s, d, Nx, Nt);
-        const float2* xn = Xr + (long)nb * NDOF;
 #pragma unroll
         for (int kt = 0; kt < 3; ++kt) {
-            const float2 x0 = __ldg(xn + 8 * kt + t), x1 = __ldg(xn + 8 * kt + t + 4);
+            const float2 x0 = xv[d][kt][0], x1 = xv[d][kt][1];
             const unsigned h0 = pack16<F16>(x0.x, x0.y), h1 = pack16<F16>(x1.x, x1.y);
             const float2 f0 = unpack16<F16>(h0), f1 = unpack16<F16>(h1);
             const unsigned l0 = pack16<F16>(x0.x - f0.x, x0.y - f0.y), l1 = pack16<F16>(x1.x - f1.x, x1.y - f1.y);
 #pragma unroll
             for (int mt = 0; mt < 3; ++mt) {
-                const uint4 w = __ldg(A4 + (d * 9 + mt * 3 + kt) * (TILE_WORDS / 4));
+                const uint4 w = A4[(d * 9 + mt * 3 + kt) * (TILE_WORDS / 4)];
                 const unsigned a[4] = {embed(w.x, p), embed(w.y, p), embed(w.z, p), embed(w.w, p)};
                 mma16816<F16>(acc[mt], a, h0, h1);
                 mma16816<F16>(acc[mt], a, l0, l1);
@@ -449,14 +476,26 @@ void launch_pack_frag(unsigned* out, const double2* A, long nsite, bool fp16, cu
 void launch_bstencil_mma(float2* Y, const float2* X, const float2* B, long vr, const unsigned* Af, int Nx, int Nt,
                          int nb, bool fp16, Gate g, cudaStream_t s) {
     const int ntiles = nb / NB_TILE;
-    const long tasks = (long)Nx * Nt * ntiles;
-    const unsigned grid = (unsigned)((tasks + 7) / 8);
+    const int G = ntiles >= 8 ? 1 : 8 / ntiles;  // sites per CTA
+    const long nsite = (long)Nx * Nt;
+    const unsigned grid = (unsigned)((nsite + G - 1) / G);
+    const size_t smem = (size_t)G * SITE_WORDS * sizeof(unsigned);
+    static bool attr_set[64] = {};  // larger than the default 48 KB when G > 4
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && !attr_set[dev]) {
+        const int mx = 8 * SITE_WORDS * (int)sizeof(unsigned);
+        cudaFuncSetAttribute(k_bstencil_mma<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_bstencil_mma<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_bstencil_mma<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_bstencil_mma<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        attr_set[dev] = true;
+    }
     if (fp16) {
-        if (B) k_bstencil_mma<true, true><<<grid, 256, 0, s>>>(Y, X, B, vr, Af, Nx, Nt, ntiles, g);
-        else k_bstencil_mma<true, false><<<grid, 256, 0, s>>>(Y, X, B, vr, Af, Nx, Nt, ntiles, g);
+        if (B) k_bstencil_mma<true, true><<<grid, 256, smem, s>>>(Y, X, B, vr, Af, Nx, Nt, ntiles, g);
+        else k_bstencil_mma<true, false><<<grid, 256, smem, s>>>(Y, X, B, vr, Af, Nx, Nt, ntiles, g);
     } else {
-        if (B) k_bstencil_mma<false, true><<<grid, 256, 0, s>>>(Y, X, B, vr, Af, Nx, Nt, ntiles, g);
-        else k_bstencil_mma<false, false><<<grid, 256, 0, s>>>(Y, X, B, vr, Af, Nx, Nt, ntiles, g);
+        if (B) k_bstencil_mma<false, true><<<grid, 256, smem, s>>>(Y, X, B, vr, Af, Nx, Nt, ntiles, g);
+        else k_bstencil_mma<false, false><<<grid, 256, smem, s>>>(Y, X, B, vr, Af, Nx, Nt, ntiles, g);
     }
     count_launch();
 }
