@@ -119,13 +119,24 @@ typedef struct {
                               GMRES-Proj solves of a block run batched (the first right-hand side
                               of a handle builds the deflation space alone first).  The outer
                               iteration limit max_outer is checked at restarts */
+    int lowrank_hops;      /* 1 (default): the intermediate grid's four hop blocks of every site
+                              applied as rank-4 factors Q R (each block of P^+ D P sums four
+                              boundary-site terms, each with a rank-1 spin projector), the same
+                              operator to rounding, with about half the bytes and FP64 work of the
+                              dense blocks; 0: dense blocks.  The factors come from a pivoted
+                              Gram-Schmidt of each dense block at set-up; a block whose rank-4
+                              reconstruction errs by more than 1e-11 relative keeps the handle
+                              dense (mg_solve_stats is unaffected) */
 } mg_params;
 
 /* solver of mg_solve (Section 2 compares both) */
 enum { MG_METHOD_MG = 0,             /* FGMRES(8) preconditioned by the deflated V-cycle */
-       MG_METHOD_FINE_DEFLATION = 1  /* no multigrid: GMRES-DR(m,k) on the fine operator for the
+       MG_METHOD_FINE_DEFLATION = 1, /* no multigrid: GMRES-DR(m,k) on the fine operator for the
                                         first right-hand side, GMRES-Proj(m,k) afterwards, FP64;
-                                        mg_solve's iters then counts Krylov steps */ };
+                                        mg_solve's iters then counts Krylov steps */
+       MG_METHOD_FINE_CGNE = 2       /* no multigrid: CGNE on the fine operator (CG on D D^+ y = b,
+                                        x = D^+ y) to the tolerance, limit cgne_max_iters, FP64;
+                                        iters counts CG steps (2 applies each) */ };
 
 typedef struct {
     long long mvps[3];       /* operator applications per grid (fine, intermediate, coarse) */
@@ -308,6 +319,12 @@ mg_status mg_coarse_solve(mg_handle h, int precision, int nrhs, const void* b, v
 
 /* Grid sizes: sites per direction and dofs per site of `level`. */
 mg_status mg_level_shape(mg_handle h, int level, int* n_x, int* n_t, int* dof);
+
+/* How `level` (1 or 2) applies its stencil: *factored = 1 when its hop blocks run as
+ * rank-4 factors (lowrank_hops, intermediate grid only), and *max_rel_err (host or
+ * NULL) the largest relative Frobenius error of those factors against the dense
+ * blocks (0 when not factored). */
+mg_status mg_stencil_info(mg_handle h, int level, int* factored, double* max_rel_err);
 
 /*
  * Standalone Wilson-Dirac apply without a hierarchy (Section 2):

@@ -18,12 +18,13 @@ import numpy as np
 from . import _lib
 from ._lib import (MG_COARSE_CGNE, MG_COARSE_DR_PROJ, MG_F32, MG_F64, MG_BF16, MG_F16, MG_FP64, MG_MIXED,  # noqa: F401
                    MG_MIXED_BF16, MG_MIXED_FP16, MG_OK,
-                   MG_METHOD_MG, MG_METHOD_FINE_DEFLATION,
+                   MG_METHOD_MG, MG_METHOD_FINE_DEFLATION, MG_METHOD_FINE_CGNE,
                    MG_ENOTCONV, MG_ETIMEOUT, MG_COARSE_PROBE_TIMEOUT, MGError, MGParams, MGSolveStats, load)
 
 __all__ = ["build", "default_params", "mg_setup", "mg_setup_from_vectors", "mg_solve", "mg_destroy",
            "mg_reset_deflation", "mg_apply", "mg_restrict", "mg_prolong", "mg_get_stencil",
-           "mg_get_prolongator", "mg_get_deflation", "mg_level_shape", "mg_wilson_apply", "mg_timing_enable",
+           "mg_get_prolongator", "mg_get_deflation", "mg_level_shape", "mg_stencil_info", "mg_wilson_apply",
+           "mg_timing_enable",
            "mg_timing_read", "mg_kernel_launches", "mg_wilson_residual_noalloc", "mg_set_deflation",
            "mg_coarse_solve", "mg_apply_block", "Handle"]
 
@@ -185,6 +186,13 @@ def mg_level_shape(h: Handle, level):
     _lib.check(load().mg_level_shape(h.ptr, level, ctypes.byref(nx), ctypes.byref(nt), ctypes.byref(dof)),
                "mg_level_shape")
     return nx.value, nt.value, dof.value
+
+
+def mg_stencil_info(h: Handle, level):
+    """(factored, max_rel_err): whether `level` applies rank-4 hop factors."""
+    f, e = ctypes.c_int(), ctypes.c_double()
+    _lib.check(load().mg_stencil_info(h.ptr, level, ctypes.byref(f), ctypes.byref(e)), "mg_stencil_info")
+    return bool(f.value), e.value
 
 
 def mg_get_stencil(h: Handle, level) -> np.ndarray:

@@ -15,7 +15,7 @@ MG_OK, MG_EINVAL, MG_ENOMEM, MG_ECUDA, MG_ENOTCONV, MG_EBUDGET, MG_ETIMEOUT = 0,
 MG_COARSE_DR_PROJ, MG_COARSE_CGNE = 0, 1
 MG_FP64, MG_MIXED, MG_MIXED_BF16, MG_MIXED_FP16 = 0, 1, 2, 3
 MG_F64, MG_F32, MG_BF16, MG_F16 = 0, 1, 2, 3
-MG_METHOD_MG, MG_METHOD_FINE_DEFLATION = 0, 1
+MG_METHOD_MG, MG_METHOD_FINE_DEFLATION, MG_METHOD_FINE_CGNE = 0, 1, 2
 
 STATUS_NAMES = {0: "MG_OK", -1: "MG_EINVAL", -2: "MG_ENOMEM", -3: "MG_ECUDA", -4: "MG_ENOTCONV",
                 -5: "MG_EBUDGET", -6: "MG_ETIMEOUT"}
@@ -33,7 +33,7 @@ class MGParams(ctypes.Structure):
         ("method", ctypes.c_int), ("parallel", ctypes.c_int), ("partial_tol", ctypes.c_double),
         ("coarse_tol_partial", ctypes.c_double), ("partial_max_iters", ctypes.c_int), ("pair_rhs", ctypes.c_int),
         ("vcycle_graph", ctypes.c_int), ("coarse_half", ctypes.c_int),
-        ("coarse_dcgs2", ctypes.c_int), ("rhs_block", ctypes.c_int),
+        ("coarse_dcgs2", ctypes.c_int), ("rhs_block", ctypes.c_int), ("lowrank_hops", ctypes.c_int),
     ]
 
 
@@ -75,7 +75,7 @@ _lib = None
 # every symbol declared in include/mg.h
 SYMBOLS = ("mg_default_params", "mg_setup", "mg_setup_from_vectors", "mg_solve", "mg_reset_deflation",
            "mg_destroy", "mg_last_error", "mg_apply", "mg_restrict", "mg_prolong", "mg_get_stencil",
-           "mg_get_prolongator", "mg_get_deflation", "mg_level_shape", "mg_wilson_apply",
+           "mg_get_prolongator", "mg_get_deflation", "mg_level_shape", "mg_stencil_info", "mg_wilson_apply",
            "mg_timing_enable", "mg_timing_read", "mg_kernel_launches", "mg_server_create", "mg_server_submit",
            "mg_server_wait", "mg_server_poll", "mg_server_stats", "mg_server_destroy", "mg_wilson_residual_noalloc",
            "mg_set_deflation", "mg_coarse_solve", "mg_apply_block")
@@ -106,6 +106,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "mg_get_prolongator": (i, [vp, i, vp]),
         "mg_get_deflation": (i, [vp, vp, vp, ctypes.POINTER(i)]),
         "mg_level_shape": (i, [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]),
+        "mg_stencil_info": (i, [vp, i, ctypes.POINTER(i), ctypes.POINTER(ctypes.c_double)]),
         "mg_wilson_apply": (i, [vp, i, i, d, i, i, vp, vp, vp]),
         "mg_timing_enable": (i, [vp, i, i]),
         "mg_timing_read": (i, [vp, i, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong)]),

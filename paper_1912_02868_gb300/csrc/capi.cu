@@ -118,8 +118,10 @@ mg_status check_params(const mg_params& p) {
         (p.method != MG_METHOD_MG || p.coarse_solver != MG_COARSE_DR_PROJ || p.partial_tol > 0.0))
         return set_error("the tensor-core block solve (precision %d) is built for the V-cycle with the deflated "
                          "coarse solve", p.precision), MG_EINVAL;
-    if (p.method != MG_METHOD_MG && p.method != MG_METHOD_FINE_DEFLATION)
+    if (p.method != MG_METHOD_MG && p.method != MG_METHOD_FINE_DEFLATION && p.method != MG_METHOD_FINE_CGNE)
         return set_error("unknown method %d", p.method), MG_EINVAL;
+    if (p.method == MG_METHOD_FINE_CGNE && p.precision != MG_FP64)
+        return set_error("the fine CGNE method runs in FP64 (precision MG_FP64)"), MG_EINVAL;
     if (p.dr_m - p.dr_k > MSMAX)
         return set_error("dr_m - dr_k must be <= %d", MSMAX), MG_EINVAL;
     if (!(p.partial_tol >= 0.0 && p.partial_tol < 1.0))
@@ -127,12 +129,11 @@ mg_status check_params(const mg_params& p) {
     if (p.partial_tol > 0.0 && (!(p.coarse_tol_partial > 0.0 && p.coarse_tol_partial < 1.0) || p.partial_max_iters < 1))
         return set_error("partial mode: coarse_tol_partial must be in (0, 1), partial_max_iters positive"),
                MG_EINVAL;
-    if (p.partial_tol > 0.0 && p.coarse_solver != MG_COARSE_DR_PROJ)
-        return set_error("the partial intermediate solve is built for the deflated coarse solve"), MG_EINVAL;
     if (p.pair_rhs != 0 && p.pair_rhs != 1) return set_error("pair_rhs must be 0 or 1"), MG_EINVAL;
     if (p.vcycle_graph != 0 && p.vcycle_graph != 1) return set_error("vcycle_graph must be 0 or 1"), MG_EINVAL;
     if (p.coarse_half != 0 && p.coarse_half != 1) return set_error("coarse_half must be 0 or 1"), MG_EINVAL;
     if (p.coarse_dcgs2 != 0 && p.coarse_dcgs2 != 1) return set_error("coarse_dcgs2 must be 0 or 1"), MG_EINVAL;
+    if (p.lowrank_hops != 0 && p.lowrank_hops != 1) return set_error("lowrank_hops must be 0 or 1"), MG_EINVAL;
     return MG_OK;
 }
 
@@ -203,6 +204,8 @@ mg_status alloc_workspaces(Handle& H, cudaStream_t s, bool owner) {
         MG_TRY(halloc_t(H, &H.p32.r, (size_t)n1));
         MG_TRY(halloc_t(H, &H.p32.ks, 1));
     }
+    if (p.method == MG_METHOD_FINE_CGNE)
+        for (int i = 0; i < 5; ++i) MG_TRY(halloc_t(H, &H.fcg[i], (size_t)n0));
     if (p.method == MG_METHOD_FINE_DEFLATION) {
         MG_TRY(halloc_t(H, &H.fdV, (size_t)(p.dr_m + 1) * n0));
         MG_TRY(halloc_t(H, &H.fdV2, (size_t)(p.dr_m + 1) * n0));
@@ -293,6 +296,8 @@ mg_status solve_rhs(Handle& H, const double2* B, double2* X, bool bdev, bool xde
         bool conv = false;
         if (H.p.method == MG_METHOD_FINE_DEFLATION)
             MG_TRY(fine_deflated_solve(H, bsrc, xdst, tol, s, &it, &rr, &conv));
+        else if (H.p.method == MG_METHOD_FINE_CGNE)
+            MG_TRY(fine_cgne_solve(H, bsrc, xdst, tol, s, &it, &rr, &conv));
         else
             MG_TRY(fgmres_solve(H, bsrc, xdst, tol, s, &it, &rr, &conv));
         if (!xdev) MG_CUDA_TRY(cudaMemcpyAsync(xi, H.fx, n0 * sizeof(double2), cudaMemcpyDeviceToHost, s));
@@ -456,6 +461,10 @@ mg_status setup_common(const void* gauge, int Lx, int Lt, double m0, int nvec, i
         TRYF(halloc_t(H, &H.A32[l], (size_t)nx[l] * nt[l] * 5 * 576));
     }
     if (p.precision != MG_FP64 && p.coarse_half) TRYF(halloc_t(H, &H.A16c, (size_t)nx[2] * nt[2] * 5 * 576));
+    if (p.lowrank_hops) {
+        TRYF(halloc_t(H, &H.F64, (size_t)nx[1] * nt[1] * LR_SITE));
+        TRYF(halloc_t(H, &H.F32, (size_t)nx[1] * nt[1] * LR_SITE));
+    }
     for (int l = 0; l < 2; ++l) {
         const size_t q = (size_t)nx[l + 1] * nt[l + 1] * 24 * 16 * (dof[l] / 2);
         TRYF(halloc_t(H, &H.Q64[l], q));
@@ -564,6 +573,7 @@ mg_status mg_default_params(mg_params* p) {
     p->coarse_half = 1;
     p->coarse_dcgs2 = 0;
     p->rhs_block = 64;
+    p->lowrank_hops = 1;
     return MG_OK;
 }
 
@@ -770,6 +780,14 @@ mg_status mg_level_shape(mg_handle h, int level, int* n_x, int* n_t, int* dof) {
     if (n_x) *n_x = L.Nx;
     if (n_t) *n_t = L.Nt;
     if (dof) *dof = L.dof;
+    return MG_OK;
+}
+
+mg_status mg_stencil_info(mg_handle h, int level, int* factored, double* max_rel_err) {
+    if (!h || level < 1 || level > 2 || !factored) return set_error("bad handle, level or output"), MG_EINVAL;
+    const Handle& H = h->h;
+    *factored = H.L64[level].F ? 1 : 0;
+    if (max_rel_err) *max_rel_err = H.L64[level].F ? H.lowrank_err : 0.0;
     return MG_OK;
 }
 

@@ -37,6 +37,7 @@ struct Level {
     const C2<T>* U = nullptr;     // level 0: gauge field
     double m0 = 0.0;
     const C2<T>* A = nullptr;     // levels 1, 2: stencil (column-major blocks)
+    const C2<T>* F = nullptr;     // level 1 with lowrank_hops: the stencil with rank-4 hop factors
     const C2<T>* Q = nullptr;     // prolongator to the next grid (none on the coarsest)
     int h = 1;                    // dofs per chirality at this grid
     // workspaces
@@ -55,6 +56,7 @@ struct Level {
             if (e0) cudaEventRecord(e0, s);
         }
         if (U) launch_wilson<T>(y, xin, U, b, m0, Nx, Nt, dagger, g, s);
+        else if (F) launch_stencil_lr<T>(y, xin, F, b, Nx, Nt, dagger, g, s);
         else launch_stencil<T>(y, xin, A, b, Nx, Nt, dof, dagger, g, s);
         if (e1) cudaEventRecord(e1, s);
     }
@@ -127,6 +129,9 @@ struct Handle {
     float2* U32 = nullptr;
     float2* A32[3] = {nullptr, nullptr, nullptr};
     unsigned* A16c = nullptr;  // FP16 copy of the coarsest operator for the cluster kernels (coarse_half)
+    double2* F64 = nullptr;    // intermediate grid with rank-4 hop factors (lowrank_hops), LR_SITE per site
+    float2* F32 = nullptr;
+    double lowrank_err = 0.0;  // largest relative error of the factored hop blocks
     float2* Q32[2] = {nullptr, nullptr};
     // fine FGMRES (FP64)
     double2* fV = nullptr;  // (m+1) x n0
@@ -151,6 +156,7 @@ struct Handle {
     // fine-grid deflation arm (method MG_METHOD_FINE_DEFLATION), FP64
     double2* fdV = nullptr;   // (m+1) x n0
     double2* fdV2 = nullptr;
+    double2* fcg[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // fine CGNE: y, r, p, q, t
     double2* fdW = nullptr;   // (k+1) x n0
     KState* fdks = nullptr;
     KState* fdpls = nullptr;
@@ -198,6 +204,8 @@ mg_status fgmres_solve_pair(Handle* HH[2], const double2* const b[2], double2* c
                             cudaStream_t s, int it_out[2], double rr_out[2], bool conv_out[2]);
 mg_status build_hierarchy(Handle& H, const double2* gauge_dev, const double2* starts0, const double2* starts1,
                           const double2* nullvecs0, const double2* nullvecs1, cudaStream_t s);
+mg_status fine_cgne_solve(Handle& H, const double2* b, double2* x, double tol, cudaStream_t s, int* iters,
+                          double* relres, bool* converged);
 mg_status fine_deflated_solve(Handle& H, const double2* b, double2* x, double tol, cudaStream_t s, int* iters,
                               double* relres, bool* converged);
 // Lockstep FGMRES of nb <= 64 right-hand sides (host or device b, x: [nb][n0]) with

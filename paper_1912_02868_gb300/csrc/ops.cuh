@@ -44,6 +44,20 @@ template <typename T>
 void launch_stencil(C2<T>* y, const C2<T>* x, const C2<T>* A, const C2<T>* b, int Nx, int Nt, int dof,
                     bool dagger, Gate g, cudaStream_t s);
 
+// The 24-dof stencil with low-rank hop blocks (intermediate grid): per site
+// LR_SITE complex entries, the self block column-major (576), then for each hop
+// direction d = 1..4 the factors of A[s][d] = Q R: Q as [i][k] (4 x 24, its
+// columns contiguous) and R as [i][l] (4 x 24, its rows contiguous).
+constexpr int LR_RANK = 4;
+constexpr int LR_SITE = 24 * 24 + 4 * 2 * LR_RANK * 24;
+template <typename T>
+void launch_stencil_lr(C2<T>* y, const C2<T>* x, const C2<T>* F, const C2<T>* b, int Nx, int Nt, bool dagger,
+                       Gate g, cudaStream_t s);
+// F (FP64, LR_SITE per site) from the dense stencil A: the self blocks copied,
+// each hop block factored by Gram-Schmidt with column pivoting (4 steps);
+// *maxerr (device) receives max over blocks of ||A - Q R||_F / ||A||_F
+void launch_factor_hops(double2* F, const double2* A, long nsite, double* maxerr, cudaStream_t s);
+
 // -------------------------------------------------------------- transfer ----
 // Q[B][c][j][l][a]: block B of the finer grid (NxF x NtF sites, 2h dofs per site),
 // chirality c, vector j < 12, site l = lx + 4 lt in the block, dof a < h.

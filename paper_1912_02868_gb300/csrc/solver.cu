@@ -333,6 +333,9 @@ mg_status cgne_solve(Handle& H, const C2<T>* f, C2<T>* x, cudaStream_t s) {
     Level<T>& L = H.levels<T>()[2];
     CoarseWS<T>& W = H.coarse<T>();
     int it = 0;
+    // coarse_tol_rest in every outer iteration, also with the partial intermediate
+    // solve: relaxing the non-deflated coarse solve like the projected one costs
+    // many outer iterations (Section 2)
     MG_TRY(cg_normal<T>(H, 2, L, f, W.V, W.r, W.p, W.q, W.t, H.p.coarse_tol_rest, H.p.cgne_max_iters, &it, s));
     L.apply(x, W.V, nullptr, true, Gate{}, s);  // x = A^+ y
     H.st.mvps[2] += 1;
@@ -727,6 +730,31 @@ mg_status fine_deflated_solve(Handle& H, const double2* b, double2* x, double to
     return MG_OK;
 }
 
+// CGNE on the fine operator, no multigrid (the paper's plain comparison method,
+// Section 3): CG on D D^+ y = b to tol, x = D^+ y, true residual checked.
+mg_status fine_cgne_solve(Handle& H, const double2* b, double2* x, double tol, cudaStream_t s, int* iters,
+                          double* relres, bool* converged) {
+    Level<double>& L0 = H.L64[0];
+    const long n = L0.n;
+    int it = 0;
+    MG_TRY(cg_normal<double>(H, 0, L0, b, H.fcg[0], H.fcg[1], H.fcg[2], H.fcg[3], H.fcg[4], tol, H.p.cgne_max_iters,
+                             &it, s));
+    L0.apply(x, H.fcg[0], nullptr, true, Gate{}, s);  // x = D^+ y
+    H.st.mvps[0] += 2;                                 // and the residual check below
+    double* fnb2 = MG_DEVF(H.sc, double, tmp) + 4;
+    double* r2 = MG_DEVF(H.sc, double, r2);
+    launch_norm2<double>(fnb2, b, n, H.red, Gate{}, s);
+    L0.apply(H.fr, x, b, false, Gate{}, s);
+    launch_norm2<double>(r2, H.fr, n, H.red, Gate{}, s);
+    Scalars hs{};
+    MG_TRY(read_scalars(H, hs, s));
+    *relres = hs.tmp[4] > 0.0 ? std::sqrt(hs.r2 / hs.tmp[4]) : 0.0;
+    *converged = *relres <= tol;
+    *iters = it;
+    H.st.outer += it;
+    return MG_OK;
+}
+
 // ---------------------------------------------------------------- set-up ----
 
 namespace {
@@ -819,6 +847,22 @@ mg_status build_hierarchy(Handle& H, const double2* gauge_dev, const double2* st
     for (int l = 1; l < 3; ++l)
         launch_convert<double, float>(H.A32[l], H.A64[l], (long)L[l].Nx * L[l].Nt * 5 * 576, Gate{}, s);
     if (H.A16c) launch_pack_half(H.A16c, H.A64[2], (long)L[2].Nx * L[2].Nt * 5 * 576, s);
+    // the intermediate grid's hop blocks as rank-4 factors (lowrank_hops), used only
+    // when every block is reproduced to rounding
+    if (H.F64) {
+        double* maxerr = MG_DEVF(H.sc, double, tmp) + 6;
+        const long ns1 = (long)L[1].Nx * L[1].Nt;
+        launch_factor_hops(H.F64, H.A64[1], ns1, maxerr, s);
+        MG_LAUNCH_CHECK();
+        Scalars hs{};
+        MG_TRY(read_scalars(H, hs, s));
+        H.lowrank_err = hs.tmp[6];
+        if (hs.tmp[6] <= 1e-11) {
+            launch_convert<double, float>(H.F32, H.F64, ns1 * LR_SITE, Gate{}, s);
+            H.L64[1].F = H.F64;
+            H.L32[1].F = H.F32;
+        }
+    }
     for (int l = 0; l < 2; ++l)
         launch_convert<double, float>(H.Q32[l], H.Q64[l], (long)L[l + 1].Nx * L[l + 1].Nt * 24 * 16 * L[l].h,
                                       Gate{}, s);

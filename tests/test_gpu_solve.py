@@ -264,3 +264,59 @@ def test_bench_size_solve_meets_tolerance(mgmod):
                 assert _true_relres(U, m0, Xh[i], B[i]) <= 1.0001e-8
         finally:
             g.close()
+
+
+@pytest.mark.parametrize("L", [16, 32])
+def test_fine_cgne_method(mgmod, L):
+    """The plain comparison method without multigrid: CGNE on the fine operator
+    (CG on D D^+ y = b, x = D^+ y), FP64, against the oracle's cgne: the same
+    iteration count within 1%, the true residual at the tolerance, and the
+    fine-operator count of Eq. 1 (two applies per step, one for x, one for the
+    residual check)."""
+    import torch
+    from oracle import krylov
+    U = synth.gauge_field(L, 0)
+    m0 = synth.m0_for(L, 0)
+    p = mgmod.default_params(method=mgmod.MG_METHOD_FINE_CGNE, precision=mgmod.MG_FP64)
+    g = mgmod.mg_setup(dev(U), L, L, m0, params=p)
+    A = lambda v: dirac.wilson(U, v.reshape(L, L, 2), m0).ravel()
+    Ad = lambda v: dirac.wilson_dagger(U, v.reshape(L, L, 2), m0).ravel()
+    try:
+        b = synth.rhs(L, 0, 3)[0]
+        x = torch.zeros(b.shape, dtype=torch.complex128, device="cuda")
+        # CG stops on its recursive residual, so the true one may sit a rounding above
+        st, it, rr, stats = mgmod.mg_solve(g, dev(b), x, 1, 1e-8, allow_notconv=True)
+        xo, info = krylov.cgne(A, Ad, b.ravel(), 1e-8)
+        assert info.converged and rr[0] <= 1.05e-8
+        assert _true_relres(U, m0, host(x), b) <= 1.05e-8
+        assert abs(it[0] - info.iters) <= max(2, 0.01 * info.iters), (it[0], info.iters)
+        assert stats["mvps"][0] == 2 * it[0] + 2 and stats["mvps"][1] == 0 and stats["mvps"][2] == 0
+        assert rel2(host(x).ravel(), xo) <= 1e-5
+    finally:
+        g.close()
+
+
+def test_nondeflated_partial_solve(mgmod):
+    """Non-deflated MG with the partial intermediate solve: CGNE on the coarsest
+    grid to 1e-8 in every outer iteration (Section 2: relaxing it like the
+    deflated solve costs outer iterations), against the oracle with the same
+    near-null vectors: outer counts within 1, the true residual at 1e-8, and
+    every coarse solve a CGNE solve."""
+    import torch
+    L = 32
+    U, m0, h = _hier(L)
+    p = mgmod.default_params(coarse_solver=mgmod.MG_COARSE_CGNE, partial_tol=0.2)
+    g = mgmod.mg_setup_from_vectors(dev(U), L, L, m0, dev(h.nullvecs[0]), dev(h.nullvecs[1]), params=p)
+    try:
+        b = synth.rhs(L, 0, 0)[0]
+        x = torch.zeros(b.shape, dtype=torch.complex128, device="cuda")
+        st, iters, relres, stats = mgmod.mg_solve(g, dev(b), x, 1, 1e-8)
+        assert relres[0] <= 1e-8 and stats["dr_solves"] == 0
+        assert _true_relres(U, m0, host(x), b) <= 1.0001e-8
+        solver = omg.MGSolver(h, omg.Params(coarse="cgne", partial_tol=0.2))
+        xo, info = solver.solve(b, 1e-8)
+        assert abs(iters[0] - info.iters) <= 1, (iters[0], info.iters)
+        assert all(kind == "cgne" for kind, _ in solver.coarse_solves)
+        assert all(t == 1e-8 for t in solver.coarse_tols)
+    finally:
+        g.close()
