@@ -39,6 +39,8 @@ L = 256
 NCONF = 10
 TOL = 1e-8
 H_DR_M = 30  # GMRES-DR / GMRES-Proj m (k = 10)
+WORKLOAD = ("256^2 x 10 configs x 1 RHS per step, deflated MG-FGMRES(8), GMRES-DR(30,10)/GMRES-Proj(30,10), "
+            "tol 1e-8 true FP64 residual; mixed: FP32 V-cycle (coarsest operator streamed as an FP16 copy), FP64 outer")
 LR_SITE = 24 * 24 + 4 * 2 * 4 * 24  # complex entries a site of the factored intermediate-grid stencil
 
 
@@ -57,16 +59,18 @@ def parse():
     ap.add_argument("--no-batching", action="store_true", help="skip the 64-right-hand-side batching sample")
     ap.add_argument("--no-scale", action="store_true", help="skip the 1024^2 x 16-right-hand-side block solve")
     ap.add_argument("--serve-requests", type=int, default=32, help="requests per phase of the served stream")
-    ap.add_argument("--serve-budget-gib", type=float, default=96.0,
+    ap.add_argument("--serve-budget-gib", type=float, default=64.0,
                     help="HBM budget of the server's resident hierarchies (below the stream's total need)")
     ap.add_argument("--serve-workers", type=int, default=8)
-    ap.add_argument("--micro", choices=["bstencil", "coarse_block"], default=None,
+    ap.add_argument("--micro", choices=["bstencil", "coarse_block", "stencil", "wilson"], default=None,
                     help="time one kernel alone (the target of the ncu captures) instead of the benchmark")
     ap.add_argument("--micro-lattice", type=int, default=256)
     ap.add_argument("--micro-nrhs", default="8,64", help="comma-separated block sizes")
     ap.add_argument("--micro-reps", type=int, default=10)
     ap.add_argument("--micro-level", type=int, default=1, help="grid of the block stencil (1 or 2)")
     ap.add_argument("--micro-fp16", action="store_true", help="FP16 instead of BF16 operator")
+    ap.add_argument("--micro-dense", action="store_true", help="dense intermediate-grid hop blocks (lowrank_hops 0)")
+    ap.add_argument("--micro-f64", action="store_true", help="--micro stencil in FP64 instead of FP32")
     ap.add_argument("--study", choices=["table1", "massgap"], default=None,
                     help="counter study of the paper's Section 3 instead of the benchmark")
     ap.add_argument("--study-sizes", default="64,128,256", help="the paper's lattice sizes")
@@ -475,8 +479,11 @@ def run_reference(args):
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "impl": "reference", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(timed) / len(timed),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "256^2 beta=6.0 U(1), 1 RHS per step, deflated MG-FGMRES(8), tol 1e-8",
-                       "lattice": L, "tol": TOL},
+            "config": {"workload": WORKLOAD, "lattice": L, "configs": NCONF, "beta": 6.0, "tol": TOL,
+                       "precision": "f64 (the oracle)",
+                       "sample": "per right-hand side, configuration 0 only: each further configuration's "
+                                 "hierarchy set-up costs about 25 s on the host; the rate is solves/s, the same "
+                                 "unit as the native arm's ten configurations per step"},
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -810,8 +817,7 @@ def run_native(args):
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": "256^2 x 10 configs x 1 RHS per step, deflated MG-FGMRES(8), GMRES-DR(30,10)/"
-                               "GMRES-Proj(30,10), tol 1e-8 true FP64 residual; mixed: FP32 V-cycle (coarsest operator streamed as an FP16 copy), FP64 outer",
+        "config": {"workload": WORKLOAD,
                    "lattice": L, "configs": nconf, "beta": 6.0, "tol": TOL, "precision": "mixed",
                    "l2": "working set > L2: 10 resident hierarchies (~3.8 GB) cycled every step",
                    "parallelism": f"replicas x{world}", "m0_fingerprints_match": fp_ok},
@@ -962,12 +968,43 @@ def run_micro(args):
     prec = mg.MG_MIXED_FP16 if args.micro_fp16 else mg.MG_MIXED_BF16
     op = mg.MG_F16 if args.micro_fp16 else mg.MG_BF16
     U = synth.gauge_field(Lm, 0, gpu=True)
-    h = mg.mg_setup(torch.from_numpy(U).to(dev), Lm, Lm, synth.m0_for(Lm, 0), params=mg.default_params(precision=prec),
+    h = mg.mg_setup(torch.from_numpy(U).to(dev), Lm, Lm, synth.m0_for(Lm, 0),
+                    params=mg.default_params(precision=prec, lowrank_hops=0 if args.micro_dense else 1),
                     starts0=torch.from_numpy(synth.nullvec_starts(Lm, 0, 0, 12, Lm * Lm * 2)).to(dev),
                     starts1=torch.from_numpy(synth.nullvec_starts(Lm, 0, 1, 12, (Lm // 4) ** 2 * 24)).to(dev))
     try:
         for nb in [int(v) for v in args.micro_nrhs.split(",")]:
-            if args.micro == "bstencil":
+            if args.micro == "wilson":
+                # the FP32 fine Wilson-Dirac apply alone: 48 B a site (spinor in, links, spinor out)
+                Ug = torch.from_numpy(U).to(dev).to(torch.complex64)
+                x = torch.complex(torch.randn((Lm, Lm, 2), device=dev), torch.randn((Lm, Lm, 2), device=dev))
+                y = torch.empty_like(x)
+                m0w = synth.m0_for(Lm, 0)
+                t = timed_launches(torch, dev, lambda: mg.mg_wilson_apply(Ug, Lm, Lm, m0w, x, y, precision=mg.MG_F32),
+                                   launches=args.micro_reps, warm=1)
+                nbytes = 48 * Lm * Lm
+                out = {"kernel": "k_wilson<float>", "sites": Lm * Lm, "us": t * 1e6, "GB_per_s": nbytes / t / 1e9,
+                       "bytes": nbytes}
+            elif args.micro == "stencil":
+                # the FP32 intermediate-grid stencil of one vector as the V-cycle applies it
+                nx, nt, dof = mg.mg_level_shape(h, 1)
+                n1, s1 = nx * nt * dof, nx * nt
+                x = torch.complex(torch.randn(n1, device=dev), torch.randn(n1, device=dev))
+                if args.micro_f64:
+                    x = x.to(torch.complex128)
+                y = torch.empty_like(x)
+                pa = mg.MG_F64 if args.micro_f64 else mg.MG_F32
+                t = timed_launches(torch, dev, lambda: mg.mg_apply(h, 1, x, y, precision=pa),
+                                   launches=args.micro_reps, warm=1)
+                fac, err = mg.mg_stencil_info(h, 1)
+                esz = 16 if args.micro_f64 else 8
+                nbytes = ((LR_SITE if fac else 5 * 576) + 2 * 24) * esz * s1
+                tn = "double" if args.micro_f64 else "float"
+                out = {"kernel": f"k_stencil_lr<{tn}>" if fac else ("k_stencil<double,24>" if args.micro_f64
+                                                                      else "k_stencil_f32"),
+                       "sites": s1, "us": t * 1e6, "GB_per_s": nbytes / t / 1e9, "bytes": nbytes,
+                       "factor_rel_err": err}
+            elif args.micro == "bstencil":
                 nx, nt, dof = mg.mg_level_shape(h, args.micro_level)
                 n1, s1 = nx * nt * dof, nx * nt
                 x = torch.complex(torch.randn((nb, n1), device=dev), torch.randn((nb, n1), device=dev))

@@ -651,18 +651,22 @@ __global__ void __launch_bounds__(CB_THREADS, 2) k_cb_update_push(CBArgs a, int 
 // generation, the others wait (at most `spin` polls) for it to change.  A wait
 // that gives up sets *err; the CTA then goes on, so every barrier still ends.
 __device__ __forceinline__ void tile_sync(unsigned* bar, unsigned n, long spin, int* err) {
-    __syncthreads();
+    __syncthreads();  // the CTA's writes of the phase precede thread 0's release below
     if (threadIdx.x == 0) {
-        volatile unsigned* gen = bar + 1;
-        const unsigned g = *gen;
-        __threadfence();
-        if (atomicAdd(bar, 1u) == n - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
+        unsigned* gen = bar + 1;
+        unsigned g, old;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(g) : "l"(gen) : "memory");
+        // arrival: release this CTA's writes, acquire the earlier arrivals' ones
+        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;\n" : "=r"(old) : "l"(bar) : "memory");
+        if (old == n - 1) {
+            asm volatile("st.relaxed.gpu.global.u32 [%0], 0;\n" ::"l"(bar) : "memory");
+            asm volatile("red.release.gpu.global.add.u32 [%0], 1;\n" ::"l"(gen) : "memory");
         } else {
             long it = 0;
-            while (*gen == g) {
+            unsigned cur;
+            while (true) {
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(cur) : "l"(gen) : "memory");
+                if (cur != g) break;
                 if (++it > spin) {
                     atomicExch(err, 1);
                     break;
@@ -670,9 +674,8 @@ __device__ __forceinline__ void tile_sync(unsigned* bar, unsigned n, long spin, 
                 __nanosleep(32);
             }
         }
-        __threadfence();
     }
-    __syncthreads();
+    __syncthreads();  // thread 0's acquire orders the other arrivals' writes before every thread's reads
 }
 
 #ifdef CB_PHASE_CLOCKS

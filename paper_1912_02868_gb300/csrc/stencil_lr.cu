@@ -12,6 +12,9 @@
 // conventions of the fine operator; the largest relative reconstruction
 // error over the blocks is reported, and the caller keeps the dense operator
 // if it is not at rounding level.
+#include <algorithm>
+#include <type_traits>
+
 #include "ops.cuh"
 
 namespace mg {
@@ -179,14 +182,125 @@ __global__ void __launch_bounds__(LR_SPB* N) k_stencil_lr(C2<T>* __restrict__ y,
     y[s * N + k] = acc;
 }
 
+
+// FP32 (bound by HBM): one thread per PAIR of dof rows (12 per site), so every
+// operator load is a 16-byte vector of two rows (Q, the self block) or two
+// columns (R); sites spread evenly over one block per SM and wave, as in the
+// dense FP32 stencil.  The 16 inner products t = R x_nbr of a site are formed
+// from per-thread partial sums (two entries each) added in shared memory in a
+// fixed order.
+constexpr int LRF_TPS = 12;
+constexpr int LRF_MAX_SPB = 16;  // sites per block (the partial sums need 24.6 KB of shared memory)
+
+__global__ void __launch_bounds__(LRF_MAX_SPB* LRF_TPS) k_stencil_lr_f32(float2* __restrict__ y,
+                                                                         const float2* __restrict__ x,
+                                                                         const float2* __restrict__ F,
+                                                                         const float2* __restrict__ b, int Nx,
+                                                                         int Nt, int spb, int dagger, Gate g) {
+    if (!gate_open(g)) return;
+    __shared__ float4 xs[LRF_MAX_SPB][5][N / 2];
+    __shared__ float2 part[LRF_MAX_SPB][4 * LR_RANK][LRF_TPS];
+    __shared__ float2 ts[LRF_MAX_SPB][4 * LR_RANK];
+    const int ls = threadIdx.x / LRF_TPS, kt = threadIdx.x - ls * LRF_TPS;
+    const long s = (long)blockIdx.x * spb + ls;
+    const long nsite = (long)Nx * Nt;
+    const bool valid = ls < spb && s < nsite;
+    const bool flip = dagger && (2 * kt >= N / 2);
+    const float4* F4 = reinterpret_cast<const float4*>(F + (valid ? s : 0) * (long)LR_SITE);
+    float4 a[N];
+    if (valid) {
+#pragma unroll
+        for (int l = 0; l < N; ++l) a[l] = __ldg(F4 + l * (N / 2) + kt);  // self block, rows 2 kt, 2 kt + 1
+        const int xx = (int)(s % Nx), t = (int)(s / Nx);
+        const long nb[5] = {s, (xx + 1 == Nx) ? s - xx : s + 1, (xx == 0) ? s + Nx - 1 : s - 1,
+                            (t + 1 == Nt) ? (long)xx : s + Nx, (t == 0) ? s + (long)Nx * (Nt - 1) : s - Nx};
+        const float4* x4 = reinterpret_cast<const float4*>(x);
+#pragma unroll
+        for (int d = 0; d < 5; ++d) {
+            float4 v = __ldg(x4 + nb[d] * (N / 2) + kt);
+            if (flip) v = make_float4(-v.x, -v.y, -v.z, -v.w);
+            xs[ls][d][kt] = v;
+        }
+    }
+    __syncthreads();
+    float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
+    if (valid) {
+        // partial sums of t_{d,i} over columns 2 kt, 2 kt + 1
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+            const float4 xv = xs[ls][d + 1][kt];
+            const float4* R4 = F4 + (N * N + d * LR_BLOCK + LR_RANK * N) / 2;
+#pragma unroll
+            for (int i = 0; i < LR_RANK; ++i) {
+                const float4 r = __ldg(R4 + i * (N / 2) + kt);
+                float2 p = cfma(make_float2(r.x, r.y), make_float2(xv.x, xv.y), make_float2(0.f, 0.f));
+                p = cfma(make_float2(r.z, r.w), make_float2(xv.z, xv.w), p);
+                part[ls][d * LR_RANK + i][kt] = p;
+            }
+        }
+        const float2* xsl = reinterpret_cast<const float2*>(&xs[ls][0][0]);
+#pragma unroll
+        for (int l = 0; l < N; ++l) {
+            const float2 xv = xsl[l];
+            acc0 = cfma(make_float2(a[l].x, a[l].y), xv, acc0);
+            acc1 = cfma(make_float2(a[l].z, a[l].w), xv, acc1);
+        }
+    }
+    __syncthreads();
+    if (valid) {
+        for (int q = kt; q < 4 * LR_RANK; q += LRF_TPS) {
+            float2 tv = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int j = 0; j < LRF_TPS; ++j) {
+                tv.x += part[ls][q][j].x;
+                tv.y += part[ls][q][j].y;
+            }
+            ts[ls][q] = tv;
+        }
+    }
+    __syncthreads();
+    if (!valid) return;
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+        const float4* Q4 = F4 + (N * N + d * LR_BLOCK) / 2;
+#pragma unroll
+        for (int i = 0; i < LR_RANK; ++i) {
+            const float4 q = __ldg(Q4 + i * (N / 2) + kt);
+            const float2 tv = ts[ls][d * LR_RANK + i];
+            acc0 = cfma(make_float2(q.x, q.y), tv, acc0);
+            acc1 = cfma(make_float2(q.z, q.w), tv, acc1);
+        }
+    }
+    if (flip) {
+        acc0 = cneg(acc0);
+        acc1 = cneg(acc1);
+    }
+    if (b) {
+        const float4 bv = __ldg(reinterpret_cast<const float4*>(b) + s * (N / 2) + kt);
+        acc0 = make_float2(bv.x - acc0.x, bv.y - acc0.y);
+        acc1 = make_float2(bv.z - acc1.x, bv.w - acc1.y);
+    }
+    reinterpret_cast<float4*>(y)[s * (N / 2) + kt] = make_float4(acc0.x, acc0.y, acc1.x, acc1.y);
+}
+
 }  // namespace
 
 template <typename T>
 void launch_stencil_lr(C2<T>* y, const C2<T>* x, const C2<T>* F, const C2<T>* b, int Nx, int Nt, bool dagger,
                        Gate g, cudaStream_t s) {
     const long nsite = (long)Nx * Nt;
-    const unsigned grid = (unsigned)((nsite + LR_SPB - 1) / LR_SPB);
-    k_stencil_lr<T><<<grid, LR_SPB * N, 0, s>>>(y, x, F, b, Nx, Nt, dagger ? 1 : 0, g);
+    if constexpr (std::is_same<T, float>::value) {
+        // whole waves of one block per SM, sites spread evenly over the blocks
+        const long sms = sm_count();
+        const long waves = (nsite + sms * LRF_MAX_SPB - 1) / (sms * LRF_MAX_SPB);
+        const long blocks = std::min(sms * waves, nsite);
+        const int spb = (int)((nsite + blocks - 1) / blocks);
+        const unsigned grid = (unsigned)((nsite + spb - 1) / spb);
+        k_stencil_lr_f32<<<grid, spb * LRF_TPS, 0, s>>>(y, x, F, b, Nx, Nt, spb, dagger ? 1 : 0, g);
+    } else {
+        const unsigned grid = (unsigned)((nsite + LR_SPB - 1) / LR_SPB);
+        k_stencil_lr<T><<<grid, LR_SPB * N, 0, s>>>(y, x, F, b, Nx, Nt, dagger ? 1 : 0, g);
+    }
     count_launch();
 }
 
