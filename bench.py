@@ -287,6 +287,26 @@ def timed_launches(torch, dev, fn, launches=10, warm=3):
     return float(np.mean(ms)) / 1e3
 
 
+def timed_level_applies(mg, torch, dev, h, level, fn, launches=10, warm=3):
+    """Mean kernel time (s) of the level applies fn() makes, from the handle's own
+    CUDA events around each apply (mg_timing_enable), L2 flushed before every call.
+    (The level-apply entry synchronizes before it returns, so events recorded
+    around the call would also count the host's return.)"""
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for i in range(warm):
+        flush.fill_(i & 0xFF)
+        fn()
+    mg.mg_timing_enable(h, level, True)
+    for i in range(launches):
+        flush.fill_((warm + i) & 0xFF)
+        fn()
+    torch.cuda.synchronize()
+    ms, n = mg.mg_timing_read(h, level)
+    mg.mg_timing_enable(h, level, False)
+    del flush
+    return ms / 1e3 / max(n, 1)
+
+
 def run_scale(mg, torch, np, dev, peaks, peak_kind, nrhs=16, Ls=1024):
     """The scale-up workload: one 1024^2 configuration (2000 sweeps, tuned m0),
     hierarchy 1024^2 x 2 -> 256^2 x 24 -> 64^2 x 24, GMRES-DR(40,16) on the
@@ -334,7 +354,7 @@ def run_scale(mg, torch, np, dev, peaks, peak_kind, nrhs=16, Ls=1024):
         y1 = torch.empty_like(x1)
         t_mma = timed_launches(torch, dev, lambda: mg.mg_apply_block(h, 1, x1, y1, nrhs, mg.MG_F16))
         b_mma = 5 * 576 * 4 * s1 + 2 * nrhs * n1 * 8  # FP16 operator once, 16 vectors in and out (complex64)
-        t_f32 = timed_launches(torch, dev, lambda: mg.mg_apply(h, 1, x1[0], y1[0], precision=mg.MG_F32))
+        t_f32 = timed_level_applies(mg, torch, dev, h, 1, lambda: mg.mg_apply(h, 1, x1[0], y1[0], precision=mg.MG_F32))
         b_f32 = (LR_SITE + 2 * 24) * 8 * s1
     finally:
         h.close()
@@ -994,8 +1014,8 @@ def run_micro(args):
                     x = x.to(torch.complex128)
                 y = torch.empty_like(x)
                 pa = mg.MG_F64 if args.micro_f64 else mg.MG_F32
-                t = timed_launches(torch, dev, lambda: mg.mg_apply(h, 1, x, y, precision=pa),
-                                   launches=args.micro_reps, warm=1)
+                t = timed_level_applies(mg, torch, dev, h, 1, lambda: mg.mg_apply(h, 1, x, y, precision=pa),
+                                        launches=args.micro_reps, warm=1)
                 fac, err = mg.mg_stencil_info(h, 1)
                 esz = 16 if args.micro_f64 else 8
                 nbytes = ((LR_SITE if fac else 5 * 576) + 2 * 24) * esz * s1
