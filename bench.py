@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--serve-budget-gib", type=float, default=64.0,
                     help="HBM budget of the server's resident hierarchies (below the stream's total need)")
     ap.add_argument("--serve-workers", type=int, default=8)
+    ap.add_argument("--coarse-mma", type=int, choices=[0, 1], default=1,
+                    help="mixed-precision handles: coarse GMRES-Proj apply on tensor cores (1) or FP32 FMAs (0)")
     ap.add_argument("--micro", choices=["bstencil", "coarse_block", "stencil", "wilson"], default=None,
                     help="time one kernel alone (the target of the ncu captures) instead of the benchmark")
     ap.add_argument("--micro-lattice", type=int, default=256)
@@ -610,7 +612,7 @@ def run_native(args):
         return replicas.max_over_ranks(v, device=dev)
 
     # ---------------- mixed precision (headline) ----------------
-    hs, setup_s = make_handles(mg.MG_MIXED)
+    hs, setup_s = make_handles(mg.MG_MIXED, coarse_mma=args.coarse_mma)
     run_steps(hs, range(W), False)
     clk = Clocks(local)
     ms, lat, iters, worst, launches, _ = run_steps(hs, range(W, W + K), True)
@@ -711,7 +713,7 @@ def run_native(args):
     # ---------- the paper's partial intermediate solve (Section 2 variant), mixed ----------
     partial = None
     if not args.no_partial:
-        hsp, setupp = make_handles(mg.MG_MIXED, partial_tol=0.2)
+        hsp, setupp = make_handles(mg.MG_MIXED, partial_tol=0.2, coarse_mma=args.coarse_mma)
         run_steps(hsp, range(W), False)
         msp, latp, itp, worstp, _, _ = run_steps(hsp, range(W, W + K), True)
         msp = max_over_ranks(msp)

@@ -97,7 +97,8 @@ typedef struct {
                               sides in lockstep on two contexts, and their coarsest solves run as
                               one cluster kernel that streams the coarse operator once for both
                               (mixed precision, V-cycle, deflated coarse solve, device buffers;
-                              the results equal those of separate solves).  0 (default): one
+                              the paired kernel applies with FP32 FMAs, and the results equal
+                              those of separate solves with coarse_mma = 0).  0 (default): one
                               right-hand side per worker */
     int vcycle_graph;      /* 1 (default): in mixed precision, once the deflation space exists, the
                               V-cycle (grid-0 and grid-1 smoothing and transfers, the coarse
@@ -127,6 +128,12 @@ typedef struct {
                               Gram-Schmidt of each dense block at set-up; a block whose rank-4
                               reconstruction errs by more than 1e-11 relative keeps the handle
                               dense (mg_solve_stats is unaffected) */
+    int coarse_mma;        /* 1 (default): with coarse_half, the single-right-hand-side GMRES-Proj
+                              cluster kernel applies the FP16 operator on tensor cores (mma.sync
+                              m16n8k16, FP32 accumulation) to each basis vector split into two
+                              FP16 parts (22 bits), where it holds the blocks of three directions
+                              in shared memory and runs CGS2 in dataflow mode (the 256^2 lattice's
+                              16^2 x 24 coarse grid and smaller); elsewhere, and with 0, FP32 FMAs */
 } mg_params;
 
 /* solver of mg_solve (Section 2 compares both) */
@@ -284,6 +291,7 @@ typedef struct {
     int paired;          /* 1: the two-right-hand-side kernel */
     long long cycles;    /* GMRES cycles of right-hand side 0 */
     long long timeouts;  /* CTAs in which a bounded wait gave up */
+    int tensor_apply;    /* 1: the apply ran on tensor cores (mg_params.coarse_mma) */
 } mg_coarse_info;
 
 /*

@@ -34,6 +34,7 @@ class MGParams(ctypes.Structure):
         ("coarse_tol_partial", ctypes.c_double), ("partial_max_iters", ctypes.c_int), ("pair_rhs", ctypes.c_int),
         ("vcycle_graph", ctypes.c_int), ("coarse_half", ctypes.c_int),
         ("coarse_dcgs2", ctypes.c_int), ("rhs_block", ctypes.c_int), ("lowrank_hops", ctypes.c_int),
+        ("coarse_mma", ctypes.c_int),
     ]
 
 
@@ -64,7 +65,7 @@ class MGCoarseInfo(ctypes.Structure):
     _fields_ = [
         ("ctas", ctypes.c_int), ("sites_per_cta", ctypes.c_int), ("dataflow", ctypes.c_int), ("dcgs2", ctypes.c_int),
         ("half_operator", ctypes.c_int), ("shared_blocks", ctypes.c_int), ("paired", ctypes.c_int),
-        ("cycles", ctypes.c_longlong), ("timeouts", ctypes.c_longlong),
+        ("cycles", ctypes.c_longlong), ("timeouts", ctypes.c_longlong), ("tensor_apply", ctypes.c_int),
     ]
 
 

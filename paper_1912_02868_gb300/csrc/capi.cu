@@ -134,6 +134,7 @@ mg_status check_params(const mg_params& p) {
     if (p.coarse_half != 0 && p.coarse_half != 1) return set_error("coarse_half must be 0 or 1"), MG_EINVAL;
     if (p.coarse_dcgs2 != 0 && p.coarse_dcgs2 != 1) return set_error("coarse_dcgs2 must be 0 or 1"), MG_EINVAL;
     if (p.lowrank_hops != 0 && p.lowrank_hops != 1) return set_error("lowrank_hops must be 0 or 1"), MG_EINVAL;
+    if (p.coarse_mma != 0 && p.coarse_mma != 1) return set_error("coarse_mma must be 0 or 1"), MG_EINVAL;
     return MG_OK;
 }
 
@@ -574,6 +575,7 @@ mg_status mg_default_params(mg_params* p) {
     p->coarse_dcgs2 = 0;
     p->rhs_block = 64;
     p->lowrank_hops = 1;
+    p->coarse_mma = 1;
     return MG_OK;
 }
 

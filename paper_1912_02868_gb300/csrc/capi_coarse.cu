@@ -46,6 +46,7 @@ CoopArgs<T> coarse_args(Handle& H, const C2<T>* f, C2<T>* x, C2<T>* r, C2<T>* V,
     a.out = out;
     a.Ah = std::is_same<T, float>::value ? H.A16c : nullptr;
     a.dc = H.p.coarse_dcgs2;
+    a.mma = H.p.coarse_mma;
     return a;
 }
 
@@ -170,6 +171,7 @@ mg_status mg_coarse_solve(mg_handle h, int precision, int nrhs, const void* b, v
         info->half_operator = cs[0].half;
         info->shared_blocks = cs[0].ash;
         info->paired = cs[0].paired;
+        info->tensor_apply = cs[0].mma;
         info->cycles = cs[0].cycles;
         info->timeouts = timeouts;
     }

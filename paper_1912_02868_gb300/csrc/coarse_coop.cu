@@ -201,6 +201,137 @@ __device__ __forceinline__ C2<T> half_entry(const unsigned* p) {
     return half_bits<T>(__ldg(p));
 }
 
+// ---- tensor-core apply of the FP16 operator (a.mma) ----
+// The staged vector holds each complex entry x as two FP16 pairs: hi = (Re, Im)
+// of x 2^10 rounded to FP16, lo = the same of the remainder, in the two words of
+// one 8-byte slot.  2^10 keeps both parts normal for the entries of a unit
+// vector and leaves a factor 64 below the FP16 range; hi + lo carries 22 bits.
+constexpr float TC_XS = 1024.f;
+constexpr float TC_XS_INV = 1.f / 1024.f;
+
+__device__ __forceinline__ float2 tc_split(float2 v) {
+    const __half2 hi = __floats2half2_rn(v.x * TC_XS, v.y * TC_XS);
+    const float2 hf = __half22float2(hi);
+    // v 2^10 - hi is exact in FP32 (hi is v 2^10 rounded to 11 bits)
+    const __half2 lo = __floats2half2_rn(fmaf(v.x, TC_XS, -hf.x), fmaf(v.y, TC_XS, -hf.y));
+    return make_float2(__uint_as_float(*reinterpret_cast<const unsigned*>(&hi)),
+                       __uint_as_float(*reinterpret_cast<const unsigned*>(&lo)));
+}
+template <typename T>
+__device__ __forceinline__ C2<T> stage_value(C2<T> v, bool split) {
+    if constexpr (std::is_same<T, float>::value) return split ? tc_split(v) : v;
+    return v;
+}
+
+// Word of the B fragment that lane column n = g (0..7) takes from a staged entry
+// p (rows 2l, 2l + 1 of the real form): n = 0: (Re hi, -Im hi), 1: (Im hi, Re hi),
+// 2 and 3: the same of lo, 4..7: zero.  The low half is the lower row.
+__device__ __forceinline__ unsigned tc_bword(float2 p, int g) {
+    const unsigned src = __float_as_uint((g & 2) ? p.y : p.x);
+    const unsigned w = (g & 1) ? __byte_perm(src, 0u, 0x1032) : (src ^ 0x80000000u);
+    return g < 4 ? w : 0u;
+}
+
+__device__ __forceinline__ void tc_mma(float (&c)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3, unsigned b0,
+                                       unsigned b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// w = sum_d A_d x_d for one own site on tensor cores (m16n8k16, FP16 inputs,
+// FP32 accumulation), by one whole warp.  Each complex product is the real
+// product A'' B'': A'' (24 x 48) has Re and Im of column l of A_d in columns
+// 2l and 2l + 1, so a stored FP16 word (real part in the low half) is already
+// an element pair of an A fragment; B'' (48 x 8) holds in rows 2l, 2l + 1 the
+// pairs of tc_bword for the staged x_d[l].  Then Re w = (column 0 + column 2)
+// 2^-10 and Im w = (column 1 + column 3) 2^-10.  The 24 rows are two M tiles,
+// the second with rows 24..31 zero; the 5 directions x 24 columns are 15 K
+// tiles.  Blocks are column-major: entry (row i, column l) of direction d is
+// word (d 24 + l) 24 + i.  Directions < ASH_DIRS come from shared memory, the
+// others from the FP16 operator in global memory, whose fragments
+// (tc_load_stream) are loaded first, so that their latency overlaps the
+// shared-memory directions, which every site accumulates first.
+constexpr int TC_SW = (5 - ASH_DIRS) * 3 * 6;  // stream fragment words a lane holds for one site
+struct TcAcc {
+    float m0[4], m1[4];  // M tiles 0 (rows 0..15) and 1 (rows 16..23)
+};
+__device__ __forceinline__ void tc_zero(TcAcc& c) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) c.m0[u] = c.m1[u] = 0.f;
+}
+// the A fragments of direction d, K tile kt from a site's blocks p (lane offset applied)
+__device__ __forceinline__ void tc_frag(const unsigned* p, unsigned (&q)[6]) {
+    q[0] = p[0];
+    q[1] = p[8];
+    q[2] = p[4 * NDOF];
+    q[3] = p[4 * NDOF + 8];
+    q[4] = p[16];
+    q[5] = p[4 * NDOF + 16];
+}
+__device__ __forceinline__ void tc_step(TcAcc& c, const unsigned (&q)[6], float2 x0, float2 x1, int g) {
+    const unsigned b0 = tc_bword(x0, g), b1 = tc_bword(x1, g);
+    tc_mma(c.m0, q[0], q[1], q[2], q[3], b0, b1);
+    tc_mma(c.m1, q[4], 0u, q[5], 0u, b0, b1);
+}
+// fragments of the streamed directions of one site (Ag: the site's blocks)
+__device__ __forceinline__ void tc_load_stream(const unsigned* __restrict__ Ag, unsigned (&f)[TC_SW], int lane) {
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int d = ASH_DIRS; d < 5; ++d)
+#pragma unroll
+        for (int kt = 0; kt < 3; ++kt) {
+            const unsigned* p = Ag + (d * NDOF + 8 * kt + t) * NDOF + g;
+            unsigned* q = f + ((d - ASH_DIRS) * 3 + kt) * 6;
+            q[0] = __ldg(p);
+            q[1] = __ldg(p + 8);
+            q[2] = __ldg(p + 4 * NDOF);
+            q[3] = __ldg(p + 4 * NDOF + 8);
+            q[4] = __ldg(p + 16);
+            q[5] = __ldg(p + 4 * NDOF + 16);
+        }
+}
+__device__ __forceinline__ void tc_stream_dirs(TcAcc& c, const unsigned (&f)[TC_SW], const float2 (*xs)[NDOF],
+                                               int lane) {
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int d = ASH_DIRS; d < 5; ++d)
+#pragma unroll
+        for (int kt = 0; kt < 3; ++kt) {
+            unsigned q[6];
+#pragma unroll
+            for (int u = 0; u < 6; ++u) q[u] = f[((d - ASH_DIRS) * 3 + kt) * 6 + u];
+            tc_step(c, q, xs[d][8 * kt + t], xs[d][8 * kt + t + 4], g);
+        }
+}
+// As: the site's shared-memory blocks
+__device__ __forceinline__ void tc_shared_dirs(TcAcc& c, const unsigned* As, const float2 (*xs)[NDOF], int lane) {
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int d = 0; d < ASH_DIRS; ++d)
+#pragma unroll
+        for (int kt = 0; kt < 3; ++kt) {
+            unsigned q[6];
+            tc_frag(As + (d * NDOF + 8 * kt + t) * NDOF + g, q);
+            tc_step(c, q, xs[d][8 * kt + t], xs[d][8 * kt + t + 4], g);
+        }
+}
+// out[0..23] = c 2^-10: lane t = 0 holds columns 0, 1 (hi) and lane t = 1
+// columns 2, 3 (lo) of rows g, g + 8 (M tile 0) and 16 + g (M tile 1)
+__device__ __forceinline__ void tc_store(const TcAcc& c, float2* out, int lane) {
+    const int g = lane >> 2, t = lane & 3;
+    float r[6] = {c.m0[0], c.m0[1], c.m0[2], c.m0[3], c.m1[0], c.m1[1]};
+#pragma unroll
+    for (int u = 0; u < 6; ++u) r[u] += __shfl_xor_sync(0xffffffffu, r[u], 1);
+    if (t == 0) {
+        out[g] = make_float2(r[0] * TC_XS_INV, r[1] * TC_XS_INV);
+        out[g + 8] = make_float2(r[2] * TC_XS_INV, r[3] * TC_XS_INV);
+        out[g + 16] = make_float2(r[4] * TC_XS_INV, r[5] * TC_XS_INV);
+    }
+}
+
 // Store v at the address dst has in the shared memory of CTA `rank` of the
 // cluster (a plain shared-memory store when rank == me).
 template <typename T>
@@ -389,14 +520,16 @@ __device__ __forceinline__ long nbr_site(long s, int d, int Nx, int Nt) {
 }
 
 // Write element k of own row (site ls) of a new basis vector into the five
-// staging slots that read it (push mode).
+// staging slots that read it (push mode); split: as the tensor-core apply's
+// two FP16 parts (tc_split).
 template <typename T>
-__device__ __forceinline__ void push_row(ClusterSmem<T>& S, int me, int e, C2<T> v) {
+__device__ __forceinline__ void push_row(ClusterSmem<T>& S, int me, int e, C2<T> v, bool split) {
     const int ls = e / NDOF, kk = e - ls * NDOF;
+    const C2<T> sv = stage_value<T>(v, split);
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
         const int code = S.pusht[ls][q];
-        st_rank<T>(&S.xs[(code >> 3) & 0x1fff][code & 7][kk], code >> 16, me, v);
+        st_rank<T>(&S.xs[(code >> 3) & 0x1fff][code & 7][kk], code >> 16, me, sv);
     }
 }
 
@@ -437,16 +570,36 @@ __device__ void push_gram_flow(const C2<T>* X, long ldx, int nd, const C2<T>* y,
     }
 }
 template <typename T>
-__device__ __forceinline__ void push_row_flow(ClusterSmem<T>& S, int e, C2<T> v) {
+__device__ __forceinline__ void push_row_flow(ClusterSmem<T>& S, int e, C2<T> v, bool split) {
     const int ls = e / NDOF, kk = e - ls * NDOF;
     const unsigned bar = smem_addr(&S.mb[2]);
+    const C2<T> sv = stage_value<T>(v, split);
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
         const int code = S.pusht[ls][q], owner = code >> 16;
-        st_async(cluster_addr(smem_addr(&S.xs[(code >> 3) & 0x1fff][code & 7][kk]), owner), v,
+        st_async(cluster_addr(smem_addr(&S.xs[(code >> 3) & 0x1fff][code & 7][kk]), owner), sv,
                  cluster_addr(bar, owner));
     }
 }
+
+#ifdef CP_PHASE_CLOCKS
+// phase timing of thread 0 of CTA 0 (a build with -DCP_PHASE_CLOCKS): the cycles
+// of each phase of the dataflow Arnoldi step, averaged per launch and printed
+// for the first launches
+__device__ unsigned cp_clock_launches = 0;
+#define CP_STAMP(k)                              \
+    do {                                         \
+        if (clk) {                               \
+            const long long now = clock64();     \
+            acc_t[k] += now - t_prev;            \
+            t_prev = now;                        \
+        }                                        \
+    } while (0)
+#else
+#define CP_STAMP(k) \
+    do {            \
+    } while (0)
+#endif
 
 // At most 128 registers a thread, so that a CTA of up to 512 threads fits one
 // SM (512 x 128 = 65536).  A solve is latency-bound; the registers go to more
@@ -506,6 +659,15 @@ __global__ void __maxnreg__(128) k_coarse_proj(CoopArgs<T> a) {
     // received this CTA's contribution to a later exchange, which this CTA makes
     // after it has read the buffer.
     const bool flow = push && a.flow;
+    // tensor-core apply (tc_apply_site): FP32 dataflow mode with the FP16 operator,
+    // its first directions in shared memory, and CGS2; the staging slots then hold
+    // split values
+    const bool mma = std::is_same<T, float>::value && flow && a.ash && a.mma && !a.dc;
+#ifdef CP_PHASE_CLOCKS
+    const bool clk = rank == 0 && tid == 0 && atomicAdd(&cp_clock_launches, 1u) < 48u;
+    long long acc_t[7] = {0, 0, 0, 0, 0, 0, 0}, t_prev = clock64();
+    int clk_steps = 0;
+#endif
     const long spin = a.spin > 0 ? a.spin : FLOW_SPIN;
     unsigned fph[3] = {0u, 0u, 0u};  // parity of the next phase of each barrier (row warps)
     // A wait that gives up marks the CTA faulted.  From then on the CTA skips
@@ -725,7 +887,7 @@ __global__ void __maxnreg__(128) k_coarse_proj(CoopArgs<T> a) {
             for (int e = tid; e < nrows; e += nt) {
                 const Z v = accum_rows<T, true>(w[e], Vl, ldv, e, S.h1, 1);
                 w[e] = v;
-                push_row_flow<T>(S, e, v);
+                push_row_flow<T>(S, e, v, mma);
             }
         }
         for (int j = 1; j < ms; ++j) {
@@ -778,7 +940,7 @@ __global__ void __maxnreg__(128) k_coarse_proj(CoopArgs<T> a) {
                 for (int e = tid; e < nrows; e += nwr * 32) {  // row warps only
                     const Z v = cscale(accum_rows<T, true>(wl[e], Vl, ldv, e, S.zc, j + 1), irho);
                     wl[e] = v;
-                    push_row_flow<T>(S, e, v);
+                    push_row_flow<T>(S, e, v, mma);
                 }
             }
             ++iters;
@@ -880,7 +1042,7 @@ __global__ void __maxnreg__(128) k_coarse_proj(CoopArgs<T> a) {
                 const Z v = cscale(rl[e], sc);
                 Vl[e] = v;
                 if (push)
-                    push_row<T>(S, rank, e, v);
+                    push_row<T>(S, rank, e, v, mma);
                 else if (a.vs)
                     a.V[r0 + e] = v;
             }
@@ -895,7 +1057,9 @@ __global__ void __maxnreg__(128) k_coarse_proj(CoopArgs<T> a) {
             Z* wl = Vl + (long)(j + 1) * ldv;
             // w = A v_j on the CTA's rows (column-major 24x24 blocks), MAX_SPC sites at a
             // time: stage the five neighbour rows of each site (other CTAs' rows: through L2)
+            CP_STAMP(6);
             if (flow && j > 0 && !ls_warp) flow_wait(2);  // v_j staged from every neighbour
+            CP_STAMP(0);
             for (int c0 = 0; c0 < my_sites; c0 += MAX_SPC) {
                 const int cs = min(MAX_SPC, my_sites - c0);
                 if (!push) {
@@ -906,7 +1070,23 @@ __global__ void __maxnreg__(128) k_coarse_proj(CoopArgs<T> a) {
                     }
                     __syncthreads();
                 }
-                if (a.Ah) {  // FP16 operator copy: half the bytes of the stream, FP32 arithmetic
+                if (mma) {  // push mode: c0 == 0, cs == my_sites
+                    if constexpr (std::is_same<T, float>::value) {
+                        // one site per row warp at a time; its streamed fragments are
+                        // loaded first and arrive during the shared-memory directions
+                        const int lane = tid & 31;
+                        if ((tid >> 5) < nwr)
+                            for (int ls = tid >> 5; ls < cs; ls += nwr) {
+                                unsigned f[TC_SW];
+                                tc_load_stream(a.Ah + (s0 + ls) * (5L * NDOF * NDOF), f, lane);
+                                TcAcc c;
+                                tc_zero(c);
+                                tc_shared_dirs(c, Ash + ls * ASH_SITE_WORDS, S.xs[ls], lane);
+                                tc_stream_dirs(c, f, S.xs[ls], lane);
+                                tc_store(c, wl + (long)ls * NDOF, lane);
+                            }
+                    }
+                } else if (a.Ah) {  // FP16 operator copy: half the bytes of the stream, FP32 arithmetic
                     for (int e = tid; e < cs * NDOF; e += nt) {
                         const int ls = e / NDOF, kk = e - ls * NDOF;
                         const unsigned* Ab = a.Ah + (s0 + c0 + ls) * (5L * NDOF * NDOF) + kk;
@@ -948,6 +1128,7 @@ __global__ void __maxnreg__(128) k_coarse_proj(CoopArgs<T> a) {
                 }
                 __syncthreads();
             }
+            CP_STAMP(1);
             if (a.lsw && j > 0) {  // step j - 1's update is complete (apply barrier)
                 conv = S.ctl[0];
                 if (S.ctl[0] | S.ctl[1]) break;  // step j is discarded: j columns
@@ -960,9 +1141,11 @@ __global__ void __maxnreg__(128) k_coarse_proj(CoopArgs<T> a) {
                 push_gram<T>(cluster, Vl, ldv, j + 1, wl, nrows, false, &S.inbox[1][0][0], nwr);
                 cluster.sync();
             }
+            CP_STAMP(2);
             reduce_inbox<T>(&S.inbox[1][0][0], ncta, j + 1, S.h1, nwr);
             for (int e = tid; e < nrows; e += nt) wl[e] = accum_rows<T, true>(wl[e], Vl, ldv, e, S.h1, j + 1);
             __syncthreads();
+            CP_STAMP(3);
             if (flow) {
                 arm(0, (unsigned)(ncta * (j + 2) * sizeof(Z)));
                 push_gram_flow<T>(Vl, ldv, j + 1, wl, nrows, true, &S.inbox[0][0][0], &S.mb[0], ncta, rank, nwr);
@@ -971,6 +1154,7 @@ __global__ void __maxnreg__(128) k_coarse_proj(CoopArgs<T> a) {
                 push_gram<T>(cluster, Vl, ldv, j + 1, wl, nrows, true, &S.inbox[0][0][0], nwr);
                 cluster.sync();
             }
+            CP_STAMP(4);
             reduce_inbox<T>(&S.inbox[0][0][0], ncta, j + 2, S.red, nwr);
             // h_{j+1,j} = ||w - V h2|| = sqrt(n2 - |h2|^2) (V orthonormal), computed
             // identically by every thread; then v_{j+1} = (w - V h2) / h_{j+1,j}
@@ -987,13 +1171,17 @@ __global__ void __maxnreg__(128) k_coarse_proj(CoopArgs<T> a) {
                     const Z v = cscale(accum_rows<T, true>(wl[e], Vl, ldv, e, S.red, j + 1), sc);
                     wl[e] = v;
                     if (flow)
-                        push_row_flow<T>(S, e, v);
+                        push_row_flow<T>(S, e, v, mma);
                     else if (push)
-                        push_row<T>(S, rank, e, v);
+                        push_row<T>(S, rank, e, v, mma);
                     else if (a.vs)
                         wg[e] = v;
                 }
             }
+            CP_STAMP(5);
+#ifdef CP_PHASE_CLOCKS
+            ++clk_steps;
+#endif
             if (flow) {
                 // no barrier: the next apply waits for its staging slots instead; the
                 // least-squares warp updates step j meanwhile
@@ -1057,7 +1245,15 @@ __global__ void __maxnreg__(128) k_coarse_proj(CoopArgs<T> a) {
         a.out->ash = a.ash;
         a.out->half = a.Ah ? 1 : 0;
         a.out->paired = 0;
+        a.out->mma = mma ? 1 : 0;
     }
+#ifdef CP_PHASE_CLOCKS
+    if (clk && clk_steps > 0)
+        printf("coarse_proj phases (cycles/step over %d steps, mma %d): staging wait %lld, apply %lld, gram1+wait %lld, "
+               "reduce+update %lld, gram2+wait %lld, reduce+v+push %lld, other %lld\n",
+               clk_steps, mma ? 1 : 0, acc_t[0] / clk_steps, acc_t[1] / clk_steps, acc_t[2] / clk_steps,
+               acc_t[3] / clk_steps, acc_t[4] / clk_steps, acc_t[5] / clk_steps, acc_t[6] / clk_steps);
+#endif
     cluster.sync();  // no CTA leaves while others may still read its shared memory
 }
 
@@ -1551,6 +1747,7 @@ __global__ void __maxnreg__(128) k_coarse_proj_pair(CoopArgs<T> a0, CoopArgs<T> 
             o->ash = 0;
             o->half = a0.Ah ? 1 : 0;
             o->paired = 1;
+            o->mma = 0;
         }
         a0.out->iters += iters[0];
         a0.out->cycles += cycles;

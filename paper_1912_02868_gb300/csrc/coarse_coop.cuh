@@ -13,8 +13,8 @@ struct CoopStats {
     long long timeouts;  // CTAs in which a bounded wait of the dataflow exchange gave up
     // shape of the last launch (written by its CTA 0): cluster size, coarse
     // sites per CTA, dataflow exchange, delayed CGS2, FP16 blocks in shared
-    // memory, FP16 operator stream, two-right-hand-side kernel
-    int ctas, spc, flow, dc, ash, half, paired, pad;
+    // memory, FP16 operator stream, two-right-hand-side kernel, tensor-core apply
+    int ctas, spc, flow, dc, ash, half, paired, mma;
 };
 
 template <typename T>
@@ -46,6 +46,9 @@ struct CoopArgs {
     long spin;         // try_wait rounds before a dataflow wait gives up (0: the default, 2^20)
     int probe;         // 1 (tests): before the first cycle every row thread waits, bounded by
                        // `spin`, on a barrier that nothing completes, so the give-up path runs
+    int mma;           // 1: the apply runs on tensor cores where the kernel can (FP32 dataflow mode
+                       // with the FP16 blocks in shared memory, CGS2): FP16 operator times the
+                       // vector split into two FP16 parts, FP32 accumulation
 };
 
 template <typename T>

@@ -308,6 +308,7 @@ CoopArgs<T> proj_args(Handle& H, const C2<T>* f, C2<T>* x) {
     a.out = H.cstats;
     a.Ah = std::is_same<T, float>::value ? H.A16c : nullptr;
     a.dc = H.p.coarse_dcgs2;
+    a.mma = H.p.coarse_mma;
     return a;
 }
 

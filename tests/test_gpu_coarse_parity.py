@@ -19,7 +19,10 @@ oracle's GMRES-DR space, loaded with mg_set_deflation):
   run in FP64 on the same FP16-rounded operator: step counts within 2%, the
   solutions within 1e-4 (measured 1e-6), and a true residual with the rounded
   operator no worse than the oracle's own (the projection uses the deflation
-  relation of the exact operator, so both level off near 1e-3);
+  relation of the exact operator, so both level off near 1e-3); with the apply
+  on tensor cores (FP16 operator times the vector split into two FP16 parts,
+  mg_params.coarse_mma) and with FP32 FMAs, the reported launch showing which
+  ran;
 * delayed CGS2 and the two-right-hand-side kernel: the launch shape they report
   shows that the path ran, and the results meet the same checks;
 * a bounded wait that gives up (a probe barrier that nothing completes) makes
@@ -102,10 +105,11 @@ def test_coarse_fp64_parity(mgmod, L):
         g.close()
 
 
+@pytest.mark.parametrize("mma", [1, 0])
 @pytest.mark.parametrize("L", [64, 256])
-def test_coarse_fp32_half_operator_parity(mgmod, L):
+def test_coarse_fp32_half_operator_parity(mgmod, L, mma):
     import torch
-    g, h, defl = _handle(mgmod, L, precision=mgmod.MG_MIXED)
+    g, h, defl = _handle(mgmod, L, precision=mgmod.MG_MIXED, coarse_mma=mma)
     try:
         n2 = h.size(2)
         tol = 1e-5
@@ -120,6 +124,7 @@ def test_coarse_fp32_half_operator_parity(mgmod, L):
         assert (info["ctas"], info["sites_per_cta"]) == EXPECT_SHAPE[L]
         if L == 256:
             assert info["shared_blocks"] == 1
+        assert info["tensor_apply"] == (mma if info["shared_blocks"] else 0)
         assert abs(it[0] - io.iters) <= max(2, 0.02 * io.iters), (it[0], io.iters)
         assert rel2(xg, xo) <= 1e-4
         assert _relres(A16, xg, b, h.shapes[2]) <= 1.5 * _relres(A16, xo, b, h.shapes[2]) + tol

@@ -7,7 +7,9 @@ solutions agree to rounding and the outer iteration counts are equal.  The two
 cluster kernels are compiled separately, so the compiler may contract a few
 products differently; where a coarse stopping test then lands within rounding
 of its threshold, a coarse solve takes a step more or less, so the coarse step
-totals agree to 0.1%.
+totals agree to 0.1%.  The paired kernel applies the coarse operator with FP32
+FMAs, so both sides run with coarse_mma = 0 (singles would otherwise use the
+tensor-core apply, which rounds differently).
 """
 import numpy as np
 import pytest
@@ -36,7 +38,8 @@ def test_pairs_equal_sequential(mgmod, L, nrhs, par):
     B = synth.rhs(L, c, 0, nrhs=nrhs)
     out = {}
     for mode, over in (("seq", dict(parallel=1)), ("pairs", dict(parallel=par, pair_rhs=1))):
-        g = mgmod.mg_setup(dev(U), L, L, m0, params=mgmod.default_params(precision=mgmod.MG_MIXED, **over), **starts)
+        g = mgmod.mg_setup(dev(U), L, L, m0,
+                           params=mgmod.default_params(precision=mgmod.MG_MIXED, coarse_mma=0, **over), **starts)
         try:
             X = torch.zeros(B.shape, dtype=torch.complex128, device="cuda")
             st, iters, relres, stats = mgmod.mg_solve(g, dev(B), X, nrhs, 1e-8)
