@@ -653,8 +653,8 @@ def run_native(args):
     roofline = {"bound": "hbm", "achieved": c_ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": c_ach / peaks["hbm_gbs"],
                 "traffic": profile_of("coarse_proj_f32_256.json").get("dram_bytes_per_launch"),
-                "kernel": "k_coarse_proj<float> (whole coarse GMRES-Proj solve, 16^2 x 24, FP16 operator, "
-                          "cluster of 16 CTAs)",
+                "kernel": "k_coarse_proj<float> (whole coarse GMRES-Proj solve, 16^2 x 24, FP16 operator"
+                          + (" applied on tensor cores" if args.coarse_mma else "") + ", cluster of 16 CTAs)",
                 "bytes_per_launch": c_bytes, "steps_per_launch": steps_per_launch,
                 "us_per_step": 1e6 * c_avg / max(steps_per_launch, 1), "avg_launch_us": c_avg * 1e6,
                 "launches": c_n, "share_of_timed_gpu_time": share, "peak_source": peak_kind,
