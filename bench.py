@@ -878,6 +878,20 @@ def study_methods(mg):
     }
 
 
+def fit_power(sizes, mvps):
+    """The power alpha of Table 1 (Section 3): least squares of log Mvps against
+    log size, size = L^2 sites, for lattice sizes L.  Returns (alpha, its
+    standard error from the residuals, with at least one degree of freedom)."""
+    import numpy as np
+    xv = np.log(np.array(sizes, dtype=float) ** 2)
+    yv = np.log(np.array(mvps, dtype=float))
+    A = np.stack([xv, np.ones_like(xv)], axis=1)
+    coef = np.linalg.lstsq(A, yv, rcond=None)[0]
+    dof = max(len(sizes) - 2, 1)
+    s2 = float(np.sum((yv - A @ coef) ** 2)) / dof
+    return float(coef[0]), float(np.sqrt(s2 * np.linalg.inv(A.T @ A)[0, 0]))
+
+
 def run_study(args):
     """Counter studies of the paper's Section 3 on the synthetic configurations,
     FP64, one Z(4) right-hand side (the paper's noise) per configuration and
@@ -945,14 +959,8 @@ def run_study(args):
                 per_size.append(float(np.mean([r["fine_equiv_mvps"] for r in ok])) if ok else None)
             fit = {"mean_fine_equiv_mvps": dict(zip(map(str, sizes), per_size)), "converged": conv}
             if all(v is not None for v in per_size):
-                xv = np.log(np.array(sizes, dtype=float) ** 2)
-                yv = np.log(np.array(per_size))
-                A = np.stack([xv, np.ones_like(xv)], axis=1)
-                coef = np.linalg.lstsq(A, yv, rcond=None)[0]
-                dof = max(len(sizes) - 2, 1)
-                s2 = float(np.sum((yv - A @ coef) ** 2)) / dof
-                se = float(np.sqrt(s2 * np.linalg.inv(A.T @ A)[0, 0]))
-                fit.update({"alpha_volume": float(coef[0]), "alpha_volume_se": se, "alpha_per_L": 2 * float(coef[0])})
+                alpha, se = fit_power(sizes, per_size)
+                fit.update({"alpha_volume": alpha, "alpha_volume_se": se, "alpha_per_L": 2 * alpha})
             else:
                 fit["alpha_volume"] = None  # some size had no converged run
             fits[name] = fit
