@@ -613,6 +613,11 @@ def run_native(args):
 
     # ---------------- mixed precision (headline) ----------------
     hs, setup_s = make_handles(mg.MG_MIXED, coarse_mma=args.coarse_mma)
+    # launch shapes the set-up's autotuner chose (the same for every handle of this size)
+    shapes = {}
+    for lvl in range(3):
+        sh, t_c, t_b = mg.mg_launch_shape(hs[0], lvl, mg.MG_F32)
+        shapes[f"level{lvl}_f32"] = {"shape": sh, "us": t_c, "builtin_us": t_b}
     run_steps(hs, range(W), False)
     clk = Clocks(local)
     ms, lat, iters, worst, launches, _ = run_steps(hs, range(W, W + K), True)
@@ -845,6 +850,7 @@ def run_native(args):
                    "parallelism": f"replicas x{world}", "m0_fingerprints_match": fp_ok},
         "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
         "outer_iters_mean": float(np.mean(iters)), "setup_s": setup_s,
+        "launch_shapes": shapes,
         "fp64": fp64,
         "partial_solve": partial,
         "batching_64rhs": batching,

@@ -128,6 +128,11 @@ typedef struct {
                               Gram-Schmidt of each dense block at set-up; a block whose rank-4
                               reconstruction errs by more than 1e-11 relative keeps the handle
                               dense (mg_solve_stats is unaffected) */
+    int autotune;          /* 1 (default): at set-up, each level apply (the fine Wilson-Dirac
+                              apply; the FP32 block stencils of grids 1 and 2) is timed with every
+                              candidate launch shape and the fastest kept (mg_launch_shape).  A
+                              shape only groups sites into blocks, so results are the same bit for
+                              bit with any choice.  0: the built-in shapes */
     int coarse_mma;        /* 1 (default): with coarse_half, the single-right-hand-side GMRES-Proj
                               cluster kernel applies the FP16 operator on tensor cores (mma.sync
                               m16n8k16, FP32 accumulation) to each basis vector split into two
@@ -333,6 +338,23 @@ mg_status mg_level_shape(mg_handle h, int level, int* n_x, int* n_t, int* dof);
  * NULL) the largest relative Frobenius error of those factors against the dense
  * blocks (0 when not factored). */
 mg_status mg_stencil_info(mg_handle h, int level, int* factored, double* max_rel_err);
+
+/* Launch shape of the apply of `level` (0..2) in `precision` (MG_F64 or MG_F32), as
+ * the set-up's autotuner chose it (mg_params.autotune): *shape = 0 for the built-in
+ * shape, else threads per block (level 0) or sites per block (FP32 stencils of
+ * levels 1 and 2).  us (host, double[2], or NULL): the time of one apply with the
+ * chosen and with the built-in shape, in microseconds, as timed at set-up on this
+ * GPU (0 where nothing was tuned: FP64 stencils, autotune off).  The shape never
+ * changes results: it only groups sites into blocks. */
+mg_status mg_launch_shape(mg_handle h, int level, int precision, int* shape, double* us);
+
+/* Pin the launch shape of the apply of `level` in `precision`: 0 (built-in), or one
+ * of the candidates the autotuner tries: 64, 128, 256 threads per block at level 0;
+ * 4, 8, 12, 16 sites per block for the FP32 stencil with rank-4 hop factors; 4, 8,
+ * 16, 24, 32 for the dense FP32 stencil.  The FP64 stencils take 0 only.  A captured
+ * V-cycle graph of the handle is dropped and captured again; solve contexts made
+ * afterwards copy the shape.  MG_EINVAL for any other shape. */
+mg_status mg_set_launch_shape(mg_handle h, int level, int precision, int shape);
 
 /*
  * Standalone Wilson-Dirac apply without a hierarchy (Section 2):

@@ -23,8 +23,8 @@ from ._lib import (MG_COARSE_CGNE, MG_COARSE_DR_PROJ, MG_F32, MG_F64, MG_BF16, M
 
 __all__ = ["build", "default_params", "mg_setup", "mg_setup_from_vectors", "mg_solve", "mg_destroy",
            "mg_reset_deflation", "mg_apply", "mg_restrict", "mg_prolong", "mg_get_stencil",
-           "mg_get_prolongator", "mg_get_deflation", "mg_level_shape", "mg_stencil_info", "mg_wilson_apply",
-           "mg_timing_enable",
+           "mg_get_prolongator", "mg_get_deflation", "mg_level_shape", "mg_stencil_info", "mg_launch_shape",
+           "mg_set_launch_shape", "mg_wilson_apply", "mg_timing_enable",
            "mg_timing_read", "mg_kernel_launches", "mg_wilson_residual_noalloc", "mg_set_deflation",
            "mg_coarse_solve", "mg_apply_block", "Handle"]
 
@@ -193,6 +193,20 @@ def mg_stencil_info(h: Handle, level):
     f, e = ctypes.c_int(), ctypes.c_double()
     _lib.check(load().mg_stencil_info(h.ptr, level, ctypes.byref(f), ctypes.byref(e)), "mg_stencil_info")
     return bool(f.value), e.value
+
+
+def mg_launch_shape(h: Handle, level, precision=MG_F32):
+    """(shape, us_chosen, us_builtin): the launch shape the set-up's autotuner chose
+    for `level`'s apply in `precision` (0 = the built-in shape) and the times of one
+    apply with it and with the built-in shape."""
+    sh, us = ctypes.c_int(), (ctypes.c_double * 2)()
+    _lib.check(load().mg_launch_shape(h.ptr, level, precision, ctypes.byref(sh), us), "mg_launch_shape")
+    return sh.value, us[0], us[1]
+
+
+def mg_set_launch_shape(h: Handle, level, precision, shape):
+    """Pin the launch shape of `level`'s apply in `precision` (0 = built-in)."""
+    _lib.check(load().mg_set_launch_shape(h.ptr, level, precision, shape), "mg_set_launch_shape")
 
 
 def mg_get_stencil(h: Handle, level) -> np.ndarray:

@@ -34,7 +34,7 @@ class MGParams(ctypes.Structure):
         ("coarse_tol_partial", ctypes.c_double), ("partial_max_iters", ctypes.c_int), ("pair_rhs", ctypes.c_int),
         ("vcycle_graph", ctypes.c_int), ("coarse_half", ctypes.c_int),
         ("coarse_dcgs2", ctypes.c_int), ("rhs_block", ctypes.c_int), ("lowrank_hops", ctypes.c_int),
-        ("coarse_mma", ctypes.c_int),
+        ("autotune", ctypes.c_int), ("coarse_mma", ctypes.c_int),
     ]
 
 
@@ -76,8 +76,10 @@ _lib = None
 # every symbol declared in include/mg.h
 SYMBOLS = ("mg_default_params", "mg_setup", "mg_setup_from_vectors", "mg_solve", "mg_reset_deflation",
            "mg_destroy", "mg_last_error", "mg_apply", "mg_restrict", "mg_prolong", "mg_get_stencil",
-           "mg_get_prolongator", "mg_get_deflation", "mg_level_shape", "mg_stencil_info", "mg_wilson_apply",
-           "mg_timing_enable", "mg_timing_read", "mg_kernel_launches", "mg_server_create", "mg_server_submit",
+           "mg_get_prolongator", "mg_get_deflation", "mg_level_shape", "mg_stencil_info", "mg_launch_shape",
+           "mg_set_launch_shape",
+           "mg_wilson_apply", "mg_timing_enable", "mg_timing_read", "mg_kernel_launches", "mg_server_create",
+           "mg_server_submit",
            "mg_server_wait", "mg_server_poll", "mg_server_stats", "mg_server_destroy", "mg_wilson_residual_noalloc",
            "mg_set_deflation", "mg_coarse_solve", "mg_apply_block")
 
@@ -108,6 +110,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "mg_get_deflation": (i, [vp, vp, vp, ctypes.POINTER(i)]),
         "mg_level_shape": (i, [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]),
         "mg_stencil_info": (i, [vp, i, ctypes.POINTER(i), ctypes.POINTER(ctypes.c_double)]),
+        "mg_launch_shape": (i, [vp, i, i, ctypes.POINTER(i), ctypes.POINTER(ctypes.c_double)]),
+        "mg_set_launch_shape": (i, [vp, i, i, i]),
         "mg_wilson_apply": (i, [vp, i, i, d, i, i, vp, vp, vp]),
         "mg_timing_enable": (i, [vp, i, i]),
         "mg_timing_read": (i, [vp, i, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong)]),

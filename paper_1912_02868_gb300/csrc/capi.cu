@@ -135,6 +135,7 @@ mg_status check_params(const mg_params& p) {
     if (p.coarse_dcgs2 != 0 && p.coarse_dcgs2 != 1) return set_error("coarse_dcgs2 must be 0 or 1"), MG_EINVAL;
     if (p.lowrank_hops != 0 && p.lowrank_hops != 1) return set_error("lowrank_hops must be 0 or 1"), MG_EINVAL;
     if (p.coarse_mma != 0 && p.coarse_mma != 1) return set_error("coarse_mma must be 0 or 1"), MG_EINVAL;
+    if (p.autotune != 0 && p.autotune != 1) return set_error("autotune must be 0 or 1"), MG_EINVAL;
     return MG_OK;
 }
 
@@ -522,6 +523,7 @@ mg_status setup_common(const void* gauge, int Lx, int Lt, double m0, int nvec, i
         set_error("set-up failed: %s", cudaGetErrorString(cudaGetLastError()));
         return fail(MG_ECUDA);
     }
+    if (p.autotune) TRYF(tune_shapes(H, s));
 #undef TRYF
     *out = hs;
     return MG_OK;
@@ -576,6 +578,7 @@ mg_status mg_default_params(mg_params* p) {
     p->rhs_block = 64;
     p->lowrank_hops = 1;
     p->coarse_mma = 1;
+    p->autotune = 1;
     return MG_OK;
 }
 
@@ -790,6 +793,43 @@ mg_status mg_stencil_info(mg_handle h, int level, int* factored, double* max_rel
     const Handle& H = h->h;
     *factored = H.L64[level].F ? 1 : 0;
     if (max_rel_err) *max_rel_err = H.L64[level].F ? H.lowrank_err : 0.0;
+    return MG_OK;
+}
+
+mg_status mg_launch_shape(mg_handle h, int level, int precision, int* shape, double* us) {
+    if (!h || level < 0 || level > 2 || !shape) return set_error("bad handle, level or output"), MG_EINVAL;
+    if (precision != MG_F64 && precision != MG_F32) return set_error("precision must be MG_F64 or MG_F32"), MG_EINVAL;
+    const Handle& H = h->h;
+    const int sh = precision == MG_F64 ? H.L64[level].shape : H.L32[level].shape;
+    const double* t = precision == MG_F64 ? H.L64[level].shape_us : H.L32[level].shape_us;
+    *shape = sh;
+    if (us) {
+        us[0] = t[0];
+        us[1] = t[1];
+    }
+    return MG_OK;
+}
+
+mg_status mg_set_launch_shape(mg_handle h, int level, int precision, int shape) {
+    if (!h || level < 0 || level > 2) return set_error("bad handle or level"), MG_EINVAL;
+    if (precision != MG_F64 && precision != MG_F32) return set_error("precision must be MG_F64 or MG_F32"), MG_EINVAL;
+    Handle& H = h->h;
+    if (H.is_context) return set_error("a solve context takes its owner's shapes"), MG_EINVAL;
+    const bool f32 = precision == MG_F32;
+    const bool wil = level == 0, lr = f32 ? H.L32[level].F != nullptr : false;
+    const int* cand = wil ? WILSON_SHAPES : lr ? STENCIL_LR_F32_SHAPES : STENCIL_F32_SHAPES;
+    const int nc = wil ? (int)(sizeof(WILSON_SHAPES) / sizeof(int))
+                       : lr ? (int)(sizeof(STENCIL_LR_F32_SHAPES) / sizeof(int))
+                            : (int)(sizeof(STENCIL_F32_SHAPES) / sizeof(int));
+    bool ok = shape == 0;
+    if (wil || f32)
+        for (int i = 0; i < nc; ++i) ok = ok || shape == cand[i];
+    if (!ok) return set_error("shape %d is not a candidate of this apply", shape), MG_EINVAL;
+    (f32 ? H.L32[level].shape : H.L64[level].shape) = shape;
+    if (H.vg.exec) {  // a captured V-cycle keeps the shapes it was captured with: capture again
+        cudaGraphExecDestroy(H.vg.exec);
+        H.vg = VGraph{};
+    }
     return MG_OK;
 }
 

@@ -47,6 +47,8 @@ struct Level {
     C2<T>* r = nullptr;           // residual
     KState* ks = nullptr;         // smoother state
     ApplyTimer* timer = nullptr;  // shared by both precisions of the grid
+    int shape = 0;                // launch shape of the apply (0: built-in; tune.cu)
+    double shape_us[2] = {0, 0};  // the tuner's times of the chosen and the built-in shape
 
     void apply(C2<T>* y, const C2<T>* xin, const C2<T>* b, bool dagger, Gate g, cudaStream_t s) const {
         cudaEvent_t e1 = nullptr;
@@ -55,9 +57,9 @@ struct Level {
             e1 = timer->next();
             if (e0) cudaEventRecord(e0, s);
         }
-        if (U) launch_wilson<T>(y, xin, U, b, m0, Nx, Nt, dagger, g, s);
-        else if (F) launch_stencil_lr<T>(y, xin, F, b, Nx, Nt, dagger, g, s);
-        else launch_stencil<T>(y, xin, A, b, Nx, Nt, dof, dagger, g, s);
+        if (U) launch_wilson<T>(y, xin, U, b, m0, Nx, Nt, dagger, g, s, shape);
+        else if (F) launch_stencil_lr<T>(y, xin, F, b, Nx, Nt, dagger, g, s, shape);
+        else launch_stencil<T>(y, xin, A, b, Nx, Nt, dof, dagger, g, s, shape);
         if (e1) cudaEventRecord(e1, s);
     }
 };
@@ -220,6 +222,8 @@ mg_status coarse_solve_block(Handle& H, const float2* f, float2* x, int nb, doub
                              long long* iters, bool probe = false, long spin = 0);
 // the tensor-core block stencil of grid l alone (device x, y: [nb][n_l] complex64, nb % 8 == 0)
 mg_status apply_block(Handle& H, int l, const float2* x, float2* y, int nb, bool fp16, cudaStream_t s);
+// Launch shapes of the handle's level applies chosen by timing (tune.cu), at set-up
+mg_status tune_shapes(Handle& H, cudaStream_t s);
 // A solve context of `owner` (capi.cu): same hierarchy and deflation space,
 // own workspaces and stream; usable with mg_solve and released with mg_destroy
 // (before its owner).  The owner's deflation space must exist.

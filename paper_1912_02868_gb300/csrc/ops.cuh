@@ -31,18 +31,27 @@ struct RedWS {
     int max_blocks = 0;
 };
 
+// Launch shapes.  The level applies below take a `shape`: 0 is the built-in
+// choice; otherwise threads per block (Wilson, one thread per site) or sites per
+// block (FP32 stencils).  A shape only groups sites into blocks: the arithmetic of
+// every site, and so every result bit, is the same for all of them (tune.cu picks
+// one by timing).
+constexpr int WILSON_SHAPES[] = {64, 128, 256};
+constexpr int STENCIL_F32_SHAPES[] = {4, 8, 16, 24, 32};
+constexpr int STENCIL_LR_F32_SHAPES[] = {4, 8, 12, 16};
+
 // ---------------------------------------------------------------- wilson ----
 // y = D x, D^+ x (dagger), or y = b - D x when b != nullptr.  Section 2.
 template <typename T>
 void launch_wilson(C2<T>* y, const C2<T>* x, const C2<T>* U, const C2<T>* b, double m0, int Lx, int Lt,
-                   bool dagger, Gate g, cudaStream_t s);
+                   bool dagger, Gate g, cudaStream_t s, int shape = 0);
 
 // --------------------------------------------------------------- stencil ----
 // y = A x (or sigma3^ A sigma3^ x, or b - A x) for the 5-point block stencil with
 // dof x dof blocks stored column-major: A[s][d][l][k] is entry (k, l).
 template <typename T>
 void launch_stencil(C2<T>* y, const C2<T>* x, const C2<T>* A, const C2<T>* b, int Nx, int Nt, int dof,
-                    bool dagger, Gate g, cudaStream_t s);
+                    bool dagger, Gate g, cudaStream_t s, int shape = 0);
 
 // The 24-dof stencil with low-rank hop blocks (intermediate grid): per site
 // LR_SITE complex entries, the self block column-major (576), then for each hop
@@ -52,7 +61,7 @@ constexpr int LR_RANK = 4;
 constexpr int LR_SITE = 24 * 24 + 4 * 2 * LR_RANK * 24;
 template <typename T>
 void launch_stencil_lr(C2<T>* y, const C2<T>* x, const C2<T>* F, const C2<T>* b, int Nx, int Nt, bool dagger,
-                       Gate g, cudaStream_t s);
+                       Gate g, cudaStream_t s, int shape = 0);
 // F (FP64, LR_SITE per site) from the dense stencil A: the self blocks copied,
 // each hop block factored by Gram-Schmidt with column pivoting (4 steps);
 // *maxerr (device) receives max over blocks of ||A - Q R||_F / ||A||_F

@@ -128,15 +128,16 @@ __global__ void __launch_bounds__(F32_MAX_SPB* F32_TPS) k_stencil_f32(float2* __
 
 template <typename T>
 void launch_stencil(C2<T>* y, const C2<T>* x, const C2<T>* A, const C2<T>* b, int Nx, int Nt, int dof,
-                    bool dagger, Gate g, cudaStream_t s) {
+                    bool dagger, Gate g, cudaStream_t s, int shape) {
     const long nsite = (long)Nx * Nt;
     // only dof = 24 is built (12 near-null vectors, chirally doubled)
     if constexpr (std::is_same<T, float>::value) {
-        // whole waves of one block per SM, sites spread evenly over the blocks
+        // built-in shape: whole waves of one block per SM, sites spread evenly
+        // over the blocks; or `shape` sites per block
         const long sms = sm_count();
         const long waves = (nsite + sms * F32_MAX_SPB - 1) / (sms * F32_MAX_SPB);
         const long blocks = std::min(sms * waves, nsite);
-        const int spb = (int)((nsite + blocks - 1) / blocks);
+        const int spb = (shape >= 1 && shape <= F32_MAX_SPB) ? shape : (int)((nsite + blocks - 1) / blocks);
         const unsigned grid = (unsigned)((nsite + spb - 1) / spb);
         k_stencil_f32<<<grid, spb * F32_TPS, 0, s>>>(y, x, A, b, Nx, Nt, spb, dagger ? 1 : 0, g);
     } else {
@@ -147,8 +148,8 @@ void launch_stencil(C2<T>* y, const C2<T>* x, const C2<T>* A, const C2<T>* b, in
 }
 
 template void launch_stencil<double>(C2<double>*, const C2<double>*, const C2<double>*, const C2<double>*, int, int,
-                                     int, bool, Gate, cudaStream_t);
+                                     int, bool, Gate, cudaStream_t, int);
 template void launch_stencil<float>(C2<float>*, const C2<float>*, const C2<float>*, const C2<float>*, int, int, int,
-                                    bool, Gate, cudaStream_t);
+                                    bool, Gate, cudaStream_t, int);
 
 }  // namespace mg

@@ -287,14 +287,15 @@ __global__ void __launch_bounds__(LRF_MAX_SPB* LRF_TPS) k_stencil_lr_f32(float2*
 
 template <typename T>
 void launch_stencil_lr(C2<T>* y, const C2<T>* x, const C2<T>* F, const C2<T>* b, int Nx, int Nt, bool dagger,
-                       Gate g, cudaStream_t s) {
+                       Gate g, cudaStream_t s, int shape) {
     const long nsite = (long)Nx * Nt;
     if constexpr (std::is_same<T, float>::value) {
-        // whole waves of one block per SM, sites spread evenly over the blocks
+        // built-in shape: whole waves of one block per SM, sites spread evenly
+        // over the blocks; or `shape` sites per block
         const long sms = sm_count();
         const long waves = (nsite + sms * LRF_MAX_SPB - 1) / (sms * LRF_MAX_SPB);
         const long blocks = std::min(sms * waves, nsite);
-        const int spb = (int)((nsite + blocks - 1) / blocks);
+        const int spb = (shape >= 1 && shape <= LRF_MAX_SPB) ? shape : (int)((nsite + blocks - 1) / blocks);
         const unsigned grid = (unsigned)((nsite + spb - 1) / spb);
         k_stencil_lr_f32<<<grid, spb * LRF_TPS, 0, s>>>(y, x, F, b, Nx, Nt, spb, dagger ? 1 : 0, g);
     } else {
@@ -313,8 +314,8 @@ void launch_factor_hops(double2* F, const double2* A, long nsite, double* maxerr
 }
 
 template void launch_stencil_lr<double>(C2<double>*, const C2<double>*, const C2<double>*, const C2<double>*, int,
-                                        int, bool, Gate, cudaStream_t);
+                                        int, bool, Gate, cudaStream_t, int);
 template void launch_stencil_lr<float>(C2<float>*, const C2<float>*, const C2<float>*, const C2<float>*, int, int,
-                                       bool, Gate, cudaStream_t);
+                                       bool, Gate, cudaStream_t, int);
 
 }  // namespace mg

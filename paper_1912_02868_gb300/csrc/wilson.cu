@@ -102,26 +102,28 @@ __global__ void __launch_bounds__(256) k_wilson(C2<T>* __restrict__ y, const C2<
 
 }  // namespace
 
+// threads: threads per block, one thread per site (a multiple of 32, at most 256)
 template <typename T>
 void wilson_grid(C2<T>* y, const C2<T>* x, const C2<T>* U, const C2<T>* b, double m0, int Lx, int Lt, bool dagger,
-                 long vr, int nb, Gate g, cudaStream_t s) {
+                 long vr, int nb, Gate g, cudaStream_t s, int threads = 256) {
     const int n = Lx * Lt;
-    const dim3 grid(nblocks(n, 256), nb);
+    const dim3 grid(nblocks(n, threads), nb);
     const T diag = (T)(m0 + 2.0);
     if (dagger) {
-        if (b) k_wilson<T, true, true><<<grid, 256, 0, s>>>(y, x, U, b, diag, Lx, Lt, vr, g);
-        else k_wilson<T, true, false><<<grid, 256, 0, s>>>(y, x, U, b, diag, Lx, Lt, vr, g);
+        if (b) k_wilson<T, true, true><<<grid, threads, 0, s>>>(y, x, U, b, diag, Lx, Lt, vr, g);
+        else k_wilson<T, true, false><<<grid, threads, 0, s>>>(y, x, U, b, diag, Lx, Lt, vr, g);
     } else {
-        if (b) k_wilson<T, false, true><<<grid, 256, 0, s>>>(y, x, U, b, diag, Lx, Lt, vr, g);
-        else k_wilson<T, false, false><<<grid, 256, 0, s>>>(y, x, U, b, diag, Lx, Lt, vr, g);
+        if (b) k_wilson<T, false, true><<<grid, threads, 0, s>>>(y, x, U, b, diag, Lx, Lt, vr, g);
+        else k_wilson<T, false, false><<<grid, threads, 0, s>>>(y, x, U, b, diag, Lx, Lt, vr, g);
     }
     count_launch();
 }
 
 template <typename T>
 void launch_wilson(C2<T>* y, const C2<T>* x, const C2<T>* U, const C2<T>* b, double m0, int Lx, int Lt,
-                   bool dagger, Gate g, cudaStream_t s) {
-    wilson_grid<T>(y, x, U, b, m0, Lx, Lt, dagger, 0, 1, g, s);
+                   bool dagger, Gate g, cudaStream_t s, int shape) {
+    const int threads = (shape >= 32 && shape <= 256 && shape % 32 == 0) ? shape : 256;
+    wilson_grid<T>(y, x, U, b, m0, Lx, Lt, dagger, 0, 1, g, s, threads);
 }
 
 template <typename T>
@@ -131,9 +133,9 @@ void launch_bwilson(C2<T>* y, const C2<T>* x, const C2<T>* U, const C2<T>* b, do
 }
 
 template void launch_wilson<double>(C2<double>*, const C2<double>*, const C2<double>*, const C2<double>*, double,
-                                    int, int, bool, Gate, cudaStream_t);
+                                    int, int, bool, Gate, cudaStream_t, int);
 template void launch_wilson<float>(C2<float>*, const C2<float>*, const C2<float>*, const C2<float>*, double, int,
-                                   int, bool, Gate, cudaStream_t);
+                                   int, bool, Gate, cudaStream_t, int);
 template void launch_bwilson<double>(C2<double>*, const C2<double>*, const C2<double>*, const C2<double>*, double,
                                      int, int, long, int, Gate, cudaStream_t);
 template void launch_bwilson<float>(C2<float>*, const C2<float>*, const C2<float>*, const C2<float>*, double, int,

@@ -37,14 +37,14 @@ def test_library_exports_every_declared_symbol():
     p = pkg.default_params()
     assert (p.nvec, p.block, p.fgmres_m, p.dr_m, p.dr_k, p.smooth_steps) == (12, 4, 8, 30, 10, 2)
     assert (p.pair_rhs, p.vcycle_graph, p.coarse_half, p.coarse_dcgs2, p.partial_tol) == (0, 1, 1, 0, 0.0)
-    assert (p.lowrank_hops, p.coarse_mma) == (1, 1)
+    assert (p.lowrank_hops, p.coarse_mma, p.autotune) == (1, 1, 1)
     out = ctypes.c_void_p()
     st = lib.mg_setup(None, 64, 64, 0.0, 12, 4, None, None, None, None, ctypes.byref(out))
     assert st == _lib.MG_EINVAL and b"gauge" in lib.mg_last_error()
     # the switches are validated before any device work (the gauge buffer is never read)
     dummy = ctypes.create_string_buffer(16)
     for field, bad in (("pair_rhs", 2), ("vcycle_graph", -1), ("coarse_half", 3), ("coarse_dcgs2", 2),
-                       ("lowrank_hops", 2), ("coarse_mma", -1)):
+                       ("lowrank_hops", 2), ("coarse_mma", -1), ("autotune", 2)):
         q = pkg.default_params(**{field: bad})
         st = lib.mg_setup(ctypes.cast(dummy, ctypes.c_void_p), 64, 64, 0.1, 12, 4, ctypes.byref(q), None, None, None,
                           ctypes.byref(out))
