@@ -358,6 +358,11 @@ def run_scale(mg, torch, np, dev, peaks, peak_kind, nrhs=16, Ls=1024):
         b_mma = 5 * 576 * 4 * s1 + 2 * nrhs * n1 * 8  # FP16 operator once, 16 vectors in and out (complex64)
         t_f32 = timed_level_applies(mg, torch, dev, h, 1, lambda: mg.mg_apply(h, 1, x1[0], y1[0], precision=mg.MG_F32))
         b_f32 = (LR_SITE + 2 * 24) * 8 * s1
+        # K1 at this size through the handle's fine apply, every launch shape (L2 flushed)
+        try:
+            k1_shapes = k1_by_shape(mg, torch, dev, h, Ls, peaks["hbm_gbs"])
+        except Exception as e:  # reported, not fatal: the solve figures above stand
+            k1_shapes = {"error": str(e)}
     finally:
         h.close()
     fine = fine_roofline(mg, dev, peaks, peak_kind, Lb=Ls)
@@ -370,6 +375,11 @@ def run_scale(mg, torch, np, dev, peaks, peak_kind, nrhs=16, Ls=1024):
             "first_rhs_gmres_dr_s": dr_s, "setup_s": setup_s, "field_gen_s": gen_s,
             "field": "GPU heatbath, bit-identical to the host generator", "m0_fingerprint_match": fp_ok,
             "k1_wilson_roofline": fine,
+            "k1_wilson_by_shape": {"what": "FP32 fine apply of the 1024^2 handle pinned to each launch shape: 0 "
+                                           "built-in (256 threads, one site each), 64/128/256 threads, 1004/1008 "
+                                           "tiles of 32 x 4 / 32 x 8 sites staged in shared memory, 2002/2004 "
+                                           "columns of 2 / 4 sites a lane with x neighbours by warp shuffles; "
+                                           "48 B a site, L2 flushed before every apply", "shapes": k1_shapes},
             "k3_block_stencil_roofline": {
                 "bound": "hbm", "kernel": f"k_bstencil_mma<fp16> (256^2 x 24, {nrhs} RHS)",
                 "achieved": b_mma / t_mma / 1e9, "peak": hb, "unit": "GB/s", "frac": b_mma / t_mma / 1e9 / hb,
@@ -988,6 +998,65 @@ def run_study(args):
     print(json.dumps(out), flush=True)
 
 
+K1_SHAPES = (0, 64, 128, 256, 1004, 1008, 2002, 2004)  # fine-apply shapes: 0 built-in, threads a block,
+#                                                        1000 + shared-memory tile rows, 2000 + sites a lane
+
+
+def k1_by_shape(mg, torch, dev, h, Lf, hbm, launches=10):
+    """The FP32 fine Wilson-Dirac apply of handle h (an Lf^2 lattice) pinned to each
+    launch shape in turn, L2 flushed before every apply, timed by the handle's own
+    events: {shape: {us, GB_per_s, frac}} at 48 B a site.  The handle's shape is
+    put back afterwards."""
+    n0 = Lf * Lf * 2
+    x = torch.complex(torch.randn(n0, device=dev), torch.randn(n0, device=dev))
+    y = torch.empty_like(x)
+    kept = mg.mg_launch_shape(h, 0, mg.MG_F32)[0]
+    out = {}
+    try:
+        for shp in K1_SHAPES:
+            mg.mg_set_launch_shape(h, 0, mg.MG_F32, shp)
+            t = timed_level_applies(mg, torch, dev, h, 0, lambda: mg.mg_apply(h, 0, x, y, precision=mg.MG_F32),
+                                    launches=launches, warm=2)
+            gbs = 48 * Lf * Lf / t / 1e9
+            out[str(shp)] = {"us": t * 1e6, "GB_per_s": gbs, "frac": gbs / hbm}
+    finally:
+        mg.mg_set_launch_shape(h, 0, mg.MG_F32, kept)
+    return out
+
+
+def run_micro_wilson(args):
+    """The FP32 fine Wilson-Dirac apply alone on an L^2 lattice (--micro-lattice),
+    every launch shape, L2 flushed before every apply: the one-thread-per-site
+    kernel at 64/128/256 threads a block, the shared-memory tiles of 32 x 4 and
+    32 x 8 sites, and the register columns of 2 and 4 sites a lane.  The hierarchy around it is built from random vectors with
+    seeded random U(1) links (the apply's cost does not depend on the values)."""
+    import numpy as np
+    import torch
+    import paper_1912_02868_gb300 as mg
+    dev = torch.device("cuda:0")
+    Lm = args.micro_lattice
+    gen = torch.Generator(device=dev).manual_seed(1912)
+    th = torch.rand((Lm, Lm, 2), generator=gen, device=dev, dtype=torch.float64) * (2 * np.pi)
+    U = torch.polar(torch.ones_like(th), th).contiguous()
+    v0 = torch.complex(torch.randn((12, Lm * Lm * 2), generator=gen, device=dev, dtype=torch.float64),
+                       torch.randn((12, Lm * Lm * 2), generator=gen, device=dev, dtype=torch.float64))
+    n1 = (Lm // 4) ** 2 * 24
+    v1 = torch.complex(torch.randn((12, n1), generator=gen, device=dev, dtype=torch.float64),
+                       torch.randn((12, n1), generator=gen, device=dev, dtype=torch.float64))
+    h = mg.mg_setup_from_vectors(U, Lm, Lm, 0.1, v0, v1, params=mg.default_params(precision=mg.MG_MIXED))
+    del v0, v1
+    try:
+        peaks, kind = measured_peaks()
+        res = k1_by_shape(mg, torch, dev, h, Lm, peaks["hbm_gbs"], launches=args.micro_reps)
+        tuned = mg.mg_launch_shape(h, 0, mg.MG_F32)
+    finally:
+        h.close()
+    print(json.dumps({"kernel": "k_wilson<float> / k_wilson_tile<float> / k_wilson_col<float>", "lattice": Lm, "bytes": 48 * Lm * Lm,
+                      "by_shape": res, "autotuner_choice": {"shape": tuned[0], "us": tuned[1], "builtin_us": tuned[2],
+                                                            "l2": "not flushed (set-up timing)"},
+                      "peak_gbs": peaks["hbm_gbs"], "peak_source": kind}), flush=True)
+
+
 def run_micro(args):
     """One kernel alone, one JSON line per block size.  bstencil: the tensor-core
     block stencil of grid 1 or 2 (L2 flushed before every launch; algorithmic
@@ -1010,18 +1079,7 @@ def run_micro(args):
                     starts1=torch.from_numpy(synth.nullvec_starts(Lm, 0, 1, 12, (Lm // 4) ** 2 * 24)).to(dev))
     try:
         for nb in [int(v) for v in args.micro_nrhs.split(",")]:
-            if args.micro == "wilson":
-                # the FP32 fine Wilson-Dirac apply alone: 48 B a site (spinor in, links, spinor out)
-                Ug = torch.from_numpy(U).to(dev).to(torch.complex64)
-                x = torch.complex(torch.randn((Lm, Lm, 2), device=dev), torch.randn((Lm, Lm, 2), device=dev))
-                y = torch.empty_like(x)
-                m0w = synth.m0_for(Lm, 0)
-                t = timed_launches(torch, dev, lambda: mg.mg_wilson_apply(Ug, Lm, Lm, m0w, x, y, precision=mg.MG_F32),
-                                   launches=args.micro_reps, warm=1)
-                nbytes = 48 * Lm * Lm
-                out = {"kernel": "k_wilson<float>", "sites": Lm * Lm, "us": t * 1e6, "GB_per_s": nbytes / t / 1e9,
-                       "bytes": nbytes}
-            elif args.micro == "stencil":
+            if args.micro == "stencil":
                 # the FP32 intermediate-grid stencil of one vector as the V-cycle applies it
                 nx, nt, dof = mg.mg_level_shape(h, 1)
                 n1, s1 = nx * nt * dof, nx * nt
@@ -1077,6 +1135,9 @@ def run_micro(args):
 
 def main():
     args = parse()
+    if args.micro == "wilson":
+        run_micro_wilson(args)
+        return
     if args.micro:
         run_micro(args)
         return

@@ -131,8 +131,9 @@ typedef struct {
     int autotune;          /* 1 (default): at set-up, each level apply (the fine Wilson-Dirac
                               apply; the FP32 block stencils of grids 1 and 2) is timed with every
                               candidate launch shape and the fastest kept (mg_launch_shape).  A
-                              shape only groups sites into blocks, so results are the same bit for
-                              bit with any choice.  0: the built-in shapes */
+                              shape only groups sites into blocks (for the fine apply: threads per
+                              block, tiles staged in shared memory, or columns of sites a thread),
+                              so results are the same bit for bit with any choice.  0: the built-in shapes */
     int coarse_mma;        /* 1 (default): with coarse_half, the single-right-hand-side GMRES-Proj
                               cluster kernel applies the FP16 operator on tensor cores (mma.sync
                               m16n8k16, FP32 accumulation) to each basis vector split into two
@@ -341,15 +342,21 @@ mg_status mg_stencil_info(mg_handle h, int level, int* factored, double* max_rel
 
 /* Launch shape of the apply of `level` (0..2) in `precision` (MG_F64 or MG_F32), as
  * the set-up's autotuner chose it (mg_params.autotune): *shape = 0 for the built-in
- * shape, else threads per block (level 0) or sites per block (FP32 stencils of
- * levels 1 and 2).  us (host, double[2], or NULL): the time of one apply with the
+ * shape, else threads per block of the one-thread-per-site kernel, 1000 + r for
+ * tiles of 32 x r sites staged in shared memory, or 2000 + r for columns of r sites
+ * a thread with the x neighbours taken from adjacent lanes (level 0), or sites per
+ * block (FP32 stencils of levels 1 and 2).  us (host, double[2], or NULL): the time of one apply with the
  * chosen and with the built-in shape, in microseconds, as timed at set-up on this
  * GPU (0 where nothing was tuned: FP64 stencils, autotune off).  The shape never
  * changes results: it only groups sites into blocks. */
 mg_status mg_launch_shape(mg_handle h, int level, int precision, int* shape, double* us);
 
 /* Pin the launch shape of the apply of `level` in `precision`: 0 (built-in), or one
- * of the candidates the autotuner tries: 64, 128, 256 threads per block at level 0;
+ * of the candidates the autotuner tries: 64, 128, 256 threads per block, 1004 and
+ * 1008 (tiles of 32 x 4 and 32 x 8 sites whose spinors, with a one-site halo, and
+ * links are staged in shared memory), or 2002 and 2004 (each thread keeps a column
+ * of 2 or 4 sites along t in registers and takes its x neighbours from the adjacent
+ * lanes of its warp) at level 0;
  * 4, 8, 12, 16 sites per block for the FP32 stencil with rank-4 hop factors; 4, 8,
  * 16, 24, 32 for the dense FP32 stencil.  The FP64 stencils take 0 only.  A captured
  * V-cycle graph of the handle is dropped and captured again; solve contexts made

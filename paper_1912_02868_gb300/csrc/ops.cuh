@@ -32,11 +32,15 @@ struct RedWS {
 };
 
 // Launch shapes.  The level applies below take a `shape`: 0 is the built-in
-// choice; otherwise threads per block (Wilson, one thread per site) or sites per
-// block (FP32 stencils).  A shape only groups sites into blocks: the arithmetic of
-// every site, and so every result bit, is the same for all of them (tune.cu picks
-// one by timing).
-constexpr int WILSON_SHAPES[] = {64, 128, 256};
+// choice; otherwise threads per block (Wilson, one thread per site), WILSON_TILE + r
+// (Wilson, tiles of 32 x r sites staged in shared memory), WILSON_COLS + r (Wilson,
+// columns of r sites a lane in registers, x neighbours by warp shuffles), or sites
+// per block (FP32 stencils).  A shape only groups sites into blocks: the arithmetic of every site,
+// and so every result bit, is the same for all of them (tune.cu picks one by
+// timing).
+constexpr int WILSON_TILE = 1000;
+constexpr int WILSON_COLS = 2000;
+constexpr int WILSON_SHAPES[] = {64, 128, 256, WILSON_TILE + 4, WILSON_TILE + 8, WILSON_COLS + 2, WILSON_COLS + 4};
 constexpr int STENCIL_F32_SHAPES[] = {4, 8, 16, 24, 32};
 constexpr int STENCIL_LR_F32_SHAPES[] = {4, 8, 12, 16};
 

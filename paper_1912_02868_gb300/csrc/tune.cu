@@ -3,7 +3,8 @@
 // The level applies -- the fine Wilson-Dirac apply and the FP32 block stencils
 // of the intermediate and coarsest grids -- take a launch shape that only groups
 // sites into blocks (threads per block for the one-thread-per-site Wilson
-// kernel, sites per block for the stencils).  Each site's arithmetic, and so
+// kernel, 32 x r tiles for the shared-memory one, sites a lane for the
+// register-column one; sites per block for the stencils).  Each site's arithmetic, and so
 // every result bit, is the same for all shapes; only the speed differs.  At
 // set-up, every tunable apply of the handle is timed with each candidate shape
 // and with the built-in one, on the handle's stream and its own workspace

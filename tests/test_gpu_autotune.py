@@ -15,6 +15,11 @@ every shape must give the same result bit for bit:
   with autotune off;
 * a whole mixed solve gives the same solution bits and outer count with the
   tuner on and off;
+* on a 48^2 lattice, whose second tile (warp) of each row is ragged, the fine
+  apply pinned to each shared-memory tile and register-column shape gives the
+  built-in bits (D and D^+,
+  FP32 and FP64), and so does a whole mixed solve with it pinned in both
+  precisions (the fused residual b - D x then runs in the tile kernel too);
 * shapes that are not candidates are refused.
 """
 import numpy as np
@@ -22,11 +27,13 @@ import pytest
 
 import synth
 import oracle_cache as oc
+from oracle import dirac
 from gpu_util import dev, host
 
 pytestmark = pytest.mark.gpu
 
-WILSON = (64, 128, 256)
+WILSON = (64, 128, 256, 1004, 1008, 2002, 2004)  # threads a block; 1000 + r: 32 x r shared-memory tiles;
+#                                                  2000 + r: r-site columns a lane, shuffles
 LR = (4, 8, 12, 16)
 DENSE = (4, 8, 16, 24, 32)
 
@@ -113,3 +120,44 @@ def test_solve_same_bits_tuned_or_not(mgmod):
             g.close()
     assert out[0][1] == out[1][1] and out[0][2] == out[1][2]
     assert np.array_equal(out[0][0], out[1][0])
+
+
+
+@pytest.mark.parametrize("tile", [1004, 1008, 2002, 2004])
+def test_tiled_fine_apply_ragged_and_in_solve(mgmod, tile):
+    """48^2 lattice: a tile row (a warp's columns) holds 32 sites, so the second of
+    every row is ragged (16 sites) and its neighbours wrap inside it.  Level-0 applies (D and
+    D^+, FP32 and FP64) equal the built-in shape's bit for bit, and so does a whole
+    mixed solve with the fine apply pinned to the tile in both precisions, which
+    also runs the fused residual b - D x of the V-cycle and of the FP64 outer
+    solve in the tile kernel."""
+    import torch
+    L, m0 = 48, 0.2
+    U = synth.gauge_field(L, 0)
+    b = synth.rhs(L, 0, 4)[0]
+    xv = synth.complex_gaussian((L * L * 2,), 7790)
+    out = []
+    for shape in (0, tile):
+        g = mgmod.mg_setup(dev(U), L, L, m0, params=mgmod.default_params(precision=mgmod.MG_MIXED, autotune=0),
+                           starts0=dev(synth.nullvec_starts(L, 0, 0, 12, L * L * 2)),
+                           starts1=dev(synth.nullvec_starts(L, 0, 1, 12, (L // 4) ** 2 * 24)))
+        try:
+            applies = []
+            for prec, dt in ((mgmod.MG_F32, torch.complex64), (mgmod.MG_F64, torch.complex128)):
+                mgmod.mg_set_launch_shape(g, 0, prec, shape)
+                assert mgmod.mg_launch_shape(g, 0, prec)[0] == shape
+                for dagger in (False, True):
+                    y = torch.full((L * L * 2,), float("nan"), dtype=dt, device="cuda")
+                    mgmod.mg_apply(g, 0, dev(xv, dt), y, dagger=dagger, precision=prec)
+                    applies.append(host(y))
+            x = torch.zeros(b.shape, dtype=torch.complex128, device="cuda")
+            _, it, rr, _ = mgmod.mg_solve(g, dev(b), x, 1, 1e-8)
+            out.append((applies, host(x), it[0], rr[0]))
+        finally:
+            g.close()
+    for a, c in zip(out[0][0], out[1][0]):
+        assert np.array_equal(a, c)
+    r = np.linalg.norm(dirac.wilson(U, out[0][1], m0) - b) / np.linalg.norm(b)
+    assert out[0][3] <= 1e-8 and r <= 1.0001e-8
+    assert out[0][2] == out[1][2] and out[0][3] == out[1][3]
+    assert np.array_equal(out[0][1], out[1][1])
