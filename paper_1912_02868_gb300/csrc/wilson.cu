@@ -12,7 +12,7 @@
 //   -x: h = U_x^*(s-x)(p0 + p1),       contributes (-h/2, -h/2)
 //   +t: h = U_t(s)   (p0 + i p1),      contributes (-h/2, +i h/2)
 //   -t: h = U_t^*(s-t)(p0 - i p1),     contributes (-h/2, -i h/2)
-// Two launch forms with the same per-site arithmetic (wilson_site), so the
+// Three launch forms with the same per-site arithmetic (wilson_site), so the
 // same result bits:
 // * k_wilson: one thread per site; the site's two spin components and its two
 //   links are one 32-byte (FP64) or 16-byte (FP32) vector load each.  Neighbour
