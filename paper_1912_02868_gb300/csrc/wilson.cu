@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(256) k_wilson(C2<T>* __restrict__ y, const C2<
                                                                 U2[sxm].a, U2[stm].b, sf, sb, diag, bb);
 }
 
-// v mod n for v in [-1, n + 33] (tile coordinates with their halo)
+// v mod n for v >= -1 (a tile or column coordinate with its one-site halo)
 __device__ __forceinline__ int wrap(int v, int n) {
     if (v < 0) return v + n;
     return v < n ? v : v % n;
